@@ -1,0 +1,89 @@
+"""The Davidson iteration of Algorithm 3 (oracle; test infrastructure).
+
+One iteration, for a basis V of k orthonormal columns whose newest column has not yet
+been projected (Algorithm 3, Sec. 5):
+
+  W(:,k) = H V(:,k)                  projection (Eq. 11)
+  B(:,k) = V^T W(:,k)                "asymmetric" matrix-vector product; B is symmetric,
+                                     so the same numbers fill row k
+  (lambda, y) = smallest eigenpair of B
+  x = V y,  r = W y - lambda x
+  stop if ||r|| <= tol
+  correct r; orthonormalise it against V; append it to V.
+
+Readings where the paper is silent (Sec. 6 names the Sadkane-Sidje variant only):
+
+* correction: diagonal (Davidson) preconditioner t_e = r_e / (lambda - D_e) with
+  D = diag(H_SB); where |lambda - D_e| < 1e-8 the denominator is replaced by
+  +-1e-8 with the sign of lambda - D_e (plus when it is zero);
+* orthogonalisation: classical Gram-Schmidt applied twice; if the norm left after it is
+  below 1e-10 of the norm before, the raw residual r is used instead, and if that also
+  collapses the iteration reports a breakdown;
+* subspace limit: 20 columns (Sec. 6.1); when the basis is full, it is collapsed to the
+  current Ritz vector x with W replaced by W y, before the new direction is added;
+* convergence: ||r||_2 <= tol on a normalised x; at most ``max_iter`` iterations.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+DENOM_GUARD = 1e-8
+BREAKDOWN = 1e-10
+
+
+def correct(r: np.ndarray, lam: float, D: np.ndarray) -> np.ndarray:
+    den = lam - D
+    small = np.abs(den) < DENOM_GUARD
+    den = np.where(small, np.where(den >= 0.0, DENOM_GUARD, -DENOM_GUARD), den)
+    return r / den
+
+
+def _cgs2(V: np.ndarray, t: np.ndarray) -> np.ndarray:
+    for _ in range(2):
+        t = t - V @ (V.T @ t)
+    return t
+
+
+def davidson(matvec, D: np.ndarray, x0: np.ndarray, tol: float = 1e-10,
+             max_iter: int = 1000, max_subspace: int = 20):
+    """Lowest eigenpair of the symmetric operator ``matvec``; returns (lam, x, info)."""
+    n = x0.shape[0]
+    V = np.zeros((n, max_subspace))
+    W = np.zeros((n, max_subspace))
+    B = np.zeros((max_subspace, max_subspace))
+    V[:, 0] = x0 / np.linalg.norm(x0)
+    k = 1
+    history = []
+    lam, x, rn = np.nan, V[:, 0].copy(), np.inf
+    for it in range(1, max_iter + 1):
+        W[:, k - 1] = matvec(V[:, k - 1])
+        col = V[:, :k].T @ W[:, k - 1]
+        B[:k, k - 1] = col
+        B[k - 1, :k] = col
+        evals, evecs = np.linalg.eigh(B[:k, :k])
+        lam, y = float(evals[0]), evecs[:, 0]
+        x = V[:, :k] @ y
+        wy = W[:, :k] @ y
+        r = wy - lam * x
+        rn = float(np.linalg.norm(r))
+        history.append((lam, rn))
+        if rn <= tol:
+            return lam, x, {"iters": it, "resnorm": rn, "converged": True, "history": history}
+        t = correct(r, lam, D)
+        if k == max_subspace:          # restart with the Ritz vector
+            V[:, 0] = x
+            W[:, 0] = wy
+            B[:, :] = 0.0
+            B[0, 0] = lam
+            k = 1
+        before = np.linalg.norm(t)
+        t_o = _cgs2(V[:, :k], t)
+        if np.linalg.norm(t_o) < BREAKDOWN * before:
+            before = np.linalg.norm(r)
+            t_o = _cgs2(V[:, :k], r)
+            if np.linalg.norm(t_o) < BREAKDOWN * before:
+                return lam, x, {"iters": it, "resnorm": rn, "converged": False,
+                                "history": history, "breakdown": True}
+        V[:, k] = t_o / np.linalg.norm(t_o)
+        k += 1
+    return lam, x, {"iters": max_iter, "resnorm": rn, "converged": False, "history": history}
