@@ -1,0 +1,202 @@
+/*
+ * dmrg.h -- C ABI of the GB300 library for the DMRG superblock Davidson path.
+ *
+ * The library finds the lowest eigenpair of a superblock Hamiltonian written in the LR
+ * form of Sec. 4.1,
+ *
+ *     H_SB = sum_a coef_a  A_a (x) B_a                                   (Eq. 9)
+ *
+ * restricted to one symmetry sector Q (Sec. 3), with the projection evaluated as the
+ * sector-decomposed matrix products
+ *
+ *     X'_{jl} += coef_a * A_{a, i->j} X_{ik} B_{a, k->l}^T                (Eq. 11)
+ *
+ * and the Davidson iteration of Algorithm 3 (Sec. 5) around it.
+ *
+ * Conventions used by every call:
+ *
+ *  - Vector layout.  A superblock vector of length n is the concatenation, in the order
+ *    of the pair list (pair_i[p], pair_k[p]), of the dense row-major segments X_{ik} of
+ *    shape [dimL[i], dimR[k]]; element psi(a, b) of segment p sits at
+ *    x[offset_p + a * dimR[k] + b], offset_p being the sum of the sizes of the earlier
+ *    segments.  The reshape of Eq. 10 is therefore the row-major one (left index slow).
+ *  - Operator blocks map input sector idx_in to output sector idx_out and are dense
+ *    row-major [rows = dim(idx_out), cols = dim(idx_in)] matrices with leading
+ *    dimension ld >= cols, in float64.  Block data may live in host or device memory
+ *    (dmrg_superblock_desc.data_location); the plan copies what it needs at creation,
+ *    so the caller may free the descriptor and the block data afterwards.
+ *  - Vectors passed to dmrg_project / dmrg_davidson_* (x, y, x0, x_out, d) are device
+ *    pointers to float64 arrays of n elements owned by the caller, unless a call says
+ *    otherwise (the *_host variants take host pointers).  They are borrowed for the
+ *    duration of the call only.
+ *  - Streams.  A stream is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Calls enqueue their work on it; the calls named *_solve*, the *_host
+ *    variants and dmrg_davidson_step return only when their results are complete.
+ *  - Errors.  No exception crosses the ABI.  Every call returns a dmrg_status;
+ *    dmrg_last_error() gives a thread-local message for the last failure.  A CUDA error
+ *    maps to DMRG_ERR_CUDA.  Invalid sizes or indices map to DMRG_ERR_INVALID_ARG or
+ *    DMRG_ERR_SHAPE before any device work is enqueued.
+ *  - Single GPU.  A plan lives on the device that was current when it was created; use
+ *    it with that device current.
+ */
+#ifndef DMRG_GB300_H
+#define DMRG_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  DMRG_OK = 0,
+  DMRG_ERR_INVALID_ARG = 1,   /* null pointer, negative size, index out of range      */
+  DMRG_ERR_SHAPE = 2,         /* block shape or pair table inconsistent with sectors  */
+  DMRG_ERR_OOM = 3,           /* device or host allocation failed                      */
+  DMRG_ERR_CUDA = 4,          /* a CUDA runtime or kernel error                        */
+  DMRG_ERR_NOT_CONVERGED = 5, /* Davidson hit max_iter; best pair and info are filled  */
+  DMRG_ERR_NUMERIC = 6,       /* NaN/Inf in a residual or a basis breakdown            */
+  DMRG_ERR_UNSUPPORTED = 7    /* option not available in this build                    */
+} dmrg_status;
+
+/* Arithmetic of the projection GEMMs.  FP64: float64 operands and accumulation.
+ * TF32: operands rounded to TF32 on the tensor cores, FP32 accumulation.
+ * BF16X3: every operand split into three BF16 terms x = x0 + x1 + x2, the six products
+ * with i + j <= 2 accumulated in FP32 on the tensor cores.  The Davidson vector work
+ * (overlaps, Gram-Schmidt, Rayleigh quotient, residual, small eigenproblem) is always
+ * float64. */
+typedef enum { DMRG_PREC_FP64 = 0, DMRG_PREC_TF32 = 1, DMRG_PREC_BF16X3 = 2 } dmrg_precision;
+
+enum { DMRG_HOST_DATA = 0, DMRG_DEVICE_DATA = 1 };
+enum { DMRG_IDENTITY_OP = -1 };
+enum { DMRG_MAX_SUBSPACE = 24 };
+
+/* One dense block A_{q_in -> q_out} of an operator (Sec. 4.1, around Eq. 11). */
+typedef struct {
+  int32_t idx_in, idx_out;  /* sector indices on this side (left or right)        */
+  int64_t rows, cols, ld;   /* rows = dim(idx_out), cols = dim(idx_in), ld >= cols */
+  const double* data;       /* row-major; host or device per data_location        */
+} dmrg_block;
+
+typedef struct {
+  int32_t nblocks;
+  const dmrg_block* blocks; /* at most one block per (idx_in, idx_out)            */
+} dmrg_operator;
+
+/* coef * (A_{a_op} (x) B_{b_op}); an op index of DMRG_IDENTITY_OP is the identity. */
+typedef struct {
+  double coef;
+  int32_t a_op, b_op;
+} dmrg_term;
+
+typedef struct {
+  int32_t nL, nR;                 /* number of enlarged-left / enlarged-right sectors */
+  const int64_t* dimL;            /* host arrays of sector dimensions                 */
+  const int64_t* dimR;
+  int32_t npairs;                 /* valid (i, k) pairs of sector Q, storage order    */
+  const int32_t* pair_i;          /* host arrays of length npairs                     */
+  const int32_t* pair_k;
+  int32_t nopsL, nopsR;
+  const dmrg_operator* opsL;      /* host array of operators (blocks may be device)   */
+  const dmrg_operator* opsR;
+  int32_t nterms;
+  const dmrg_term* terms;         /* host array                                       */
+  int32_t data_location;          /* DMRG_HOST_DATA or DMRG_DEVICE_DATA               */
+} dmrg_superblock_desc;
+
+typedef struct {
+  dmrg_precision prec;   /* projection arithmetic inside Davidson (default FP64)          */
+  double tol;            /* stop when ||H x - lambda x||_2 <= tol, ||x|| = 1 (1e-10)      */
+  int32_t max_iter;      /* Davidson iterations before DMRG_ERR_NOT_CONVERGED (1000)      */
+  int32_t max_subspace;  /* basis size that triggers a restart, <= 24 (20, Sec. 6.1)     */
+  int32_t fp64_refine;   /* low-precision modes: re-anchor with FP64 projections (1)      */
+  double refine_ratio;   /* re-anchor when the low-precision residual has fallen by this
+                            factor below the last FP64 residual (1e-3)                   */
+} dmrg_options;
+
+typedef struct {
+  double energy;            /* lambda of the returned pair (FP64 Rayleigh quotient)       */
+  double resnorm;           /* ||H x - lambda x||_2 of the returned pair                  */
+  int32_t iters;            /* Davidson iterations                                        */
+  int32_t projections;      /* projections in the plan's precision                        */
+  int32_t fp64_projections; /* FP64 projections (all of them in FP64 mode)                */
+  int32_t restarts;         /* basis collapses (subspace limit or re-anchoring)           */
+} dmrg_solve_info;
+
+typedef struct {
+  int64_t n;                /* superblock dimension                                       */
+  int64_t records;          /* transition pairs of Eq. 11                                 */
+  int64_t flops;            /* algorithmic FLOPs of one projection (cheaper order, non-
+                               identity factors only)                                      */
+  int64_t tiles_stage1, tiles_stage2;
+  int64_t device_bytes;     /* device memory owned by the plan                            */
+} dmrg_plan_stats;
+
+typedef struct dmrg_plan dmrg_plan;
+typedef struct dmrg_davidson_state dmrg_davidson_state;
+
+/* Fills the defaults listed above. */
+void dmrg_options_default(dmrg_options* opt);
+
+/* Builds the operation records of Sec. 7 (Algorithm 5, line 1: records and their FLOP
+ * workload) and uploads the operator blocks to a device arena owned by the plan; also
+ * computes diag(H_SB) for the Davidson correction.  desc and its arrays are read during
+ * the call only.  opt may be NULL (defaults).  On success *out owns device memory until
+ * dmrg_plan_destroy. */
+dmrg_status dmrg_plan_create(const dmrg_superblock_desc* desc, const dmrg_options* opt,
+                             void* stream, dmrg_plan** out);
+void dmrg_plan_destroy(dmrg_plan* plan);
+dmrg_status dmrg_plan_get_stats(const dmrg_plan* plan, dmrg_plan_stats* stats);
+
+/* y = H_SB x (Eq. 11 summed over all records), in the given precision.  x and y are
+ * device arrays of n float64 and must not overlap.  Enqueued on stream. */
+dmrg_status dmrg_project(dmrg_plan* plan, const double* x, double* y, void* stream);
+dmrg_status dmrg_project_prec(dmrg_plan* plan, dmrg_precision prec, const double* x,
+                              double* y, void* stream);
+
+/* d = diag(H_SB) (device array of n float64), the Davidson preconditioner input. */
+dmrg_status dmrg_diagonal(dmrg_plan* plan, double* d, void* stream);
+
+/* s[j] = sum_e V[j * ldv + e] * w[e] for j < k: the "asymmetric" matrix-vector product
+ * V^T w of Sec. 6.1 (Algorithm 3 lines 3 and 11) on a tall-skinny column-major V of n
+ * rows and k <= 24 columns.  V, w, s are device pointers; ldv >= n.  Enqueued. */
+dmrg_status dmrg_gemv_trans(const double* V, int64_t ldv, int64_t n, int32_t k,
+                            const double* w, double* s, void* stream);
+
+/* Davidson state: basis V, projections W, the small matrix B of Algorithm 3, started
+ * from x0 (device, n float64, normalised by the call). */
+dmrg_status dmrg_state_create(dmrg_plan* plan, const double* x0, void* stream,
+                              dmrg_davidson_state** out);
+void dmrg_state_destroy(dmrg_davidson_state* st);
+/* One iteration of Algorithm 3.  Synchronises the stream; *converged is set to 1 when
+ * the residual of the current Ritz pair is below tol. */
+dmrg_status dmrg_davidson_step(dmrg_davidson_state* st, void* stream, int32_t* converged);
+dmrg_status dmrg_state_get_info(const dmrg_davidson_state* st, dmrg_solve_info* info);
+/* x_out = current Ritz vector V y (device, n float64).  Enqueued. */
+dmrg_status dmrg_state_ritz(dmrg_davidson_state* st, double* x_out, void* stream);
+
+/* Full Davidson solve from x0 (device) into x_out (device); info may be NULL.  Returns
+ * DMRG_ERR_NOT_CONVERGED with x_out and info filled when max_iter is reached. */
+dmrg_status dmrg_davidson_solve(dmrg_plan* plan, const double* x0, double* x_out,
+                                dmrg_solve_info* info, void* stream);
+/* Same, with x0 and x_out in host memory: the host-to-device copy of x0 and the
+ * device-to-host copy of x_out are part of the call. */
+dmrg_status dmrg_davidson_solve_host(dmrg_plan* plan, const double* x0_host,
+                                     double* x_out_host, dmrg_solve_info* info,
+                                     void* stream);
+
+/* 1 if projections in this precision are available in this build, else 0. */
+int32_t dmrg_precision_available(dmrg_precision prec);
+
+/* Number of kernels this library has launched in this process (all devices). */
+int64_t dmrg_kernel_launches(void);
+
+const char* dmrg_status_string(dmrg_status s);
+const char* dmrg_last_error(void);
+/* Library version string. */
+const char* dmrg_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DMRG_GB300_H */

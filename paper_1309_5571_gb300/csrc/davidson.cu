@@ -1,0 +1,338 @@
+// The Davidson iteration of Algorithm 3 on the GPU, driven by a thin host loop.
+//
+// Per iteration (k basis columns, the newest one not yet projected):
+//   projection     W(:,k-1) = H V(:,k-1)                     (line 2; plan precision)
+//   overlap        B(:,k-1) = V^T W(:,k-1), mirrored into row k-1  (line 3)
+//   jacobi         (lambda, y) = lowest eigenpair of B            (line 4)
+//   residual       r = W y - lambda V y, ||r||, t = r/(lambda - D), V^T t   (lines 5-6, 9)
+//   [host]         read ||r||, lambda; decide convergence / restart (line 7)
+//   cgs x2         t -= V (V^T t), twice                         (lines 11-12)
+//   finish         t /= ||t||, append                            (line 13)
+// Readings where the paper is silent are the ones of the FP64 oracle: diagonal
+// correction with a 1e-8 denominator guard, classical Gram-Schmidt applied twice with a
+// fall-back to the raw residual on breakdown, restart to the Ritz vector when the basis
+// holds max_subspace columns (20 in Sec. 6.1), stop on ||r||_2 <= tol.
+//
+// Low-precision projections (TF32, BF16X3) carry an error of order eps * ||H||, which
+// bounds how small the computed residual can get.  The mixed mode therefore anchors the
+// iteration with float64 projections: whenever the basis is collapsed (subspace limit,
+// or the low-precision residual fell below refine_ratio times the last exact residual,
+// or below tol), the new single basis vector x is projected in FP64, so lambda = x^T H x
+// is an FP64 Rayleigh quotient and the residual W(:,0) - lambda x is exact.  Only such an
+// exact residual can end the iteration.  Later low-precision columns then only carry
+// the error of the correction x - x_anchor, which shrinks as the iteration converges.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+
+#include "internal.h"
+
+using namespace dmrg;
+
+struct dmrg_davidson_state {
+  dmrg_plan* plan = nullptr;
+  int64_t n = 0, ldv = 0;
+  int kmax = 20;
+  double* V = nullptr;     // (kmax + 1) columns
+  double* W = nullptr;     // kmax columns
+  double* D = nullptr;     // padded diag(H_SB)
+  double* xbuf = nullptr;  // Ritz vector at a restart
+  double* wbuf = nullptr;  // W y at a restart
+  DevSmall* small = nullptr;
+  DevSmall* hsmall = nullptr;  // pinned mirror
+  VecWork vw;
+  int k = 1;
+  int iters = 0, projections = 0, fp64_projections = 0, restarts = 0;
+  double lambda = NAN, rnorm = INFINITY;
+  bool converged = false;
+  bool mixed = false;
+  bool anchor_pending = false;
+  double anchor_rnorm = INFINITY;
+  int ritz_k = 1;  // columns that small->y refers to; 0: V(:,0) holds the Ritz vector
+};
+
+namespace {
+
+dmrg_status read_small(dmrg_davidson_state* s, cudaStream_t st) {
+  DMRG_CUDA_TRY(cudaMemcpyAsync(s->hsmall, s->small, sizeof(DevSmall), cudaMemcpyDeviceToHost, st));
+  DMRG_CUDA_TRY(cudaStreamSynchronize(st));
+  return DMRG_OK;
+}
+
+dmrg_status project_col(dmrg_davidson_state* s, int col, bool fp64, cudaStream_t st) {
+  dmrg_precision prec = fp64 ? DMRG_PREC_FP64 : s->plan->opt.prec;
+  DMRG_TRY(dmrg_project_prec(s->plan, prec, s->V + col * s->ldv, s->W + col * s->ldv, st));
+  if (prec == DMRG_PREC_FP64) s->fp64_projections++;
+  else s->projections++;
+  return DMRG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+dmrg_status dmrg_state_create(dmrg_plan* plan, const double* x0, void* stream,
+                              dmrg_davidson_state** out) {
+  if (!plan || !out || (!x0 && plan->n)) {
+    set_error("NULL argument");
+    return DMRG_ERR_INVALID_ARG;
+  }
+  *out = nullptr;
+  if (plan->n == 0) {
+    set_error("empty superblock (n = 0)");
+    return DMRG_ERR_SHAPE;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  auto* s = new (std::nothrow) dmrg_davidson_state();
+  if (!s) {
+    set_error("host allocation failed");
+    return DMRG_ERR_OOM;
+  }
+  s->plan = plan;
+  s->n = plan->n;
+  s->ldv = round_up(plan->n, 32);
+  s->kmax = plan->opt.max_subspace;
+  s->mixed = plan->opt.prec != DMRG_PREC_FP64 && plan->opt.fp64_refine;
+  auto fail = [&](dmrg_status e) { dmrg_state_destroy(s); return e; };
+  const size_t col = sizeof(double) * (size_t)s->ldv;
+  if (cudaMalloc((void**)&s->V, col * (s->kmax + 1)) != cudaSuccess ||
+      cudaMalloc((void**)&s->W, col * s->kmax) != cudaSuccess ||
+      cudaMalloc((void**)&s->D, col) != cudaSuccess ||
+      cudaMalloc((void**)&s->xbuf, col) != cudaSuccess ||
+      cudaMalloc((void**)&s->wbuf, col) != cudaSuccess ||
+      cudaMalloc((void**)&s->small, sizeof(DevSmall)) != cudaSuccess ||
+      cudaMallocHost((void**)&s->hsmall, sizeof(DevSmall)) != cudaSuccess) {
+    cudaGetLastError();
+    set_error("allocation of the Davidson workspace (%zu bytes) failed",
+              col * (2 * s->kmax + 4));
+    return fail(DMRG_ERR_OOM);
+  }
+  dmrg_status e = vec_work_create(&s->vw);
+  if (e != DMRG_OK) return fail(e);
+  if (cudaMemsetAsync(s->V, 0, col * (s->kmax + 1), st) != cudaSuccess ||
+      cudaMemsetAsync(s->W, 0, col * s->kmax, st) != cudaSuccess ||
+      cudaMemsetAsync(s->D, 0, col, st) != cudaSuccess ||
+      cudaMemsetAsync(s->xbuf, 0, col, st) != cudaSuccess ||
+      cudaMemsetAsync(s->wbuf, 0, col, st) != cudaSuccess ||
+      cudaMemsetAsync(s->small, 0, sizeof(DevSmall), st) != cudaSuccess ||
+      cudaMemcpyAsync(s->D, plan->D, sizeof(double) * s->n, cudaMemcpyDeviceToDevice, st) !=
+          cudaSuccess) {
+    set_error("workspace initialisation failed");
+    return fail(DMRG_ERR_CUDA);
+  }
+  if ((e = launch_normalize(s->vw, x0, s->V, s->n, s->small, st)) != DMRG_OK) return fail(e);
+  if ((e = read_small(s, st)) != DMRG_OK) return fail(e);
+  if (!(s->hsmall->nrm2 > 0.0) || !std::isfinite(s->hsmall->nrm2)) {
+    set_error("start vector has zero or non-finite norm");
+    return fail(DMRG_ERR_INVALID_ARG);
+  }
+  s->k = 1;
+  *out = s;
+  return DMRG_OK;
+}
+
+void dmrg_state_destroy(dmrg_davidson_state* s) {
+  if (!s) return;
+  cudaFree(s->V);
+  cudaFree(s->W);
+  cudaFree(s->D);
+  cudaFree(s->xbuf);
+  cudaFree(s->wbuf);
+  cudaFree(s->small);
+  cudaFreeHost(s->hsmall);
+  vec_work_destroy(&s->vw);
+  delete s;
+}
+
+dmrg_status dmrg_davidson_step(dmrg_davidson_state* s, void* stream, int32_t* converged) {
+  if (!s) {
+    set_error("NULL state");
+    return DMRG_ERR_INVALID_ARG;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  if (converged) *converged = s->converged ? 1 : 0;
+  if (s->converged) return DMRG_OK;
+  const int64_t ldv = s->ldv, n = s->n;
+  const int k = s->k, col = k - 1;
+  const bool anchor = s->mixed && s->anchor_pending;
+  const bool fp64 = !s->mixed && s->plan->opt.prec == DMRG_PREC_FP64;
+  DMRG_TRY(project_col(s, col, fp64 || anchor, st));
+  s->anchor_pending = false;
+  DMRG_TRY(launch_overlap(s->vw, s->V, ldv, n, k, s->W + col * ldv, nullptr, s->small, col, st));
+  DMRG_TRY(launch_jacobi(s->small, k, st));
+  double* tcol = s->V + (int64_t)k * ldv;
+  DMRG_TRY(launch_residual(s->vw, s->V, s->W, s->D, ldv, n, k, tcol, s->small, 0, st));
+  DMRG_TRY(read_small(s, st));
+  s->iters++;
+  s->lambda = s->hsmall->lambda;
+  s->rnorm = std::sqrt(std::max(0.0, s->hsmall->rnorm2));
+  if (s->hsmall->flags & 2 || !std::isfinite(s->lambda)) {
+    set_error("non-finite residual or eigenvalue at iteration %d", s->iters);
+    return DMRG_ERR_NUMERIC;
+  }
+  const double tol = s->plan->opt.tol;
+  const bool exact = !s->mixed || anchor;  // residual computed from FP64 projections only
+  const bool lowprec_plain = !fp64 && !s->mixed;
+  if (s->mixed && k == 1) s->anchor_rnorm = s->rnorm;
+  s->ritz_k = k;
+  if (s->rnorm <= tol && (exact || lowprec_plain)) {
+    s->converged = true;
+    if (converged) *converged = 1;
+    return DMRG_OK;
+  }
+  bool do_anchor = false, do_restart = false;
+  if (s->mixed &&
+      (s->rnorm <= tol || (k > 1 && s->rnorm <= s->plan->opt.refine_ratio * s->anchor_rnorm)))
+    do_anchor = true;
+  if (k == s->kmax) {
+    if (s->mixed) do_anchor = true;
+    else do_restart = true;
+  }
+  if (do_anchor) {
+    // collapse to the normalised Ritz vector; its projection is redone in FP64
+    DMRG_TRY(launch_ritz(s->V, s->W, ldv, n, k, s->small, s->xbuf, nullptr, st));
+    DMRG_TRY(launch_normalize(s->vw, s->xbuf, s->V, n, s->small, st));
+    s->k = 1;
+    s->restarts++;
+    s->anchor_pending = true;
+    s->ritz_k = 0;
+    return DMRG_OK;
+  }
+  int knew = k;
+  if (do_restart) {
+    // V = [x], W = [W y], B = [lambda]; the correction t (column k) is kept
+    DMRG_TRY(launch_ritz(s->V, s->W, ldv, n, k, s->small, s->xbuf, s->wbuf, st));
+    DMRG_CUDA_TRY(cudaMemcpyAsync(s->V, s->xbuf, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+    DMRG_CUDA_TRY(cudaMemcpyAsync(s->W, s->wbuf, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+    DMRG_TRY(launch_set_B00(s->small, st));
+    knew = 1;
+    s->restarts++;
+    s->ritz_k = 0;
+    DMRG_TRY(launch_overlap(s->vw, s->V, ldv, n, knew, tcol, s->small->s[0], s->small, -1, st));
+  }
+  // classical Gram-Schmidt, twice, then normalise
+  for (int attempt = 0; attempt < 2; ++attempt) {
+    DMRG_CUDA_TRY(cudaMemsetAsync(&s->small->flags, 0, sizeof(int32_t), st));
+    DMRG_TRY(launch_cgs(s->vw, s->V, ldv, n, knew, tcol, s->small, 0, 1, st));
+    DMRG_TRY(launch_cgs(s->vw, s->V, ldv, n, knew, tcol, s->small, 1, 2, st));
+    DMRG_TRY(launch_finish(tcol, n, s->small, st));
+    DMRG_TRY(read_small(s, st));
+    if (!(s->hsmall->flags & 1)) break;
+    if (attempt == 1) {
+      set_error("Davidson basis breakdown at iteration %d (||r|| = %g)", s->iters, s->rnorm);
+      return DMRG_ERR_NUMERIC;
+    }
+    // fall back to the raw residual r (mode 1 writes t = r) and orthogonalise again;
+    // after a restart the basis is [x] with W = [W y], so r = W(:,0) - lambda V(:,0)
+    if (do_restart) {
+      static const double e1[KMAX] = {1.0};
+      DMRG_CUDA_TRY(cudaMemcpyAsync(s->small->y, e1, sizeof(e1), cudaMemcpyHostToDevice, st));
+    }
+    DMRG_TRY(launch_residual(s->vw, s->V, s->W, s->D, ldv, n, knew, tcol, s->small, 1, st));
+  }
+  if (knew != k) {
+    DMRG_CUDA_TRY(cudaMemcpyAsync(s->V + (int64_t)knew * ldv, tcol, sizeof(double) * ldv,
+                                  cudaMemcpyDeviceToDevice, st));
+  }
+  s->k = knew + 1;
+  return DMRG_OK;
+}
+
+dmrg_status dmrg_state_get_info(const dmrg_davidson_state* s, dmrg_solve_info* info) {
+  if (!s || !info) {
+    set_error("NULL argument");
+    return DMRG_ERR_INVALID_ARG;
+  }
+  info->energy = s->lambda;
+  info->resnorm = s->rnorm;
+  info->iters = s->iters;
+  info->projections = s->projections;
+  info->fp64_projections = s->fp64_projections;
+  info->restarts = s->restarts;
+  return DMRG_OK;
+}
+
+dmrg_status dmrg_state_ritz(dmrg_davidson_state* s, double* x_out, void* stream) {
+  if (!s || !x_out) {
+    set_error("NULL argument");
+    return DMRG_ERR_INVALID_ARG;
+  }
+  if (s->ritz_k == 0) {  // the basis was collapsed onto the Ritz vector
+    DMRG_CUDA_TRY(cudaMemcpyAsync(x_out, s->V, sizeof(double) * s->n, cudaMemcpyDeviceToDevice,
+                                  (cudaStream_t)stream));
+    return DMRG_OK;
+  }
+  return launch_ritz(s->V, s->W, s->ldv, s->n, s->ritz_k, s->small, x_out, nullptr,
+                     (cudaStream_t)stream);
+}
+
+dmrg_status dmrg_davidson_solve(dmrg_plan* plan, const double* x0, double* x_out,
+                                dmrg_solve_info* info, void* stream) {
+  if (!plan || !x0 || !x_out) {
+    set_error("NULL argument");
+    return DMRG_ERR_INVALID_ARG;
+  }
+  dmrg_davidson_state* s = nullptr;
+  DMRG_TRY(dmrg_state_create(plan, x0, stream, &s));
+  dmrg_status e = DMRG_OK;
+  int32_t conv = 0;
+  while (!conv && s->iters < plan->opt.max_iter) {
+    e = dmrg_davidson_step(s, stream, &conv);
+    if (e != DMRG_OK) break;
+  }
+  if (e == DMRG_OK) e = dmrg_state_ritz(s, x_out, stream);
+  if (info) dmrg_state_get_info(s, info);
+  if (e == DMRG_OK && cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) {
+    set_error("solve: %s", cudaGetErrorString(cudaGetLastError()));
+    e = DMRG_ERR_CUDA;
+  }
+  if (e == DMRG_OK && !conv) {
+    set_error("Davidson did not converge in %d iterations (||r|| = %g)", s->iters, s->rnorm);
+    e = DMRG_ERR_NOT_CONVERGED;
+  }
+  dmrg_state_destroy(s);
+  return e;
+}
+
+dmrg_status dmrg_davidson_solve_host(dmrg_plan* plan, const double* x0_host,
+                                     double* x_out_host, dmrg_solve_info* info, void* stream) {
+  if (!plan || !x0_host || !x_out_host) {
+    set_error("NULL argument");
+    return DMRG_ERR_INVALID_ARG;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  double *dx0 = nullptr, *dx = nullptr;
+  const size_t bytes = sizeof(double) * (size_t)plan->n;
+  if (cudaMalloc((void**)&dx0, bytes) != cudaSuccess || cudaMalloc((void**)&dx, bytes) != cudaSuccess) {
+    cudaFree(dx0);
+    set_error("allocation of the solve vectors failed");
+    return DMRG_ERR_OOM;
+  }
+  dmrg_status e = DMRG_OK;
+  if (cudaMemcpyAsync(dx0, x0_host, bytes, cudaMemcpyHostToDevice, st) != cudaSuccess) {
+    set_error("host-to-device copy of x0 failed");
+    e = DMRG_ERR_CUDA;
+  }
+  if (e == DMRG_OK) e = dmrg_davidson_solve(plan, dx0, dx, info, stream);
+  if (e == DMRG_OK || e == DMRG_ERR_NOT_CONVERGED) {
+    if (cudaMemcpyAsync(x_out_host, dx, bytes, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess) {
+      set_error("device-to-host copy of x failed");
+      e = DMRG_ERR_CUDA;
+    }
+  }
+  cudaFree(dx0);
+  cudaFree(dx);
+  return e;
+}
+
+dmrg_status dmrg_gemv_trans(const double* V, int64_t ldv, int64_t n, int32_t k,
+                            const double* w, double* s, void* stream) {
+  if ((n > 0 && (!V || !w)) || !s || n < 0 || k < 1 || k > DMRG_MAX_SUBSPACE || ldv < n) {
+    set_error("dmrg_gemv_trans: bad argument (k must be in [1, %d], ldv >= n)", DMRG_MAX_SUBSPACE);
+    return DMRG_ERR_INVALID_ARG;
+  }
+  return launch_gemv_trans_public(V, ldv, n, k, w, s, (cudaStream_t)stream);
+}
+
+}  // extern "C"

@@ -1,0 +1,206 @@
+// Internal declarations shared by the translation units of the library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "dmrg.h"
+
+namespace dmrg {
+
+// ---------------------------------------------------------------- errors
+void set_error(const char* fmt, ...);
+
+#define DMRG_CUDA_TRY(expr)                                                          \
+  do {                                                                               \
+    cudaError_t e_ = (expr);                                                         \
+    if (e_ != cudaSuccess) {                                                         \
+      ::dmrg::set_error("%s: %s (%s:%d)", #expr, cudaGetErrorString(e_), __FILE__,   \
+                        __LINE__);                                                   \
+      return DMRG_ERR_CUDA;                                                          \
+    }                                                                                \
+  } while (0)
+
+#define DMRG_TRY(expr)                \
+  do {                                \
+    dmrg_status s_ = (expr);          \
+    if (s_ != DMRG_OK) return s_;     \
+  } while (0)
+
+// Kernel launches are counted and checked with cudaGetLastError right after the launch.
+void note_launch();
+#define DMRG_LAUNCH_CHECK()                  \
+  do {                                       \
+    ::dmrg::note_launch();                   \
+    DMRG_CUDA_TRY(cudaGetLastError());       \
+  } while (0)
+
+// ---------------------------------------------------------------- operand addressing
+// Operands of the FP64 projection GEMMs are addressed relative to one of four base
+// pointers that change from call to call: the operator arena owned by the plan, the
+// input vector X, the stage-1 intermediates T and the output vector Y.
+enum Space : int32_t { SP_ARENA = 0, SP_X = 1, SP_T = 2, SP_Y = 3 };
+
+struct Bases {
+  const double* p[4];
+};
+
+// Element (r, c) of an operand sits at base[space] + off + r * rs + c * cs.
+struct Operand {
+  int64_t off;
+  int64_t rs, cs;
+  int32_t space;
+  int32_t pad_;
+};
+
+// One K-segment of a job: C += alpha * P[M x K] * Q[K x N].
+struct Seg64 {
+  Operand P, Q;
+  int32_t K;
+  int32_t pad_;
+  double alpha;
+};
+
+// One output matrix C[M x N] (row stride ldc) written as the sum of its segments plus
+// axpy * X(axpy operand) (the term whose two factors are identities).
+struct Job64 {
+  Operand C;
+  Operand Xaxpy;
+  double axpy;
+  int32_t M, N;
+  int32_t seg_begin, seg_end;
+};
+
+struct Tile64 {
+  int32_t job;
+  int32_t m0, n0;
+  int32_t pad_;
+};
+
+constexpr int kTileM = 64;
+constexpr int kTileN = 64;
+constexpr int kTileK = 16;
+
+// ---------------------------------------------------------------- plan
+struct Record {
+  int32_t term;
+  int32_t a_blk, b_blk;  // index into the block table of each side, -1 = identity
+  int32_t pin, pout;     // input / output pair index
+  int32_t i, j, k, l;    // sectors
+  int64_t di, dj, dk, dl;
+  double coef;
+  int32_t a_first;       // 1: T = A X then T B^T; 0: U = X B^T then A U
+  int64_t inter_off;     // offset of T or U in the intermediate buffer
+};
+
+struct HostBlock {
+  int32_t idx_in, idx_out;
+  int64_t rows, cols;
+  int64_t arena_off;     // row-major, ld = cols
+};
+
+struct TcPlan;           // tensor-core (low precision) part, see gemm_tc.cu
+
+}  // namespace dmrg
+
+struct dmrg_plan {
+  int device = 0;
+  dmrg_options opt{};
+  int64_t n = 0;
+  std::vector<int64_t> dimL, dimR;
+  std::vector<int32_t> pair_i, pair_k;
+  std::vector<int64_t> pair_off;  // npairs + 1
+  std::vector<std::vector<dmrg::HostBlock>> opsL, opsR;
+  std::vector<dmrg_term> terms;
+  std::vector<dmrg::Record> records;
+  int64_t flops = 0;
+
+  double* arena = nullptr;        // operator blocks
+  size_t arena_elems = 0;
+  std::vector<double> arena_host; // staging copy (freed after upload)
+  double* T = nullptr;            // stage-1 intermediates
+  size_t T_elems = 0;
+  double* D = nullptr;            // diag(H_SB)
+
+  dmrg::Job64* d_jobs = nullptr;
+  dmrg::Seg64* d_segs = nullptr;
+  dmrg::Tile64* d_tiles1 = nullptr;
+  dmrg::Tile64* d_tiles2 = nullptr;
+  int64_t ntiles1 = 0, ntiles2 = 0;
+  size_t device_bytes = 0;
+
+  dmrg::TcPlan* tc = nullptr;     // built on first low-precision use
+};
+
+namespace dmrg {
+// gemm_fp64.cu
+dmrg_status launch_project_fp64(dmrg_plan* plan, const double* x, double* y,
+                                cudaStream_t stream);
+// gemm_tc.cu
+dmrg_status launch_project_tc(dmrg_plan* plan, dmrg_precision prec, const double* x,
+                              double* y, cudaStream_t stream);
+void destroy_tc(dmrg_plan* plan);
+bool tc_available(dmrg_precision prec);
+
+// vec.cu -- Davidson vector kernels
+constexpr int KMAX = DMRG_MAX_SUBSPACE;
+constexpr int kVecThreads = 256;
+
+struct DevSmall {
+  double B[KMAX * KMAX];  // projected matrix, row-major
+  double y[KMAX];         // lowest eigenvector of B
+  double s[3][KMAX];      // Gram-Schmidt coefficients
+  double lambda;
+  double rnorm2;          // ||r||^2 of the current Ritz pair
+  double tnorm2_before;   // ||t||^2 before orthogonalisation
+  double tnorm2;          // ||t||^2 after the latest Gram-Schmidt pass
+  double nrm2;            // generic norm result
+  int32_t flags;          // bit 0: breakdown, bit 1: non-finite
+  int32_t jacobi_sweeps;
+};
+
+struct VecWork {
+  double* partials = nullptr;   // [grid x slots]
+  unsigned int* counter = nullptr;
+  int grid = 0;
+};
+
+dmrg_status vec_work_create(VecWork* w);
+void vec_work_destroy(VecWork* w);
+
+// s_out[j] = V_j . w for j < k (V column-major, ldv); if Bcol >= 0 also fills row and
+// column Bcol of small->B.
+dmrg_status launch_overlap(const VecWork& w, const double* V, int64_t ldv, int64_t n,
+                           int k, const double* vec, double* s_out, DevSmall* small,
+                           int Bcol, cudaStream_t st);
+dmrg_status launch_jacobi(DevSmall* small, int k, cudaStream_t st);
+// r = W y - lambda V y, t = r / (lambda - D) (mode 0) or t = r (mode 1) into tcol;
+// reductions: rnorm2, s[0] = V^T t, tnorm2_before.
+dmrg_status launch_residual(const VecWork& w, const double* V, const double* W,
+                            const double* D, int64_t ldv, int64_t n, int k, double* tcol,
+                            DevSmall* small, int mode, cudaStream_t st);
+// t -= V s[sin]; s[sout] = V^T t; tnorm2 = ||t||^2
+dmrg_status launch_cgs(const VecWork& w, const double* V, int64_t ldv, int64_t n, int k,
+                       double* tcol, DevSmall* small, int sin, int sout, cudaStream_t st);
+// flags breakdown (tnorm2 < 1e-20 tnorm2_before) else t /= ||t||
+dmrg_status launch_finish(double* tcol, int64_t n, DevSmall* small, cudaStream_t st);
+// x = V y, optionally wy = W y (n elements, written unpadded)
+dmrg_status launch_ritz(const double* V, const double* W, int64_t ldv, int64_t n, int k,
+                        const DevSmall* small, double* x_out, double* wy_out,
+                        cudaStream_t st);
+// nrm2 = ||src||^2 then dst = src / ||src|| (dst padded to ldv with zeros by caller)
+dmrg_status launch_normalize(const VecWork& w, const double* src, double* dst, int64_t n,
+                             DevSmall* small, cudaStream_t st);
+dmrg_status launch_set_B00(DevSmall* small, cudaStream_t st);
+dmrg_status launch_gemv_trans_public(const double* V, int64_t ldv, int64_t n, int k,
+                                     const double* w, double* s, cudaStream_t st);
+
+// plan.cu
+dmrg_status compute_diagonal(dmrg_plan* plan, double* d, cudaStream_t st);
+
+inline int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
+
+}  // namespace dmrg

@@ -1,0 +1,543 @@
+// Plan creation: operation records of Sec. 7 and the FP64 GEMM work lists.
+//
+// Sec. 7 observes that the operator blocks A and B are fixed during the Davidson
+// iterations, so everything that depends only on them is prepared once: the list of
+// operation records (one per transition pair of Eq. 11, each with its input segment,
+// output segment, blocks and FLOP workload -- Algorithm 5, line 1), the choice of the
+// cheaper multiplication order per record, the device copies of the blocks and the
+// diagonal of H_SB used by the Davidson correction.  The paper's CPU/GPU partitioning
+// and stream scheduling (Algorithms 5-7) have no counterpart: all records run on the
+// GPU in two launches (stage 1: intermediates, stage 2: output GEMMs whose K dimension
+// concatenates every record that writes the same output segment).
+#include <algorithm>
+#include <cstring>
+#include <map>
+
+#include "internal.h"
+
+using namespace dmrg;
+
+namespace {
+
+dmrg_status validate_and_copy(const dmrg_superblock_desc* d, dmrg_plan* p) {
+  if (!d) {
+    set_error("desc is NULL");
+    return DMRG_ERR_INVALID_ARG;
+  }
+  if (d->nL <= 0 || d->nR <= 0 || d->npairs < 0 || d->nterms < 0 || d->nopsL < 0 ||
+      d->nopsR < 0) {
+    set_error("negative or zero sector/pair/term counts");
+    return DMRG_ERR_INVALID_ARG;
+  }
+  if (!d->dimL || !d->dimR || (d->npairs && (!d->pair_i || !d->pair_k)) ||
+      (d->nterms && !d->terms) || (d->nopsL && !d->opsL) || (d->nopsR && !d->opsR)) {
+    set_error("NULL array in desc");
+    return DMRG_ERR_INVALID_ARG;
+  }
+  if (d->data_location != DMRG_HOST_DATA && d->data_location != DMRG_DEVICE_DATA) {
+    set_error("data_location must be DMRG_HOST_DATA or DMRG_DEVICE_DATA");
+    return DMRG_ERR_INVALID_ARG;
+  }
+  p->dimL.assign(d->dimL, d->dimL + d->nL);
+  p->dimR.assign(d->dimR, d->dimR + d->nR);
+  for (auto v : p->dimL)
+    if (v < 0) { set_error("negative left sector dimension"); return DMRG_ERR_INVALID_ARG; }
+  for (auto v : p->dimR)
+    if (v < 0) { set_error("negative right sector dimension"); return DMRG_ERR_INVALID_ARG; }
+  p->pair_i.assign(d->pair_i, d->pair_i + d->npairs);
+  p->pair_k.assign(d->pair_k, d->pair_k + d->npairs);
+  p->pair_off.assign(d->npairs + 1, 0);
+  std::map<std::pair<int, int>, int> seen;
+  for (int q = 0; q < d->npairs; ++q) {
+    int i = p->pair_i[q], k = p->pair_k[q];
+    if (i < 0 || i >= d->nL || k < 0 || k >= d->nR) {
+      set_error("pair %d = (%d,%d) out of range", q, i, k);
+      return DMRG_ERR_INVALID_ARG;
+    }
+    if (!seen.emplace(std::make_pair(i, k), q).second) {
+      set_error("pair (%d,%d) listed twice", i, k);
+      return DMRG_ERR_SHAPE;
+    }
+    p->pair_off[q + 1] = p->pair_off[q] + p->dimL[i] * p->dimR[k];
+  }
+  p->n = p->pair_off[d->npairs];
+  p->terms.assign(d->terms, d->terms + d->nterms);
+  for (auto& t : p->terms) {
+    if ((t.a_op != DMRG_IDENTITY_OP && (t.a_op < 0 || t.a_op >= d->nopsL)) ||
+        (t.b_op != DMRG_IDENTITY_OP && (t.b_op < 0 || t.b_op >= d->nopsR))) {
+      set_error("term names a missing operator");
+      return DMRG_ERR_INVALID_ARG;
+    }
+  }
+  // stage all blocks into one host arena (row-major, ld = cols)
+  size_t total = 0;
+  for (int side = 0; side < 2; ++side) {
+    int nops = side ? d->nopsR : d->nopsL;
+    const dmrg_operator* ops = side ? d->opsR : d->opsL;
+    const std::vector<int64_t>& dim = side ? p->dimR : p->dimL;
+    int nsec = side ? d->nR : d->nL;
+    auto& dst = side ? p->opsR : p->opsL;
+    dst.assign(nops, {});
+    for (int o = 0; o < nops; ++o) {
+      if (ops[o].nblocks < 0 || (ops[o].nblocks && !ops[o].blocks)) {
+        set_error("operator %d has a bad block list", o);
+        return DMRG_ERR_INVALID_ARG;
+      }
+      std::map<std::pair<int, int>, int> keys;
+      for (int b = 0; b < ops[o].nblocks; ++b) {
+        const dmrg_block& blk = ops[o].blocks[b];
+        if (blk.idx_in < 0 || blk.idx_in >= nsec || blk.idx_out < 0 || blk.idx_out >= nsec) {
+          set_error("operator %d block %d: sector index out of range", o, b);
+          return DMRG_ERR_INVALID_ARG;
+        }
+        if (blk.rows != dim[blk.idx_out] || blk.cols != dim[blk.idx_in] || blk.ld < blk.cols ||
+            (blk.rows * blk.cols > 0 && !blk.data)) {
+          set_error("operator %d block %d (%d->%d): shape %lldx%lld (ld %lld) does not match "
+                    "sectors %lldx%lld",
+                    o, b, blk.idx_in, blk.idx_out, (long long)blk.rows, (long long)blk.cols,
+                    (long long)blk.ld, (long long)dim[blk.idx_out], (long long)dim[blk.idx_in]);
+          return DMRG_ERR_SHAPE;
+        }
+        if (!keys.emplace(std::make_pair(blk.idx_in, blk.idx_out), b).second) {
+          set_error("operator %d has two blocks %d->%d", o, blk.idx_in, blk.idx_out);
+          return DMRG_ERR_SHAPE;
+        }
+        HostBlock hb{blk.idx_in, blk.idx_out, blk.rows, blk.cols, (int64_t)total};
+        dst[o].push_back(hb);
+        total += (size_t)round_up(blk.rows * blk.cols, 32);  // 256-byte aligned blocks
+      }
+    }
+  }
+  p->arena_elems = total;
+  p->arena_host.assign(total, 0.0);
+  for (int side = 0; side < 2; ++side) {
+    int nops = side ? d->nopsR : d->nopsL;
+    const dmrg_operator* ops = side ? d->opsR : d->opsL;
+    auto& dst = side ? p->opsR : p->opsL;
+    for (int o = 0; o < nops; ++o) {
+      for (int b = 0; b < ops[o].nblocks; ++b) {
+        const dmrg_block& blk = ops[o].blocks[b];
+        double* out = p->arena_host.data() + dst[o][b].arena_off;
+        if (blk.rows * blk.cols == 0) continue;
+        if (d->data_location == DMRG_HOST_DATA) {
+          for (int64_t r = 0; r < blk.rows; ++r)
+            std::memcpy(out + r * blk.cols, blk.data + r * blk.ld, sizeof(double) * blk.cols);
+        } else {
+          DMRG_CUDA_TRY(cudaMemcpy2D(out, sizeof(double) * blk.cols, blk.data,
+                                     sizeof(double) * blk.ld, sizeof(double) * blk.cols,
+                                     blk.rows, cudaMemcpyDeviceToHost));
+        }
+      }
+    }
+  }
+  return DMRG_OK;
+}
+
+struct Builder {
+  std::vector<Job64> jobs;
+  std::vector<Seg64> segs;
+  std::vector<Tile64> tiles1, tiles2;
+};
+
+Operand opnd(int space, int64_t off, int64_t rs, int64_t cs) {
+  Operand o;
+  o.off = off;
+  o.rs = rs;
+  o.cs = cs;
+  o.space = space;
+  o.pad_ = 0;
+  return o;
+}
+
+void add_tiles(std::vector<Tile64>& tiles, int job, int64_t M, int64_t N) {
+  for (int64_t m0 = 0; m0 < std::max<int64_t>(M, 1); m0 += kTileM)
+    for (int64_t n0 = 0; n0 < std::max<int64_t>(N, 1); n0 += kTileN)
+      tiles.push_back(Tile64{job, (int32_t)m0, (int32_t)n0, 0});
+}
+
+dmrg_status build_records_and_jobs(dmrg_plan* p, Builder* bld) {
+  const int npairs = (int)p->pair_i.size();
+  std::map<std::pair<int, int>, int> pidx;
+  for (int q = 0; q < npairs; ++q) pidx[{p->pair_i[q], p->pair_k[q]}] = q;
+  const int nL = (int)p->dimL.size(), nR = (int)p->dimR.size();
+  std::vector<HostBlock> idL(nL), idR(nR);
+  for (int i = 0; i < nL; ++i) idL[i] = HostBlock{i, i, p->dimL[i], p->dimL[i], -1};
+  for (int k = 0; k < nR; ++k) idR[k] = HostBlock{k, k, p->dimR[k], p->dimR[k], -1};
+
+  p->records.clear();
+  p->flops = 0;
+  int64_t inter = 0;
+  for (int t = 0; t < (int)p->terms.size(); ++t) {
+    const dmrg_term& term = p->terms[t];
+    const std::vector<HostBlock>& As = term.a_op == DMRG_IDENTITY_OP ? idL : p->opsL[term.a_op];
+    const std::vector<HostBlock>& Bs = term.b_op == DMRG_IDENTITY_OP ? idR : p->opsR[term.b_op];
+    for (int ai = 0; ai < (int)As.size(); ++ai) {
+      for (int bi = 0; bi < (int)Bs.size(); ++bi) {
+        const HostBlock& A = As[ai];
+        const HostBlock& B = Bs[bi];
+        auto in = pidx.find({A.idx_in, B.idx_in});
+        auto out = pidx.find({A.idx_out, B.idx_out});
+        if (in == pidx.end() || out == pidx.end()) continue;
+        Record r{};
+        r.term = t;
+        r.a_blk = term.a_op == DMRG_IDENTITY_OP ? -1 : ai;
+        r.b_blk = term.b_op == DMRG_IDENTITY_OP ? -1 : bi;
+        r.pin = in->second;
+        r.pout = out->second;
+        r.i = A.idx_in; r.j = A.idx_out; r.k = B.idx_in; r.l = B.idx_out;
+        r.di = p->dimL[r.i]; r.dj = p->dimL[r.j]; r.dk = p->dimR[r.k]; r.dl = p->dimR[r.l];
+        r.coef = term.coef;
+        r.inter_off = -1;
+        if (r.a_blk >= 0 && r.b_blk >= 0) {
+          int64_t cA = 2 * r.dj * r.di * r.dk + 2 * r.dj * r.dk * r.dl;
+          int64_t cB = 2 * r.di * r.dk * r.dl + 2 * r.dj * r.di * r.dl;
+          r.a_first = cA <= cB ? 1 : 0;
+          p->flops += std::min(cA, cB);
+          r.inter_off = inter;
+          inter += round_up(r.a_first ? r.dj * r.dk : r.di * r.dl, 32);
+        } else if (r.a_blk >= 0) {
+          p->flops += 2 * r.dj * r.di * r.dk;
+        } else if (r.b_blk >= 0) {
+          p->flops += 2 * r.di * r.dk * r.dl;
+        }
+        p->records.push_back(r);
+      }
+    }
+  }
+  p->T_elems = (size_t)inter;
+
+  auto A_of = [&](const Record& r) -> const HostBlock& {
+    return p->opsL[p->terms[r.term].a_op][r.a_blk];
+  };
+  auto B_of = [&](const Record& r) -> const HostBlock& {
+    return p->opsR[p->terms[r.term].b_op][r.b_blk];
+  };
+
+  // stage 1: one job per record with two non-identity factors
+  std::vector<std::pair<int64_t, int>> order1;
+  for (const Record& r : p->records) {
+    if (r.a_blk < 0 || r.b_blk < 0) continue;
+    Job64 job{};
+    Seg64 s{};
+    if (r.a_first) {  // T[dj x dk] = A[dj x di] X[di x dk]
+      const HostBlock& A = A_of(r);
+      job.C = opnd(SP_T, r.inter_off, r.dk, 1);
+      job.M = (int32_t)r.dj;
+      job.N = (int32_t)r.dk;
+      s.P = opnd(SP_ARENA, A.arena_off, A.cols, 1);
+      s.Q = opnd(SP_X, p->pair_off[r.pin], r.dk, 1);
+      s.K = (int32_t)r.di;
+    } else {          // U[di x dl] = X[di x dk] B^T[dk x dl]
+      const HostBlock& B = B_of(r);
+      job.C = opnd(SP_T, r.inter_off, r.dl, 1);
+      job.M = (int32_t)r.di;
+      job.N = (int32_t)r.dl;
+      s.P = opnd(SP_X, p->pair_off[r.pin], r.dk, 1);
+      s.Q = opnd(SP_ARENA, B.arena_off, 1, B.cols);
+      s.K = (int32_t)r.dk;
+    }
+    s.alpha = 1.0;
+    job.axpy = 0.0;
+    job.Xaxpy = opnd(SP_X, 0, 0, 0);
+    job.seg_begin = (int32_t)bld->segs.size();
+    bld->segs.push_back(s);
+    job.seg_end = (int32_t)bld->segs.size();
+    int jid = (int)bld->jobs.size();
+    bld->jobs.push_back(job);
+    order1.push_back({(int64_t)s.K, jid});
+  }
+  // stage 2: one job per output pair
+  std::vector<std::vector<int>> by_out(npairs);
+  for (int ri = 0; ri < (int)p->records.size(); ++ri) by_out[p->records[ri].pout].push_back(ri);
+  std::vector<std::pair<int64_t, int>> order2;
+  for (int q = 0; q < npairs; ++q) {
+    int i = p->pair_i[q], k = p->pair_k[q];
+    Job64 job{};
+    job.C = opnd(SP_Y, p->pair_off[q], p->dimR[k], 1);
+    job.M = (int32_t)p->dimL[i];
+    job.N = (int32_t)p->dimR[k];
+    job.axpy = 0.0;
+    job.Xaxpy = opnd(SP_X, p->pair_off[q], p->dimR[k], 1);
+    job.seg_begin = (int32_t)bld->segs.size();
+    int64_t cost = 0;
+    for (int ri : by_out[q]) {
+      const Record& r = p->records[ri];
+      Seg64 s{};
+      s.alpha = r.coef;
+      if (r.a_blk >= 0 && r.b_blk >= 0) {
+        if (r.a_first) {  // Y += coef T[dj x dk] B^T[dk x dl]
+          const HostBlock& B = B_of(r);
+          s.P = opnd(SP_T, r.inter_off, r.dk, 1);
+          s.Q = opnd(SP_ARENA, B.arena_off, 1, B.cols);
+          s.K = (int32_t)r.dk;
+        } else {          // Y += coef A[dj x di] U[di x dl]
+          const HostBlock& A = A_of(r);
+          s.P = opnd(SP_ARENA, A.arena_off, A.cols, 1);
+          s.Q = opnd(SP_T, r.inter_off, r.dl, 1);
+          s.K = (int32_t)r.di;
+        }
+      } else if (r.a_blk >= 0) {  // (A (x) 1): Y_jl += coef A X_il, k == l
+        const HostBlock& A = A_of(r);
+        s.P = opnd(SP_ARENA, A.arena_off, A.cols, 1);
+        s.Q = opnd(SP_X, p->pair_off[r.pin], r.dk, 1);
+        s.K = (int32_t)r.di;
+      } else if (r.b_blk >= 0) {  // (1 (x) B): Y_jl += coef X_jk B^T, i == j
+        const HostBlock& B = B_of(r);
+        s.P = opnd(SP_X, p->pair_off[r.pin], r.dk, 1);
+        s.Q = opnd(SP_ARENA, B.arena_off, 1, B.cols);
+        s.K = (int32_t)r.dk;
+      } else {                    // (1 (x) 1): Y += coef X
+        job.axpy += r.coef;
+        continue;
+      }
+      if (s.K == 0) continue;
+      cost += s.K;
+      bld->segs.push_back(s);
+    }
+    job.seg_end = (int32_t)bld->segs.size();
+    int jid = (int)bld->jobs.size();
+    bld->jobs.push_back(job);
+    order2.push_back({cost, jid});
+  }
+  // longest-first ordering of the tiles of each stage (LPT)
+  auto by_cost = [](const std::pair<int64_t, int>& a, const std::pair<int64_t, int>& b) {
+    return a.first != b.first ? a.first > b.first : a.second < b.second;
+  };
+  std::stable_sort(order1.begin(), order1.end(), by_cost);
+  std::stable_sort(order2.begin(), order2.end(), by_cost);
+  for (auto& pr : order1) add_tiles(bld->tiles1, pr.second, bld->jobs[pr.second].M, bld->jobs[pr.second].N);
+  for (auto& pr : order2) {
+    const Job64& j = bld->jobs[pr.second];
+    if (j.M == 0 || j.N == 0) continue;
+    add_tiles(bld->tiles2, pr.second, j.M, j.N);
+  }
+  return DMRG_OK;
+}
+
+template <typename T>
+dmrg_status upload(T** dst, const std::vector<T>& src, size_t* bytes, cudaStream_t st) {
+  *dst = nullptr;
+  if (src.empty()) return DMRG_OK;
+  DMRG_CUDA_TRY(cudaMalloc((void**)dst, sizeof(T) * src.size()));
+  *bytes += sizeof(T) * src.size();
+  DMRG_CUDA_TRY(cudaMemcpyAsync(*dst, src.data(), sizeof(T) * src.size(),
+                                cudaMemcpyHostToDevice, st));
+  return DMRG_OK;
+}
+
+// ---------------------------------------------------------------- diagonal of H_SB
+// D[off_p + a * dk + b] = sum_t coef_t diag(A_t,ii)[a] * diag(B_t,kk)[b] over the terms
+// whose factors have a diagonal-sector block (identity factors contribute 1).
+struct DiagEntry {
+  int64_t a_off, b_off;   // arena offsets of the diagonal blocks, -1 identity, -2 absent
+  int64_t a_ld, b_ld;
+  double coef;
+};
+
+__global__ void diag_kernel(const double* __restrict__ arena, const DiagEntry* __restrict__ ent,
+                            int nterms, const int64_t* __restrict__ pair_off,
+                            const int64_t* __restrict__ pair_dk, double* __restrict__ D) {
+  const int p = blockIdx.y;
+  const int64_t off = pair_off[p], size = pair_off[p + 1] - off, dk = pair_dk[p];
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < size;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t a = e / dk, b = e - a * dk;
+    double acc = 0.0;
+    for (int t = 0; t < nterms; ++t) {
+      const DiagEntry& d = ent[(int64_t)p * nterms + t];
+      if (d.a_off == -2 || d.b_off == -2) continue;
+      const double da = d.a_off == -1 ? 1.0 : arena[d.a_off + a * (d.a_ld + 1)];
+      const double db = d.b_off == -1 ? 1.0 : arena[d.b_off + b * (d.b_ld + 1)];
+      acc = fma(d.coef * da, db, acc);
+    }
+    D[off + e] = acc;
+  }
+}
+
+}  // namespace
+
+namespace dmrg {
+
+dmrg_status compute_diagonal(dmrg_plan* p, double* d, cudaStream_t st) {
+  const int npairs = (int)p->pair_i.size();
+  const int nterms = (int)p->terms.size();
+  if (npairs == 0 || p->n == 0) return DMRG_OK;
+  std::vector<DiagEntry> ent((size_t)npairs * std::max(nterms, 1));
+  for (int q = 0; q < npairs; ++q) {
+    int i = p->pair_i[q], k = p->pair_k[q];
+    for (int t = 0; t < nterms; ++t) {
+      DiagEntry e{-2, -2, 0, 0, p->terms[t].coef};
+      const dmrg_term& term = p->terms[t];
+      if (term.a_op == DMRG_IDENTITY_OP) {
+        e.a_off = -1;
+      } else {
+        for (auto& hb : p->opsL[term.a_op])
+          if (hb.idx_in == i && hb.idx_out == i) { e.a_off = hb.arena_off; e.a_ld = hb.cols; }
+      }
+      if (term.b_op == DMRG_IDENTITY_OP) {
+        e.b_off = -1;
+      } else {
+        for (auto& hb : p->opsR[term.b_op])
+          if (hb.idx_in == k && hb.idx_out == k) { e.b_off = hb.arena_off; e.b_ld = hb.cols; }
+      }
+      ent[(size_t)q * nterms + t] = e;
+    }
+  }
+  std::vector<int64_t> dk(npairs);
+  for (int q = 0; q < npairs; ++q) dk[q] = p->dimR[p->pair_k[q]];
+  DiagEntry* d_ent = nullptr;
+  int64_t *d_off = nullptr, *d_dk = nullptr;
+  size_t dummy = 0;
+  DMRG_TRY(upload(&d_ent, ent, &dummy, st));
+  DMRG_TRY(upload(&d_off, p->pair_off, &dummy, st));
+  DMRG_TRY(upload(&d_dk, dk, &dummy, st));
+  dim3 grid(64, npairs);
+  diag_kernel<<<grid, 256, 0, st>>>(p->arena, d_ent, nterms, d_off, d_dk, d);
+  note_launch();
+  cudaError_t e = cudaGetLastError();
+  cudaStreamSynchronize(st);
+  cudaFree(d_ent);
+  cudaFree(d_off);
+  cudaFree(d_dk);
+  if (e != cudaSuccess) {
+    set_error("diag_kernel: %s", cudaGetErrorString(e));
+    return DMRG_ERR_CUDA;
+  }
+  return DMRG_OK;
+}
+
+}  // namespace dmrg
+
+extern "C" {
+
+dmrg_status dmrg_plan_create(const dmrg_superblock_desc* desc, const dmrg_options* opt,
+                             void* stream, dmrg_plan** out) {
+  if (!out) {
+    set_error("out is NULL");
+    return DMRG_ERR_INVALID_ARG;
+  }
+  *out = nullptr;
+  dmrg_plan* p = new (std::nothrow) dmrg_plan();
+  if (!p) {
+    set_error("host allocation failed");
+    return DMRG_ERR_OOM;
+  }
+  if (opt) p->opt = *opt; else dmrg_options_default(&p->opt);
+  if (p->opt.max_subspace < 2 || p->opt.max_subspace > DMRG_MAX_SUBSPACE ||
+      p->opt.max_iter < 1 || !(p->opt.tol >= 0.0) ||
+      (int)p->opt.prec < 0 || (int)p->opt.prec > 2) {
+    set_error("options out of range (max_subspace must be in [2, %d])", DMRG_MAX_SUBSPACE);
+    delete p;
+    return DMRG_ERR_INVALID_ARG;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  dmrg_status s = validate_and_copy(desc, p);
+  if (s != DMRG_OK) { delete p; return s; }
+  cudaGetDevice(&p->device);
+  Builder bld;
+  s = build_records_and_jobs(p, &bld);
+  if (s != DMRG_OK) { delete p; return s; }
+  auto fail = [&](dmrg_status st_) { dmrg_plan_destroy(p); return st_; };
+  if (p->arena_elems) {
+    if (cudaMalloc((void**)&p->arena, sizeof(double) * p->arena_elems) != cudaSuccess) {
+      set_error("cudaMalloc of %zu bytes for the operator arena failed",
+                sizeof(double) * p->arena_elems);
+      return fail(DMRG_ERR_OOM);
+    }
+    p->device_bytes += sizeof(double) * p->arena_elems;
+    if (cudaMemcpyAsync(p->arena, p->arena_host.data(), sizeof(double) * p->arena_elems,
+                        cudaMemcpyHostToDevice, st) != cudaSuccess) {
+      set_error("arena upload failed");
+      return fail(DMRG_ERR_CUDA);
+    }
+  }
+  if (p->T_elems) {
+    if (cudaMalloc((void**)&p->T, sizeof(double) * p->T_elems) != cudaSuccess) {
+      set_error("cudaMalloc for the intermediates failed");
+      return fail(DMRG_ERR_OOM);
+    }
+    p->device_bytes += sizeof(double) * p->T_elems;
+  }
+  if ((s = upload(&p->d_jobs, bld.jobs, &p->device_bytes, st)) != DMRG_OK) return fail(s);
+  if ((s = upload(&p->d_segs, bld.segs, &p->device_bytes, st)) != DMRG_OK) return fail(s);
+  if ((s = upload(&p->d_tiles1, bld.tiles1, &p->device_bytes, st)) != DMRG_OK) return fail(s);
+  if ((s = upload(&p->d_tiles2, bld.tiles2, &p->device_bytes, st)) != DMRG_OK) return fail(s);
+  p->ntiles1 = (int64_t)bld.tiles1.size();
+  p->ntiles2 = (int64_t)bld.tiles2.size();
+  if (p->n > 0) {
+    if (cudaMalloc((void**)&p->D, sizeof(double) * p->n) != cudaSuccess) {
+      set_error("cudaMalloc for the diagonal failed");
+      return fail(DMRG_ERR_OOM);
+    }
+    p->device_bytes += sizeof(double) * p->n;
+    if ((s = compute_diagonal(p, p->D, st)) != DMRG_OK) return fail(s);
+  }
+  if (cudaStreamSynchronize(st) != cudaSuccess) {
+    set_error("plan upload: %s", cudaGetErrorString(cudaGetLastError()));
+    return fail(DMRG_ERR_CUDA);
+  }
+  *out = p;
+  return DMRG_OK;
+}
+
+void dmrg_plan_destroy(dmrg_plan* p) {
+  if (!p) return;
+  destroy_tc(p);
+  cudaFree(p->arena);
+  cudaFree(p->T);
+  cudaFree(p->D);
+  cudaFree(p->d_jobs);
+  cudaFree(p->d_segs);
+  cudaFree(p->d_tiles1);
+  cudaFree(p->d_tiles2);
+  delete p;
+}
+
+dmrg_status dmrg_plan_get_stats(const dmrg_plan* p, dmrg_plan_stats* s) {
+  if (!p || !s) {
+    set_error("NULL argument");
+    return DMRG_ERR_INVALID_ARG;
+  }
+  s->n = p->n;
+  s->records = (int64_t)p->records.size();
+  s->flops = p->flops;
+  s->tiles_stage1 = p->ntiles1;
+  s->tiles_stage2 = p->ntiles2;
+  s->device_bytes = (int64_t)p->device_bytes;
+  return DMRG_OK;
+}
+
+dmrg_status dmrg_diagonal(dmrg_plan* p, double* d, void* stream) {
+  if (!p || (!d && p->n)) {
+    set_error("NULL argument");
+    return DMRG_ERR_INVALID_ARG;
+  }
+  if (p->n == 0) return DMRG_OK;
+  DMRG_CUDA_TRY(cudaMemcpyAsync(d, p->D, sizeof(double) * p->n, cudaMemcpyDeviceToDevice,
+                                (cudaStream_t)stream));
+  return DMRG_OK;
+}
+
+dmrg_status dmrg_project_prec(dmrg_plan* p, dmrg_precision prec, const double* x, double* y,
+                              void* stream) {
+  if (!p || (p->n && (!x || !y))) {
+    set_error("NULL argument");
+    return DMRG_ERR_INVALID_ARG;
+  }
+  if (p->n == 0) return DMRG_OK;
+  if ((const double*)y < x + p->n && x < (const double*)y + p->n) {
+    set_error("x and y overlap");
+    return DMRG_ERR_INVALID_ARG;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  if (prec == DMRG_PREC_FP64) return launch_project_fp64(p, x, y, st);
+  if (prec == DMRG_PREC_TF32 || prec == DMRG_PREC_BF16X3) return launch_project_tc(p, prec, x, y, st);
+  set_error("unknown precision %d", (int)prec);
+  return DMRG_ERR_INVALID_ARG;
+}
+
+dmrg_status dmrg_project(dmrg_plan* p, const double* x, double* y, void* stream) {
+  return dmrg_project_prec(p, DMRG_PREC_FP64, x, y, stream);
+}
+
+}  // extern "C"

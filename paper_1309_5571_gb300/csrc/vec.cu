@@ -1,0 +1,570 @@
+// Davidson vector kernels (Algorithm 3, all lines except the projection) and the small
+// projected eigenproblem.
+//
+// Every kernel streams the tall-skinny basis V (and W) once, column-major with columns
+// contiguous (leading dimension ldv, a multiple of 32 elements, zero padding beyond n),
+// reading 16-byte double2 pairs so a warp touches 512 contiguous bytes per column.  The
+// paper's gemv_trans kernel (Sec. 6.1, Algorithm 4) gives each thread a row and keeps
+// a belt of column sums in registers, then reduces across the block; here a thread also
+// keeps all k <= 24 column sums in registers, the block reduces with warp shuffles, and
+// the cross-block reduction is a deterministic one-pass scheme: every block writes its
+// partial sums, and the last block to finish (atomic ticket) adds them in block order.
+// Several Algorithm 3 lines are fused so each pass over V does as much as possible:
+//   residual:  x = V y, W y, r = W y - lambda x, t = r / (lambda - D),  ||r||^2,
+//              V^T t and ||t||^2                                 (lines 5, 6, 9, 11)
+//   cgs:       t -= V s, then V^T t and ||t||^2                     (lines 12, 11)
+//   finish:    normalise t                                           (line 13)
+#include <math.h>
+
+#include "internal.h"
+
+namespace dmrg {
+namespace {
+
+constexpr int kGridPerSM = 4;
+constexpr int kSlots = KMAX + 4;
+
+struct Ticket {
+  // returns true in every thread of the last block to arrive
+  __device__ static bool last_block(unsigned int* counter) {
+    __shared__ bool is_last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      unsigned int t = atomicAdd(counter, 1u);
+      is_last = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    return is_last;
+  }
+};
+
+// Block-reduce the per-thread values acc[0..NDOT+NEXTRA): the first NDOT are dot
+// products of which only kdots < NDOT are live (slots 0..kdots), the last NEXTRA are
+// always live and go to slots kdots..kdots+NEXTRA.  Every index into acc is a
+// compile-time constant, so acc stays in registers.  Stores this block's partial sums at
+// partials[blockIdx.x * kSlots + slot].
+template <int NDOT, int NEXTRA>
+__device__ void block_partials(double (&acc)[NDOT + NEXTRA], int kdots, double* partials) {
+  __shared__ double red[kVecThreads / 32][kSlots];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int j = 0; j < NDOT + NEXTRA; ++j) {
+    const bool live = j < NDOT ? (j < kdots) : true;
+    const int slot = j < NDOT ? j : kdots + (j - NDOT);
+    if (live) {
+      double v = acc[j];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == 0) red[warp][slot] = v;
+    }
+  }
+  __syncthreads();
+  const int nv = kdots + NEXTRA;
+  for (int j = threadIdx.x; j < nv; j += blockDim.x) {
+    double v = 0.0;
+    for (int w = 0; w < kVecThreads / 32; ++w) v += red[w][j];
+    partials[(int64_t)blockIdx.x * kSlots + j] = v;
+  }
+}
+
+// In the last block: total[j] = sum over blocks (fixed order) of partials, j < nv.
+__device__ void final_sums(const double* partials, int nv, double* total) {
+  __shared__ double tmp[kVecThreads];
+  for (int j = 0; j < nv; ++j) {
+    double v = 0.0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
+      v += __ldcg(&partials[(int64_t)b * kSlots + j]);
+    tmp[threadIdx.x] = v;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+      if (threadIdx.x < s) tmp[threadIdx.x] += tmp[threadIdx.x + s];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) total[j] = tmp[0];
+    __syncthreads();
+  }
+}
+
+__device__ __forceinline__ double2 ld2(const double* p) {
+  return __ldg(reinterpret_cast<const double2*>(p));
+}
+__device__ __forceinline__ double2 ld2cg(const double* p) {
+  return __ldcg(reinterpret_cast<const double2*>(p));
+}
+
+// ---------------------------------------------------------------- overlap  s = V^T w
+__global__ void __launch_bounds__(kVecThreads)
+overlap_kernel(const double* __restrict__ V, int64_t ldv, int64_t n2, int k,
+               const double* __restrict__ w, double* __restrict__ partials,
+               unsigned int* counter, double* s_out, DevSmall* small, int Bcol) {
+  double acc[KMAX];
+#pragma unroll
+  for (int j = 0; j < KMAX; ++j) acc[j] = 0.0;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n2;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const double2 wv = ld2cg(w + 2 * e);
+#pragma unroll
+    for (int j = 0; j < KMAX; ++j) {
+      if (j < k) {
+        const double2 v = ld2(V + j * ldv + 2 * e);
+        acc[j] = fma(v.x, wv.x, fma(v.y, wv.y, acc[j]));
+      }
+    }
+  }
+  block_partials<KMAX, 0>(acc, k, partials);
+  if (Ticket::last_block(counter)) {
+    __shared__ double tot[KMAX];
+    final_sums(partials, k, tot);
+    for (int j = threadIdx.x; j < k; j += blockDim.x) {
+      if (s_out) s_out[j] = tot[j];
+      if (Bcol >= 0) {
+        small->B[j * KMAX + Bcol] = tot[j];
+        small->B[Bcol * KMAX + j] = tot[j];
+      }
+    }
+    if (threadIdx.x == 0) *counter = 0u;
+  }
+}
+
+// Public variant of the overlap for caller-owned V (any ldv, any alignment): scalar loads.
+__global__ void __launch_bounds__(kVecThreads)
+gemv_trans_kernel(const double* __restrict__ V, int64_t ldv, int64_t n, int k,
+                  const double* __restrict__ w, double* __restrict__ partials,
+                  unsigned int* counter, double* s_out) {
+  double acc[KMAX];
+#pragma unroll
+  for (int j = 0; j < KMAX; ++j) acc[j] = 0.0;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const double wv = __ldg(w + e);
+#pragma unroll
+    for (int j = 0; j < KMAX; ++j)
+      if (j < k) acc[j] = fma(__ldg(V + j * ldv + e), wv, acc[j]);
+  }
+  block_partials<KMAX, 0>(acc, k, partials);
+  if (Ticket::last_block(counter)) {
+    __shared__ double tot[KMAX];
+    final_sums(partials, k, tot);
+    for (int j = threadIdx.x; j < k; j += blockDim.x) s_out[j] = tot[j];
+    if (threadIdx.x == 0) *counter = 0u;
+  }
+}
+
+// ---------------------------------------------------------------- residual + correction
+__global__ void __launch_bounds__(kVecThreads)
+residual_kernel(const double* __restrict__ V, const double* __restrict__ W,
+                const double* __restrict__ D, int64_t ldv, int64_t n2, int k,
+                double* __restrict__ tcol, double* __restrict__ partials,
+                unsigned int* counter, DevSmall* small, int mode) {
+  __shared__ double ys[KMAX];
+  __shared__ double lam_s;
+  if (threadIdx.x < KMAX) ys[threadIdx.x] = threadIdx.x < k ? small->y[threadIdx.x] : 0.0;
+  if (threadIdx.x == 0) lam_s = small->lambda;
+  __syncthreads();
+  const double lam = lam_s;
+  double acc[KMAX + 2];  // [0..k): V^T t, [k]: ||r||^2, [k+1]: ||t||^2
+#pragma unroll
+  for (int j = 0; j < KMAX + 2; ++j) acc[j] = 0.0;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n2;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    double2 v[KMAX];
+    double x0 = 0.0, x1 = 0.0, w0 = 0.0, w1 = 0.0;
+#pragma unroll
+    for (int j = 0; j < KMAX; ++j) {
+      if (j < k) {
+        v[j] = ld2(V + j * ldv + 2 * e);
+        const double2 wv = ld2(W + j * ldv + 2 * e);
+        x0 = fma(ys[j], v[j].x, x0);
+        x1 = fma(ys[j], v[j].y, x1);
+        w0 = fma(ys[j], wv.x, w0);
+        w1 = fma(ys[j], wv.y, w1);
+      }
+    }
+    const double r0 = w0 - lam * x0, r1 = w1 - lam * x1;
+    double t0 = r0, t1 = r1;
+    if (mode == 0) {
+      const double2 d = ld2(D + 2 * e);
+      double q0 = lam - d.x, q1 = lam - d.y;
+      if (fabs(q0) < 1e-8) q0 = q0 >= 0.0 ? 1e-8 : -1e-8;
+      if (fabs(q1) < 1e-8) q1 = q1 >= 0.0 ? 1e-8 : -1e-8;
+      t0 = r0 / q0;
+      t1 = r1 / q1;
+    }
+    reinterpret_cast<double2*>(tcol)[e] = make_double2(t0, t1);
+#pragma unroll
+    for (int j = 0; j < KMAX; ++j)
+      if (j < k) acc[j] = fma(v[j].x, t0, fma(v[j].y, t1, acc[j]));
+    acc[KMAX] = fma(r0, r0, fma(r1, r1, acc[KMAX]));
+    acc[KMAX + 1] = fma(t0, t0, fma(t1, t1, acc[KMAX + 1]));
+  }
+  block_partials<KMAX, 2>(acc, k, partials);
+  if (Ticket::last_block(counter)) {
+    __shared__ double tot[KMAX + 2];
+    final_sums(partials, k + 2, tot);
+    for (int j = threadIdx.x; j < k; j += blockDim.x) small->s[0][j] = tot[j];
+    if (threadIdx.x == 0) {
+      small->rnorm2 = tot[k];
+      small->tnorm2_before = tot[k + 1];
+      small->tnorm2 = tot[k + 1];
+      if (!isfinite(tot[k]) || !isfinite(tot[k + 1])) small->flags |= 2;
+      *counter = 0u;
+    }
+  }
+}
+
+// ---------------------------------------------------------------- Gram-Schmidt pass
+__global__ void __launch_bounds__(kVecThreads)
+cgs_kernel(const double* __restrict__ V, int64_t ldv, int64_t n2, int k, double* tcol,
+           double* __restrict__ partials, unsigned int* counter, DevSmall* small, int sin,
+           int sout) {
+  __shared__ double ss[KMAX];
+  if (threadIdx.x < KMAX) ss[threadIdx.x] = threadIdx.x < k ? small->s[sin][threadIdx.x] : 0.0;
+  __syncthreads();
+  double acc[KMAX + 1];
+#pragma unroll
+  for (int j = 0; j < KMAX + 1; ++j) acc[j] = 0.0;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n2;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    double2 t = reinterpret_cast<const double2*>(tcol)[e];
+    double2 v[KMAX];
+#pragma unroll
+    for (int j = 0; j < KMAX; ++j) {
+      if (j < k) {
+        v[j] = ld2(V + j * ldv + 2 * e);
+        t.x = fma(-ss[j], v[j].x, t.x);
+        t.y = fma(-ss[j], v[j].y, t.y);
+      }
+    }
+    reinterpret_cast<double2*>(tcol)[e] = t;
+#pragma unroll
+    for (int j = 0; j < KMAX; ++j)
+      if (j < k) acc[j] = fma(v[j].x, t.x, fma(v[j].y, t.y, acc[j]));
+    acc[KMAX] = fma(t.x, t.x, fma(t.y, t.y, acc[KMAX]));
+  }
+  block_partials<KMAX, 1>(acc, k, partials);
+  if (Ticket::last_block(counter)) {
+    __shared__ double tot[KMAX + 1];
+    final_sums(partials, k + 1, tot);
+    for (int j = threadIdx.x; j < k; j += blockDim.x) small->s[sout][j] = tot[j];
+    if (threadIdx.x == 0) {
+      small->tnorm2 = tot[k];
+      if (!isfinite(tot[k])) small->flags |= 2;
+      *counter = 0u;
+    }
+  }
+}
+
+// ---------------------------------------------------------------- normalise new column
+__global__ void finish_kernel(double* tcol, int64_t n2, DevSmall* small) {
+  const double before = small->tnorm2_before, after = small->tnorm2;
+  const bool breakdown = !(after > 1e-20 * before) || !(after > 0.0);
+  if (breakdown) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) small->flags |= 1;
+    return;
+  }
+  const double inv = 1.0 / sqrt(after);
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n2;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    double2 t = reinterpret_cast<double2*>(tcol)[e];
+    t.x *= inv;
+    t.y *= inv;
+    reinterpret_cast<double2*>(tcol)[e] = t;
+  }
+}
+
+// ---------------------------------------------------------------- Ritz vector
+__global__ void ritz_kernel(const double* __restrict__ V, const double* __restrict__ W,
+                            int64_t ldv, int64_t n, int k, const DevSmall* small,
+                            double* __restrict__ x_out, double* __restrict__ wy_out) {
+  __shared__ double ys[KMAX];
+  if (threadIdx.x < KMAX) ys[threadIdx.x] = threadIdx.x < k ? small->y[threadIdx.x] : 0.0;
+  __syncthreads();
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    double x = 0.0, wy = 0.0;
+    for (int j = 0; j < k; ++j) {
+      x = fma(ys[j], V[j * ldv + e], x);
+      if (wy_out) wy = fma(ys[j], W[j * ldv + e], wy);
+    }
+    x_out[e] = x;
+    if (wy_out) wy_out[e] = wy;
+  }
+}
+
+// ---------------------------------------------------------------- normalise a vector
+__global__ void __launch_bounds__(kVecThreads)
+sumsq_kernel(const double* __restrict__ src, int64_t n, double* __restrict__ partials,
+             unsigned int* counter, DevSmall* small) {
+  double acc[1] = {0.0};
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x)
+    acc[0] = fma(src[e], src[e], acc[0]);
+  block_partials<0, 1>(acc, 0, partials);
+  if (Ticket::last_block(counter)) {
+    __shared__ double tot[1];
+    final_sums(partials, 1, tot);
+    if (threadIdx.x == 0) {
+      small->nrm2 = tot[0];
+      *counter = 0u;
+    }
+  }
+}
+
+__global__ void scale_copy_kernel(const double* __restrict__ src, double* __restrict__ dst,
+                                  int64_t n, const DevSmall* small) {
+  const double inv = 1.0 / sqrt(small->nrm2);
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x)
+    dst[e] = src[e] * inv;
+}
+
+__global__ void set_B00_kernel(DevSmall* small) {
+  // after a restart the basis is the single Ritz vector x with B = [lambda]
+  for (int j = threadIdx.x; j < KMAX * KMAX; j += blockDim.x) small->B[j] = 0.0;
+  __syncthreads();
+  if (threadIdx.x == 0) small->B[0] = small->lambda;
+}
+
+// ---------------------------------------------------------------- small eigenproblem
+// Smallest eigenpair of the symmetric k x k matrix B (Algorithm 3 line 4) by the cyclic
+// Jacobi method with the round-robin ordering: each of the k-1 steps of a sweep applies
+// k/2 disjoint rotations at once.  A rotation (p, q) uses the symmetric Schur
+// decomposition of the 2 x 2 block: tau = (a_qq - a_pp) / (2 a_pq),
+// t = sign(tau) / (|tau| + sqrt(1 + tau^2)), c = 1 / sqrt(1 + t^2), s = t c, which
+// zeroes a_pq in J^T A J.  Sweeps stop when the off-diagonal mass is below 1e-30 of the
+// total (or after 30 sweeps).
+__global__ void __launch_bounds__(256) jacobi_kernel(DevSmall* small, int k) {
+  __shared__ double A[KMAX][KMAX + 1];
+  __shared__ double Q[KMAX][KMAX + 1];
+  __shared__ double cs[KMAX / 2], sn[KMAX / 2];
+  __shared__ int pp[KMAX / 2], qq[KMAX / 2];
+  __shared__ int perm[KMAX];
+  __shared__ double red[256];
+  __shared__ int done;
+  const int tid = threadIdx.x;
+  const int kk = (k + 1) & ~1;  // even number of players; the extra one is a dummy
+  for (int e = tid; e < KMAX * KMAX; e += blockDim.x) {
+    const int r = e / KMAX, c = e % KMAX;
+    A[r][c] = (r < k && c < k) ? small->B[r * KMAX + c] : 0.0;
+    Q[r][c] = (r == c) ? 1.0 : 0.0;
+  }
+  if (tid < kk) perm[tid] = tid;
+  __syncthreads();
+  int sweep = 0;
+  for (; sweep < 30; ++sweep) {
+    // convergence test: off-diagonal vs total Frobenius mass
+    double off = 0.0, tot = 0.0;
+    for (int e = tid; e < k * k; e += blockDim.x) {
+      const int r = e / k, c = e % k;
+      const double v = A[r][c] * A[r][c];
+      tot += v;
+      if (r != c) off += v;
+    }
+    red[tid] = off;
+    __syncthreads();
+    for (int s = 128; s > 0; s >>= 1) {
+      if (tid < s) red[tid] += red[tid + s];
+      __syncthreads();
+    }
+    const double offsum = red[0];
+    __syncthreads();
+    red[tid] = tot;
+    __syncthreads();
+    for (int s = 128; s > 0; s >>= 1) {
+      if (tid < s) red[tid] += red[tid + s];
+      __syncthreads();
+    }
+    if (tid == 0) done = (offsum <= 1e-30 * red[0]) || k <= 1;
+    __syncthreads();
+    if (done) break;
+    for (int step = 0; step < kk - 1; ++step) {
+      // pairs of this round: (perm[i], perm[kk-1-i])
+      if (tid < kk / 2) {
+        int p = perm[tid], q = perm[kk - 1 - tid];
+        if (p > q) { const int t = p; p = q; q = t; }
+        double c = 1.0, s = 0.0;
+        if (q < k) {
+          const double apq = A[p][q];
+          if (apq != 0.0) {
+            const double tau = (A[q][q] - A[p][p]) / (2.0 * apq);
+            const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+            c = 1.0 / sqrt(1.0 + t * t);
+            s = t * c;
+          }
+        }
+        pp[tid] = p;
+        qq[tid] = q;
+        cs[tid] = c;
+        sn[tid] = s;
+      }
+      __syncthreads();
+      // rows: A <- J^T A
+      for (int e = tid; e < (kk / 2) * kk; e += blockDim.x) {
+        const int pr = e / kk, col = e % kk;
+        const int p = pp[pr], q = qq[pr];
+        if (q >= k || col >= k) continue;
+        const double c = cs[pr], s = sn[pr];
+        const double ap = A[p][col], aq = A[q][col];
+        A[p][col] = c * ap - s * aq;
+        A[q][col] = s * ap + c * aq;
+      }
+      __syncthreads();
+      // columns: A <- A J, Q <- Q J
+      for (int e = tid; e < (kk / 2) * kk; e += blockDim.x) {
+        const int pr = e / kk, row = e % kk;
+        const int p = pp[pr], q = qq[pr];
+        if (q >= k || row >= k) continue;
+        const double c = cs[pr], s = sn[pr];
+        const double ap = A[row][p], aq = A[row][q];
+        A[row][p] = c * ap - s * aq;
+        A[row][q] = s * ap + c * aq;
+        const double qp = Q[row][p], qv = Q[row][q];
+        Q[row][p] = c * qp - s * qv;
+        Q[row][q] = s * qp + c * qv;
+      }
+      __syncthreads();
+      // exact zero for the annihilated entries
+      if (tid < kk / 2) {
+        const int p = pp[tid], q = qq[tid];
+        if (q < k && sn[tid] != 0.0) { A[p][q] = 0.0; A[q][p] = 0.0; }
+      }
+      // rotate the tournament (player 0 fixed)
+      if (tid == 0) {
+        const int last = perm[kk - 1];
+        for (int i = kk - 1; i > 1; --i) perm[i] = perm[i - 1];
+        perm[1] = last;
+      }
+      __syncthreads();
+    }
+  }
+  if (tid == 0) {
+    int best = 0;
+    for (int i = 1; i < k; ++i)
+      if (A[i][i] < A[best][best]) best = i;
+    small->lambda = A[best][best];
+    small->jacobi_sweeps = sweep;
+    done = best;
+  }
+  __syncthreads();
+  if (tid < KMAX) small->y[tid] = tid < k ? Q[tid][done] : 0.0;
+}
+
+}  // namespace
+
+static int vec_grid() {
+  static int grid = 0;
+  if (!grid) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    grid = std::max(1, sms) * kGridPerSM;
+  }
+  return grid;
+}
+
+dmrg_status vec_work_create(VecWork* w) {
+  w->grid = vec_grid();
+  DMRG_CUDA_TRY(cudaMalloc((void**)&w->partials, sizeof(double) * (size_t)w->grid * kSlots));
+  DMRG_CUDA_TRY(cudaMalloc((void**)&w->counter, sizeof(unsigned int) * 16));
+  DMRG_CUDA_TRY(cudaMemset(w->counter, 0, sizeof(unsigned int) * 16));
+  return DMRG_OK;
+}
+
+void vec_work_destroy(VecWork* w) {
+  cudaFree(w->partials);
+  cudaFree(w->counter);
+  w->partials = nullptr;
+  w->counter = nullptr;
+}
+
+dmrg_status launch_overlap(const VecWork& w, const double* V, int64_t ldv, int64_t n, int k,
+                           const double* vec, double* s_out, DevSmall* small, int Bcol,
+                           cudaStream_t st) {
+  overlap_kernel<<<w.grid, kVecThreads, 0, st>>>(V, ldv, (n + 1) / 2, k, vec, w.partials,
+                                                 w.counter, s_out, small, Bcol);
+  DMRG_LAUNCH_CHECK();
+  return DMRG_OK;
+}
+
+dmrg_status launch_jacobi(DevSmall* small, int k, cudaStream_t st) {
+  jacobi_kernel<<<1, 256, 0, st>>>(small, k);
+  DMRG_LAUNCH_CHECK();
+  return DMRG_OK;
+}
+
+dmrg_status launch_residual(const VecWork& w, const double* V, const double* W,
+                            const double* D, int64_t ldv, int64_t n, int k, double* tcol,
+                            DevSmall* small, int mode, cudaStream_t st) {
+  residual_kernel<<<w.grid, kVecThreads, 0, st>>>(V, W, D, ldv, (n + 1) / 2, k, tcol,
+                                                  w.partials, w.counter, small, mode);
+  DMRG_LAUNCH_CHECK();
+  return DMRG_OK;
+}
+
+dmrg_status launch_cgs(const VecWork& w, const double* V, int64_t ldv, int64_t n, int k,
+                       double* tcol, DevSmall* small, int sin, int sout, cudaStream_t st) {
+  cgs_kernel<<<w.grid, kVecThreads, 0, st>>>(V, ldv, (n + 1) / 2, k, tcol, w.partials,
+                                             w.counter, small, sin, sout);
+  DMRG_LAUNCH_CHECK();
+  return DMRG_OK;
+}
+
+dmrg_status launch_finish(double* tcol, int64_t n, DevSmall* small, cudaStream_t st) {
+  finish_kernel<<<vec_grid(), kVecThreads, 0, st>>>(tcol, (n + 1) / 2, small);
+  DMRG_LAUNCH_CHECK();
+  return DMRG_OK;
+}
+
+dmrg_status launch_ritz(const double* V, const double* W, int64_t ldv, int64_t n, int k,
+                        const DevSmall* small, double* x_out, double* wy_out, cudaStream_t st) {
+  ritz_kernel<<<vec_grid(), kVecThreads, 0, st>>>(V, W, ldv, n, k, small, x_out, wy_out);
+  DMRG_LAUNCH_CHECK();
+  return DMRG_OK;
+}
+
+dmrg_status launch_normalize(const VecWork& w, const double* src, double* dst, int64_t n,
+                             DevSmall* small, cudaStream_t st) {
+  sumsq_kernel<<<w.grid, kVecThreads, 0, st>>>(src, n, w.partials, w.counter, small);
+  DMRG_LAUNCH_CHECK();
+  scale_copy_kernel<<<w.grid, kVecThreads, 0, st>>>(src, dst, n, small);
+  DMRG_LAUNCH_CHECK();
+  return DMRG_OK;
+}
+
+dmrg_status launch_set_B00(DevSmall* small, cudaStream_t st) {
+  set_B00_kernel<<<1, 256, 0, st>>>(small);
+  DMRG_LAUNCH_CHECK();
+  return DMRG_OK;
+}
+
+}  // namespace dmrg
+
+namespace dmrg {
+
+// Public s = V^T w.  The cross-block partial sums live in a stream-ordered scratch
+// allocation made for this call.
+dmrg_status launch_gemv_trans_public(const double* V, int64_t ldv, int64_t n, int k,
+                                     const double* w, double* s, cudaStream_t st) {
+  if (n == 0) {
+    DMRG_CUDA_TRY(cudaMemsetAsync(s, 0, sizeof(double) * k, st));
+    return DMRG_OK;
+  }
+  VecWork vw;
+  vw.grid = vec_grid();
+  DMRG_CUDA_TRY(cudaMallocAsync((void**)&vw.partials, sizeof(double) * (size_t)vw.grid * kSlots, st));
+  DMRG_CUDA_TRY(cudaMallocAsync((void**)&vw.counter, sizeof(unsigned int), st));
+  DMRG_CUDA_TRY(cudaMemsetAsync(vw.counter, 0, sizeof(unsigned int), st));
+  gemv_trans_kernel<<<vw.grid, kVecThreads, 0, st>>>(V, ldv, n, k, w, vw.partials, vw.counter, s);
+  note_launch();
+  cudaError_t e = cudaGetLastError();
+  cudaFreeAsync(vw.partials, st);
+  cudaFreeAsync(vw.counter, st);
+  if (e != cudaSuccess) {
+    set_error("gemv_trans_kernel: %s", cudaGetErrorString(e));
+    return DMRG_ERR_CUDA;
+  }
+  return DMRG_OK;
+}
+
+}  // namespace dmrg
