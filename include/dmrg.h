@@ -163,6 +163,22 @@ dmrg_status dmrg_diagonal(dmrg_plan* plan, double* d, void* stream);
 dmrg_status dmrg_gemv_trans(const double* V, int64_t ldv, int64_t n, int32_t k,
                             const double* w, double* s, void* stream);
 
+/* Allocation-free variant of dmrg_gemv_trans (the paper has no counterpart: it exists for
+ * callers that cannot let a library allocate device memory, such as an application whose
+ * own allocator owns all device memory, or a latency-critical loop where cudaMalloc and
+ * cudaFree would synchronise the device).  Same arguments and result as dmrg_gemv_trans;
+ * no cudaMalloc, cudaFree or other allocating routine is called.  The cross-block partial
+ * sums live in one fixed scratch array inside the library (196,864 bytes, held by every GPU
+ * that loads the library until the process exits); k above 24, the column count that array
+ * holds, is rejected with DMRG_ERR_INVALID_ARG.  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress) with that device current, so make that first
+ * call before any stream capture.  All calls on a device share the array and it keeps the
+ * last call's contents (the counter that must start at zero is cleared by every call);
+ * calls that overlap on the GPU, e.g. from unordered streams, race on it.  Enqueued on
+ * stream. */
+dmrg_status dmrg_gemv_trans_noalloc(const double* V, int64_t ldv, int64_t n, int32_t k,
+                                    const double* w, double* s, void* stream);
+
 /* Davidson state: basis V, projections W, the small matrix B of Algorithm 3, started
  * from x0 (device, n float64, normalised by the call). */
 dmrg_status dmrg_state_create(dmrg_plan* plan, const double* x0, void* stream,

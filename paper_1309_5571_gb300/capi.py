@@ -96,6 +96,8 @@ SIGNATURES = {
     "dmrg_diagonal": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "dmrg_gemv_trans": (C.c_int, [C.c_void_p, C.c_int64, C.c_int64, C.c_int32, C.c_void_p,
                                   C.c_void_p, C.c_void_p]),
+    "dmrg_gemv_trans_noalloc": (C.c_int, [C.c_void_p, C.c_int64, C.c_int64, C.c_int32,
+                                          C.c_void_p, C.c_void_p, C.c_void_p]),
     "dmrg_state_create": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_void_p)]),
     "dmrg_state_destroy": (None, [C.c_void_p]),
     "dmrg_davidson_step": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_int32)]),
@@ -348,4 +350,18 @@ def gemv_trans(V, k: int, w, stream=None):
     s = torch.empty(k, dtype=torch.float64, device="cuda")
     _check(load().dmrg_gemv_trans(V.data_ptr(), ldv, n, k, w.data_ptr(), s.data_ptr(),
                                   _stream_ptr(stream)))
+    return s
+
+
+def gemv_trans_noalloc(V, k: int, w, s=None, stream=None):
+    """Same product as gemv_trans through the allocation-free entry point; the library
+    allocates nothing (pass ``s`` to keep the caller's side free of allocations too)."""
+    torch = _torch()
+    if V.dtype != torch.float64 or not V.is_cuda or not V.is_contiguous():
+        raise ValueError("V must be a contiguous CUDA float64 tensor of shape (columns, ldv)")
+    n = w.numel()
+    if s is None:
+        s = torch.empty(k, dtype=torch.float64, device="cuda")
+    _check(load().dmrg_gemv_trans_noalloc(V.data_ptr(), V.shape[1], n, k, w.data_ptr(),
+                                          s.data_ptr(), _stream_ptr(stream)))
     return s
