@@ -49,6 +49,7 @@ struct dmrg_davidson_state {
   bool anchor_pending = false;
   double anchor_rnorm = INFINITY;
   int ritz_k = 1;  // columns that small->y refers to; 0: V(:,0) holds the Ritz vector
+  bool anchored = false;  // column 0 of W is an FP64 projection (mixed mode)
 };
 
 namespace {
@@ -56,7 +57,7 @@ namespace {
 dmrg_status read_small(dmrg_davidson_state* s, cudaStream_t st) {
   DMRG_CUDA_TRY(cudaMemcpyAsync(s->hsmall, s->small, sizeof(DevSmall), cudaMemcpyDeviceToHost, st));
   DMRG_CUDA_TRY(cudaStreamSynchronize(st));
-  return DMRG_OK;
+  return tc_error_status(s->plan);
 }
 
 dmrg_status project_col(dmrg_davidson_state* s, int col, bool fp64, cudaStream_t st) {
@@ -155,10 +156,13 @@ dmrg_status dmrg_davidson_step(dmrg_davidson_state* s, void* stream, int32_t* co
   const int64_t ldv = s->ldv, n = s->n;
   const int k = s->k, col = k - 1;
   const bool anchor = s->mixed && s->anchor_pending;
+  if (anchor) s->anchored = true;
   const bool fp64 = !s->mixed && s->plan->opt.prec == DMRG_PREC_FP64;
   DMRG_TRY(project_col(s, col, fp64 || anchor, st));
   s->anchor_pending = false;
-  DMRG_TRY(launch_overlap(s->vw, s->V, ldv, n, k, s->W + col * ldv, nullptr, s->small, col, st));
+  // after an FP64 anchor, the anchor row of B comes from the exact column W(:,0)
+  const double* w0 = (s->mixed && s->anchored) ? s->W : nullptr;
+  DMRG_TRY(launch_overlap(s->vw, s->V, ldv, n, k, s->W + col * ldv, nullptr, s->small, col, st, w0));
   DMRG_TRY(launch_jacobi(s->small, k, st));
   double* tcol = s->V + (int64_t)k * ldv;
   DMRG_TRY(launch_residual(s->vw, s->V, s->W, s->D, ldv, n, k, tcol, s->small, 0, st));

@@ -1,15 +1,905 @@
-// Low-precision (tensor-core) projection: placeholder until the tcgen05 path lands.
+// Low-precision projection on the 5th-generation tensor cores (tcgen05 + TMEM).
+//
+// Eq. 11 is evaluated in the same two stages as the FP64 path (stage 1: one GEMM per
+// record with two proper factors; stage 2: one GEMM per output segment whose K dimension
+// concatenates every record writing that segment), but every GEMM runs as
+//     D[128 x 128] (FP32, in TMEM) += A_tile[128 x K] . B_tile[128 x K]^T
+// with both operands K-major in shared memory.  Two arithmetics:
+//   TF32   : operands stored as FP32 rounded to TF32, one product per K step;
+//   BF16x3 : every operand stored as three BF16 planes x = x0 + x1 + x2 (24 significant
+//            bits); the six products x_i y_j with i + j <= 2 are accumulated in FP32.
+//
+// Operand tiles are "images": the exact shared-memory byte image of a 128-row x 128-byte
+// K-major tile in the 128-byte swizzled canonical layout (8-row atoms of 1024 bytes, the
+// 16-byte chunk c of row r stored at chunk c ^ (r % 8)), zero-padded to whole tiles, with
+// the planes of one (row tile, K tile) contiguous.  A tile therefore arrives in shared
+// memory with ONE bulk asynchronous copy (cp.async.bulk, the TMA engine) and no bounds
+// logic.  Operator blocks are packed once per plan (they are fixed during Davidson, Sec. 7);
+// the Davidson vector is packed per projection in two forms (A-form: rows = left index;
+// B-form: rows = right index); stage-1 epilogues write their results directly as images
+// for stage 2.  The record order "X B^T first" is computed transposed, U^T = B X^T, so that
+// every epilogue writes its accumulator rows as image rows.
+//
+// Kernel structure (persistent, one CTA per SM, 192 threads):
+//   warp 0     producer: bulk copies of A and B tiles into a ring of shared-memory stages
+//   warp 1     allocates 256 TMEM columns (two 128-column FP32 accumulators) and one lane
+//              issues tcgen05.mma; tcgen05.commit releases stages and publishes accumulators
+//   warps 2-5  epilogue: tcgen05.ld of the accumulator (warp w reads TMEM lanes
+//              32 (w % 4) .. + 31), then either an image of the result (stage 1) or FP64 Y
+//              plus the identity-identity term (stage 2)
+// Every mbarrier wait is bounded (2 s of %globaltimer); on a timeout the kernel records an
+// error code, stops issuing work, waits (bounded) for its own copies and MMAs, frees TMEM
+// and returns.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <map>
+#include <tuple>
+
 #include "internal.h"
 
 namespace dmrg {
 
-dmrg_status launch_project_tc(dmrg_plan*, dmrg_precision, const double*, double*, cudaStream_t) {
-  set_error("low-precision projection is not built yet");
-  return DMRG_ERR_UNSUPPORTED;
+struct TcSeg {
+  int64_t p_off, q_off;   // byte offsets of the first tile of the operand images
+  int32_t p_buf, q_buf;   // which image buffer
+  int32_t p_nkt, q_nkt;   // K tiles per row tile in each image
+  int32_t nkt;            // K tiles of this segment
+  int32_t pad_;
+};
+
+struct TcJob {
+  int32_t seg_begin, seg_end;
+  int32_t M, N;
+  int32_t out_fp64;       // 0: write an image (stage 1), 1: write FP64 Y (stage 2)
+  int32_t out_nkt;        // K tiles of the output image (stage 1)
+  int64_t out_off;        // byte offset of the output image, or element offset in Y
+  int64_t x_off;          // element offset of X for the identity-identity term
+  double axpy;
+};
+
+struct TcTile {
+  int32_t job, mt, nt, pad_;
+};
+
+struct PackJob {
+  int64_t src_off;        // element offset in the FP64 source
+  int64_t rs, cs;         // element (r, k) at src[src_off + r * rs + k * cs]
+  int64_t dst_off;        // byte offset of the image
+  int32_t R, K;
+  int32_t nkt;
+  int32_t src_space;      // 0: operator arena, 1: vector X
+  double scale;
+};
+
+struct PackChunk {
+  int32_t job, rt, kt, pad_;
+};
+
+enum TcBuf { TB_OPS = 0, TB_XA = 1, TB_XB = 2, TB_INTER = 3 };
+
+struct TcPlan {
+  dmrg_precision prec = DMRG_PREC_BF16X3;
+  int planes = 3, kt_elems = 64;
+  uint8_t* buf[4] = {nullptr, nullptr, nullptr, nullptr};
+  size_t buf_bytes[4] = {0, 0, 0, 0};
+  PackJob* d_xpack_jobs = nullptr;
+  PackChunk* d_xpack_chunks = nullptr;
+  int64_t n_xpack_chunks = 0;
+  TcJob* d_jobs = nullptr;
+  TcSeg* d_segs = nullptr;
+  TcTile* d_tiles1 = nullptr;
+  TcTile* d_tiles2 = nullptr;
+  int64_t ntiles1 = 0, ntiles2 = 0;
+  int* d_err = nullptr;   // device view of a mapped host word: kernel error codes
+  int* h_err = nullptr;
+  int sms = 0;
+};
+
+namespace tc {
+
+constexpr int kRows = 128;                 // rows of an image tile, M and N of the MMA
+constexpr int kChunk = 128 * 128;          // bytes of one plane of one image tile
+constexpr int kThreads = 192;
+constexpr int kTmemCols = 256;             // two 128-column FP32 accumulators
+constexpr uint64_t kWaitNs = 2000000000ull;
+
+// ---------------------------------------------------------------- PTX wrappers
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ uint64_t gtime() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait for the phase of the given parity.  Returns false on abort or timeout.
+__device__ __noinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag,
+                                       int* gerr, int code) {
+  uint64_t t0 = 0;
+  for (uint32_t i = 0;; ++i) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((i & 63) == 63) {
+      if (*abort_flag) return false;
+      const uint64_t t = gtime();
+      if (t0 == 0) {
+        t0 = t;
+      } else if (t - t0 > kWaitNs) {
+        *abort_flag = 1;
+        atomicCAS(gerr, 0, code);
+        return false;
+      }
+    }
+  }
+}
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes,
+                                         uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+      "l"(src), "r"(bytes), "r"(bar)
+      : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+               : "memory");
+}
+// Shared-memory matrix descriptor: K-major operand in the 128-byte swizzled layout;
+// 8-row core-matrix groups 1024 bytes apart (stride byte offset), descriptor version 1.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)(16u >> 4) << 16;
+  d |= (uint64_t)(1024u >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
+  return d;
+}
+// Instruction descriptor: FP32 accumulate, A/B format (1 = BF16 in kind::f16,
+// 2 = TF32 in kind::tf32), both K-major, N = 128, M = 128.
+template <bool TF32>
+__host__ __device__ constexpr uint32_t instr_desc() {
+  return (1u << 4) | ((TF32 ? 2u : 1u) << 7) | ((TF32 ? 2u : 1u) << 10) |
+         ((uint32_t)(kRows >> 3) << 17) | ((uint32_t)(kRows >> 4) << 24);
+}
+template <bool TF32>
+__device__ __forceinline__ void mma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                    uint32_t accumulate) {
+  if constexpr (TF32) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+        : "memory");
+  } else {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+        : "memory");
+  }
+}
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+        "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]),
+        "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]),
+        "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]),
+        "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]),
+        "=r"(v[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ float to_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+__device__ __forceinline__ uint32_t pack2_bf16(__nv_bfloat16 a, __nv_bfloat16 b) {
+  return (uint32_t)__bfloat16_as_ushort(a) | ((uint32_t)__bfloat16_as_ushort(b) << 16);
 }
 
-void destroy_tc(dmrg_plan*) {}
+// byte offset of the 16-byte group g of row r inside one plane of an image tile
+__host__ __device__ __forceinline__ uint32_t swz(int r, int g) {
+  return (uint32_t)((r >> 3) * 1024 + (r & 7) * 128 + ((g ^ (r & 7)) << 4));
+}
 
-bool tc_available(dmrg_precision) { return false; }
+// ---------------------------------------------------------------- packing kernel
+// One CTA packs one image tile (128 rows x 128 bytes x planes) of one pack job from FP64.
+template <int PLANES, bool TF32>
+__global__ void __launch_bounds__(256)
+pack_kernel(const PackChunk* __restrict__ chunks, const PackJob* __restrict__ jobs,
+            const double* __restrict__ arena, const double* __restrict__ x,
+            uint8_t* __restrict__ dst) {
+  constexpr int EPG = TF32 ? 4 : 8;  // elements per 16-byte group
+  constexpr int KT = TF32 ? 32 : 64;
+  const PackChunk ch = chunks[blockIdx.x];
+  const PackJob jb = jobs[ch.job];
+  const double* src = (jb.src_space ? x : arena) + jb.src_off;
+  uint8_t* base = dst + jb.dst_off + ((int64_t)ch.rt * jb.nkt + ch.kt) * PLANES * kChunk;
+  const bool kfast = jb.cs == 1;
+  for (int idx = threadIdx.x; idx < kRows * 8; idx += blockDim.x) {
+    int r, g;
+    if (kfast) { g = idx & 7; r = idx >> 3; }
+    else { r = idx & (kRows - 1); g = idx >> 7; }
+    const int64_t grow = (int64_t)ch.rt * kRows + r;
+    const int k0 = ch.kt * KT + g * EPG;
+    double v[EPG];
+#pragma unroll
+    for (int e = 0; e < EPG; ++e) {
+      const int k = k0 + e;
+      v[e] = (grow < jb.R && k < jb.K) ? jb.scale * src[grow * jb.rs + (int64_t)k * jb.cs] : 0.0;
+    }
+    const uint32_t off = swz(r, g);
+    if constexpr (TF32) {
+      uint4 q;
+      q.x = __float_as_uint(to_tf32((float)v[0]));
+      q.y = __float_as_uint(to_tf32((float)v[1]));
+      q.z = __float_as_uint(to_tf32((float)v[2]));
+      q.w = __float_as_uint(to_tf32((float)v[3]));
+      *reinterpret_cast<uint4*>(base + off) = q;
+    } else {
+      __nv_bfloat16 h[3][8];
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        const double a = v[e];
+        const __nv_bfloat16 h0 = __double2bfloat16(a);
+        const double r1 = a - (double)__bfloat162float(h0);
+        const __nv_bfloat16 h1 = __double2bfloat16(r1);
+        const double r2 = r1 - (double)__bfloat162float(h1);
+        h[0][e] = h0;
+        h[1][e] = h1;
+        h[2][e] = __double2bfloat16(r2);
+      }
+#pragma unroll
+      for (int p = 0; p < PLANES; ++p) {
+        uint4 q;
+        q.x = pack2_bf16(h[p][0], h[p][1]);
+        q.y = pack2_bf16(h[p][2], h[p][3]);
+        q.z = pack2_bf16(h[p][4], h[p][5]);
+        q.w = pack2_bf16(h[p][6], h[p][7]);
+        *reinterpret_cast<uint4*>(base + p * kChunk + off) = q;
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------- grouped GEMM kernel
+template <int PLANES, int STAGES, bool TF32>
+__global__ void __launch_bounds__(kThreads, 1)
+tc_gemm_kernel(const TcTile* __restrict__ tiles, int ntiles, const TcJob* __restrict__ jobs,
+               const TcSeg* __restrict__ segs, const uint8_t* __restrict__ b0,
+               const uint8_t* __restrict__ b1, const uint8_t* __restrict__ b2,
+               const uint8_t* __restrict__ b3, uint8_t* __restrict__ out_img,
+               double* __restrict__ y, const double* __restrict__ x, int* __restrict__ gerr) {
+  constexpr uint32_t kStageA = PLANES * kChunk;
+  constexpr uint32_t kStage = 2 * kStageA;
+  constexpr int KT = TF32 ? 32 : 64;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+  __shared__ __align__(8) uint64_t full_bar[STAGES], empty_bar[STAGES];
+  __shared__ __align__(8) uint64_t tfull_bar[2], tempty_bar[2], drain_bar;
+  __shared__ uint32_t tmem_slot;
+  __shared__ volatile int abort_flag;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(smem_u32(&full_bar[s]), 1);
+      mbar_init(smem_u32(&empty_bar[s]), 1);
+    }
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(smem_u32(&tfull_bar[a]), 1);
+      mbar_init(smem_u32(&tempty_bar[a]), 128);
+    }
+    mbar_init(smem_u32(&drain_bar), 1);
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&tmem_slot)),
+                 "r"(kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = tmem_slot;
+  const uint8_t* bufs[4] = {b0, b1, b2, b3};
+
+  if (warp == 0) {
+    // ------------------------------------------------ producer
+    if (lane == 0) {
+      int stage = 0;
+      uint32_t phase = 0;
+      int64_t issued = 0;
+      for (int t = blockIdx.x; t < ntiles && !abort_flag; t += gridDim.x) {
+        const TcTile tile = tiles[t];
+        const TcJob job = jobs[tile.job];
+        for (int si = job.seg_begin; si < job.seg_end && !abort_flag; ++si) {
+          const TcSeg sg = segs[si];
+          const uint8_t* P = bufs[sg.p_buf] + sg.p_off + (int64_t)tile.mt * sg.p_nkt * kStageA;
+          const uint8_t* Q = bufs[sg.q_buf] + sg.q_off + (int64_t)tile.nt * sg.q_nkt * kStageA;
+          for (int kt = 0; kt < sg.nkt; ++kt) {
+            if (!mbar_wait(smem_u32(&empty_bar[stage]), phase ^ 1, &abort_flag, gerr, 1)) break;
+            const uint32_t sa = smem_u32(smem + stage * kStage);
+            const uint32_t fb = smem_u32(&full_bar[stage]);
+            mbar_expect_tx(fb, kStage);
+            bulk_g2s(sa, P + (int64_t)kt * kStageA, kStageA, fb);
+            bulk_g2s(sa + kStageA, Q + (int64_t)kt * kStageA, kStageA, fb);
+            ++issued;
+            if (++stage == STAGES) { stage = 0; phase ^= 1; }
+          }
+        }
+      }
+      if (abort_flag) {
+        // wait (bounded) for the copies still in flight: the last min(issued, STAGES) loads
+        int s = stage;
+        uint32_t ph = phase;
+        for (int i = 0; i < STAGES && i < issued; ++i) {
+          if (--s < 0) { s = STAGES - 1; ph ^= 1; }
+          const uint64_t t0 = gtime();
+          while (!mbar_try_wait(smem_u32(&full_bar[s]), ph) && gtime() - t0 < kWaitNs) {}
+        }
+      }
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      int stage = 0;
+      uint32_t phase = 0;
+      int acc = 0;
+      uint32_t acc_phase = 0;
+      bool any = false;
+      constexpr uint32_t idesc = instr_desc<TF32>();
+      for (int t = blockIdx.x; t < ntiles && !abort_flag; t += gridDim.x) {
+        const TcJob job = jobs[tiles[t].job];
+        if (job.seg_begin == job.seg_end) continue;
+        if (!mbar_wait(smem_u32(&tempty_bar[acc]), acc_phase ^ 1, &abort_flag, gerr, 2)) break;
+        tc_fence_after();
+        const uint32_t d_tmem = tmem_base + (uint32_t)(acc * kRows);
+        uint32_t accumulate = 0;
+        for (int si = job.seg_begin; si < job.seg_end && !abort_flag; ++si) {
+          const int nkt = segs[si].nkt;
+          for (int kt = 0; kt < nkt; ++kt) {
+            if (!mbar_wait(smem_u32(&full_bar[stage]), phase, &abort_flag, gerr, 3)) break;
+            tc_fence_after();
+            const uint32_t sa = smem_u32(smem + stage * kStage);
+            const uint32_t sb = sa + kStageA;
+#pragma unroll
+            for (int pr = 0; pr < (PLANES == 3 ? 6 : 1); ++pr) {
+              // (pa, pb) in (0,0) (0,1) (1,0) (0,2) (1,1) (2,0)
+              const int pa = PLANES == 3 ? (pr == 0 ? 0 : pr == 1 ? 0 : pr == 2 ? 1 : pr == 3 ? 0 : pr == 4 ? 1 : 2) : 0;
+              const int pb = PLANES == 3 ? (pr == 0 ? 0 : pr == 1 ? 1 : pr == 2 ? 0 : pr == 3 ? 2 : pr == 4 ? 1 : 0) : 0;
+#pragma unroll
+              for (int kk = 0; kk < 4; ++kk) {
+                const uint64_t ad = smem_desc(sa + pa * kChunk + kk * 32);
+                const uint64_t bd = smem_desc(sb + pb * kChunk + kk * 32);
+                mma<TF32>(d_tmem, ad, bd, idesc, accumulate);
+                accumulate = 1;
+              }
+            }
+            tc_commit(smem_u32(&empty_bar[stage]));
+            any = true;
+            if (++stage == STAGES) { stage = 0; phase ^= 1; }
+          }
+        }
+        tc_commit(smem_u32(&tfull_bar[acc]));
+        acc ^= 1;
+        if (acc == 0) acc_phase ^= 1;
+      }
+      if (any) {
+        // all MMAs issued by this thread complete before TMEM is released
+        tc_commit(smem_u32(&drain_bar));
+        const uint64_t t0 = gtime();
+        while (!mbar_try_wait(smem_u32(&drain_bar), 0) && gtime() - t0 < kWaitNs) {}
+      }
+    }
+  } else {
+    // ------------------------------------------------ epilogue (warps 2..5)
+    const int quarter = warp & 3;
+    const int row = quarter * 32 + lane;
+    int acc = 0;
+    uint32_t acc_phase = 0;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+      const TcTile tile = tiles[t];
+      const TcJob job = jobs[tile.job];
+      const bool has = job.seg_begin < job.seg_end;
+      if (has) {
+        if (!mbar_wait(smem_u32(&tfull_bar[acc]), acc_phase, &abort_flag, gerr, 4)) break;
+        tc_fence_after();
+      }
+      const int64_t m = (int64_t)tile.mt * kRows + row;
+      for (int c0 = 0; c0 < kRows; c0 += 32) {
+        uint32_t v[32];
+        if (has) {
+          tmem_ld32(tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(acc * kRows + c0), v);
+        } else {
+#pragma unroll
+          for (int j = 0; j < 32; ++j) v[j] = 0u;
+        }
+        const int n0 = tile.nt * kRows + c0;
+        if (job.out_fp64) {
+          if (m < job.M) {
+            double* yr = y + job.out_off + m * job.N;
+            const double* xr = x + job.x_off + m * job.N;
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+              const int n = n0 + j;
+              if (n < job.N) {
+                double val = (double)__uint_as_float(v[j]);
+                if (job.axpy != 0.0) val = fma(job.axpy, xr[n], val);
+                yr[n] = val;
+              }
+            }
+          }
+        } else {
+          const int kt = n0 / KT;
+          if (kt < job.out_nkt) {
+            uint8_t* tb = out_img + job.out_off + ((int64_t)tile.mt * job.out_nkt + kt) * PLANES * kChunk;
+            if constexpr (TF32) {
+#pragma unroll
+              for (int g = 0; g < 8; ++g) {
+                uint4 q;
+                q.x = __float_as_uint(to_tf32(__uint_as_float(v[4 * g + 0])));
+                q.y = __float_as_uint(to_tf32(__uint_as_float(v[4 * g + 1])));
+                q.z = __float_as_uint(to_tf32(__uint_as_float(v[4 * g + 2])));
+                q.w = __float_as_uint(to_tf32(__uint_as_float(v[4 * g + 3])));
+                *reinterpret_cast<uint4*>(tb + swz(row, g)) = q;
+              }
+            } else {
+              const int gbase = (n0 % KT) / 8;
+#pragma unroll
+              for (int g = 0; g < 4; ++g) {
+                uint32_t w0[4], w1[4], w2[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                  __nv_bfloat16 h[2][3];
+#pragma unroll
+                  for (int u = 0; u < 2; ++u) {
+                    const float f = __uint_as_float(v[8 * g + 2 * e + u]);
+                    const __nv_bfloat16 h0 = __float2bfloat16_rn(f);
+                    const float r1 = f - __bfloat162float(h0);
+                    const __nv_bfloat16 h1 = __float2bfloat16_rn(r1);
+                    const float r2 = r1 - __bfloat162float(h1);
+                    h[u][0] = h0;
+                    h[u][1] = h1;
+                    h[u][2] = __float2bfloat16_rn(r2);
+                  }
+                  w0[e] = pack2_bf16(h[0][0], h[1][0]);
+                  w1[e] = pack2_bf16(h[0][1], h[1][1]);
+                  w2[e] = pack2_bf16(h[0][2], h[1][2]);
+                }
+                const uint32_t off = swz(row, gbase + g);
+                *reinterpret_cast<uint4*>(tb + off) = make_uint4(w0[0], w0[1], w0[2], w0[3]);
+                *reinterpret_cast<uint4*>(tb + kChunk + off) = make_uint4(w1[0], w1[1], w1[2], w1[3]);
+                *reinterpret_cast<uint4*>(tb + 2 * kChunk + off) = make_uint4(w2[0], w2[1], w2[2], w2[3]);
+              }
+            }
+          }
+        }
+      }
+      if (has) {
+        tc_fence_before();
+        mbar_arrive(smem_u32(&tempty_bar[acc]));
+        acc ^= 1;
+        if (acc == 0) acc_phase ^= 1;
+      }
+    }
+  }
+  __syncwarp();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 1) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
+                 "r"(kTmemCols)
+                 : "memory");
+  }
+}
+
+template <int PLANES, int STAGES, bool TF32>
+constexpr size_t smem_bytes() {
+  return (size_t)STAGES * 2 * PLANES * kChunk + 1024;
+}
+
+}  // namespace tc
+
+// ======================================================================== host side
+namespace {
+
+using tc::kChunk;
+using tc::kRows;
+
+int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+
+struct ImageAlloc {
+  int64_t bytes = 0;
+  int64_t add(int64_t rows, int64_t K, int planes, int kt_elems, int* nkt_out) {
+    const int nrt = ceil_div(rows, kRows), nkt = ceil_div(K, kt_elems);
+    *nkt_out = nkt;
+    const int64_t off = bytes;
+    bytes += (int64_t)nrt * nkt * planes * kChunk;
+    return off;
+  }
+};
+
+template <typename T>
+dmrg_status upload_vec(T** dst, const std::vector<T>& v, cudaStream_t st) {
+  *dst = nullptr;
+  if (v.empty()) return DMRG_OK;
+  DMRG_CUDA_TRY(cudaMalloc((void**)dst, sizeof(T) * v.size()));
+  DMRG_CUDA_TRY(cudaMemcpyAsync(*dst, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice, st));
+  return DMRG_OK;
+}
+
+void free_tc(TcPlan* t) {
+  if (!t) return;
+  for (int b = 0; b < 4; ++b)
+    if (b != TB_XB) cudaFree(t->buf[b]);
+  if (t->h_err) cudaFreeHost(t->h_err);
+  cudaFree(t->d_xpack_jobs);
+  cudaFree(t->d_xpack_chunks);
+  cudaFree(t->d_jobs);
+  cudaFree(t->d_segs);
+  cudaFree(t->d_tiles1);
+  cudaFree(t->d_tiles2);
+  delete t;
+}
+
+template <int PLANES, bool TF32>
+dmrg_status launch_pack(const std::vector<PackChunk>& chunks, const PackChunk* d_chunks,
+                        const PackJob* d_jobs, const double* arena, const double* x,
+                        uint8_t* dst, cudaStream_t st) {
+  if (chunks.empty()) return DMRG_OK;
+  tc::pack_kernel<PLANES, TF32><<<(unsigned)chunks.size(), 256, 0, st>>>(d_chunks, d_jobs, arena, x, dst);
+  DMRG_LAUNCH_CHECK();
+  return DMRG_OK;
+}
+
+dmrg_status build_tc(dmrg_plan* p, dmrg_precision prec, cudaStream_t st, TcPlan** out) {
+  TcPlan* t = new TcPlan();
+  t->prec = prec;
+  const bool tf32 = prec == DMRG_PREC_TF32;
+  t->planes = tf32 ? 1 : 3;
+  t->kt_elems = tf32 ? 32 : 64;
+  const int planes = t->planes, KT = t->kt_elems;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&t->sms, cudaDevAttrMultiProcessorCount, dev);
+  auto fail = [&](dmrg_status s) { free_tc(t); return s; };
+
+  // ---- operator images, keyed by (side, op, block, scale)
+  ImageAlloc ops_alloc;
+  std::vector<PackJob> op_jobs;
+  std::map<std::tuple<int, int, int, double>, std::pair<int64_t, int>> op_img;  // -> (off, nkt)
+  auto op_image = [&](int side, int op, int blk, double scale) -> std::pair<int64_t, int> {
+    auto key = std::make_tuple(side, op, blk, scale);
+    auto it = op_img.find(key);
+    if (it != op_img.end()) return it->second;
+    const HostBlock& hb = side == 0 ? p->opsL[op][blk] : p->opsR[op][blk];
+    int nkt = 0;
+    const int64_t off = ops_alloc.add(hb.rows, hb.cols, planes, KT, &nkt);
+    PackJob j{};
+    j.src_off = hb.arena_off;
+    j.rs = hb.cols;
+    j.cs = 1;
+    j.dst_off = off;
+    j.R = (int32_t)hb.rows;
+    j.K = (int32_t)hb.cols;
+    j.nkt = nkt;
+    j.src_space = 0;
+    j.scale = scale;
+    op_jobs.push_back(j);
+    op_img[key] = {off, nkt};
+    return {off, nkt};
+  };
+
+  // ---- vector images (A-form rows = left index, B-form rows = right index)
+  const int npairs = (int)p->pair_i.size();
+  ImageAlloc xa_alloc;  // both forms share one buffer: A-form tiles, then B-form tiles
+  std::vector<PackJob> x_jobs;
+  std::vector<std::pair<int64_t, int>> xa(npairs), xb(npairs);
+  for (int q = 0; q < npairs; ++q) {
+    const int64_t di = p->dimL[p->pair_i[q]], dk = p->dimR[p->pair_k[q]];
+    int nkt = 0;
+    int64_t off = xa_alloc.add(di, dk, planes, KT, &nkt);
+    xa[q] = {off, nkt};
+    if (di * dk > 0) {
+      PackJob j{p->pair_off[q], dk, 1, off, (int32_t)di, (int32_t)dk, nkt, 1, 1.0};
+      j.dst_off = off;
+      x_jobs.push_back(j);
+    }
+    off = xa_alloc.add(dk, di, planes, KT, &nkt);
+    xb[q] = {off, nkt};
+    if (di * dk > 0) {
+      PackJob j{p->pair_off[q], 1, dk, off, (int32_t)dk, (int32_t)di, nkt, 1, 1.0};
+      x_jobs.push_back(j);
+    }
+  }
+
+  // ---- jobs
+  ImageAlloc inter_alloc;
+  std::vector<TcJob> jobs;
+  std::vector<TcSeg> segs;
+  std::vector<TcTile> tiles1, tiles2;
+  std::vector<std::pair<int64_t, int>> inter(p->records.size(), {-1, 0});
+  std::vector<std::pair<int64_t, int>> order1, order2;
+  auto seg = [](int pbuf, std::pair<int64_t, int> P, int qbuf, std::pair<int64_t, int> Q, int nkt) {
+    TcSeg s{};
+    s.p_off = P.first;
+    s.p_nkt = P.second;
+    s.p_buf = pbuf;
+    s.q_off = Q.first;
+    s.q_nkt = Q.second;
+    s.q_buf = qbuf;
+    s.nkt = nkt;
+    return s;
+  };
+  for (size_t ri = 0; ri < p->records.size(); ++ri) {
+    const Record& r = p->records[ri];
+    if (r.a_blk < 0 || r.b_blk < 0) continue;
+    const int a_op = p->terms[r.term].a_op, b_op = p->terms[r.term].b_op;
+    TcJob job{};
+    job.out_fp64 = 0;
+    job.axpy = 0.0;
+    job.seg_begin = (int32_t)segs.size();
+    int nkt_out = 0;
+    if (r.a_first) {  // T [dj x dk] = A [dj x di] X [di x dk]
+      job.M = (int32_t)r.dj;
+      job.N = (int32_t)r.dk;
+      const int64_t off = inter_alloc.add(r.dj, r.dk, planes, KT, &nkt_out);
+      job.out_off = off;
+      job.out_nkt = nkt_out;
+      inter[ri] = {off, nkt_out};
+      if (r.di > 0)
+        segs.push_back(seg(TB_OPS, op_image(0, a_op, r.a_blk, 1.0), TB_XB, xb[r.pin], ceil_div(r.di, KT)));
+    } else {          // U^T [dl x di] = (coef B) [dl x dk] X^T [dk x di]
+      job.M = (int32_t)r.dl;
+      job.N = (int32_t)r.di;
+      const int64_t off = inter_alloc.add(r.dl, r.di, planes, KT, &nkt_out);
+      job.out_off = off;
+      job.out_nkt = nkt_out;
+      inter[ri] = {off, nkt_out};
+      if (r.dk > 0)
+        segs.push_back(seg(TB_OPS, op_image(1, b_op, r.b_blk, r.coef), TB_XA, xa[r.pin], ceil_div(r.dk, KT)));
+    }
+    job.seg_end = (int32_t)segs.size();
+    if (job.M > 0 && job.N > 0) {
+      int64_t cost = 0;
+      for (int s = job.seg_begin; s < job.seg_end; ++s) cost += segs[s].nkt;
+      order1.push_back({cost, (int)jobs.size()});
+    }
+    jobs.push_back(job);
+  }
+  std::vector<std::vector<int>> by_out(npairs);
+  for (size_t ri = 0; ri < p->records.size(); ++ri) by_out[p->records[ri].pout].push_back((int)ri);
+  for (int q = 0; q < npairs; ++q) {
+    const int i = p->pair_i[q], k = p->pair_k[q];
+    TcJob job{};
+    job.M = (int32_t)p->dimL[i];
+    job.N = (int32_t)p->dimR[k];
+    job.out_fp64 = 1;
+    job.out_off = p->pair_off[q];
+    job.x_off = p->pair_off[q];
+    job.axpy = 0.0;
+    job.seg_begin = (int32_t)segs.size();
+    for (int ri : by_out[q]) {
+      const Record& r = p->records[ri];
+      const int a_op = p->terms[r.term].a_op, b_op = p->terms[r.term].b_op;
+      if (r.a_blk >= 0 && r.b_blk >= 0) {
+        if (r.a_first) {
+          if (r.dk > 0)
+            segs.push_back(seg(TB_INTER, inter[ri], TB_OPS, op_image(1, b_op, r.b_blk, r.coef), ceil_div(r.dk, KT)));
+        } else {
+          if (r.di > 0)
+            segs.push_back(seg(TB_OPS, op_image(0, a_op, r.a_blk, 1.0), TB_INTER, inter[ri], ceil_div(r.di, KT)));
+        }
+      } else if (r.a_blk >= 0) {   // (coef A) X_{il}, k == l
+        if (r.di > 0)
+          segs.push_back(seg(TB_OPS, op_image(0, a_op, r.a_blk, r.coef), TB_XB, xb[r.pin], ceil_div(r.di, KT)));
+      } else if (r.b_blk >= 0) {   // X_{jk} (coef B)^T, i == j
+        if (r.dk > 0)
+          segs.push_back(seg(TB_XA, xa[r.pin], TB_OPS, op_image(1, b_op, r.b_blk, r.coef), ceil_div(r.dk, KT)));
+      } else {
+        job.axpy += r.coef;
+      }
+    }
+    job.seg_end = (int32_t)segs.size();
+    if (job.M > 0 && job.N > 0) {
+      int64_t cost = 0;
+      for (int s = job.seg_begin; s < job.seg_end; ++s) cost += segs[s].nkt;
+      order2.push_back({cost, (int)jobs.size()});
+    }
+    jobs.push_back(job);
+  }
+  auto by_cost = [](const std::pair<int64_t, int>& a, const std::pair<int64_t, int>& b) {
+    return a.first != b.first ? a.first > b.first : a.second < b.second;
+  };
+  std::stable_sort(order1.begin(), order1.end(), by_cost);
+  std::stable_sort(order2.begin(), order2.end(), by_cost);
+  for (auto& pr : order1) {
+    const TcJob& j = jobs[pr.second];
+    for (int mt = 0; mt < ceil_div(j.M, kRows); ++mt)
+      for (int nt = 0; nt < ceil_div(j.N, kRows); ++nt) tiles1.push_back(TcTile{pr.second, mt, nt, 0});
+  }
+  for (auto& pr : order2) {
+    const TcJob& j = jobs[pr.second];
+    for (int mt = 0; mt < ceil_div(j.M, kRows); ++mt)
+      for (int nt = 0; nt < ceil_div(j.N, kRows); ++nt) tiles2.push_back(TcTile{pr.second, mt, nt, 0});
+  }
+  // stage-1 N tiles read Q image row tiles; stage-2 image K tiles must cover the segment
+  // (image row tiles = ceil(rows / 128) >= tiles; image K tiles = nkt): checked here
+  for (const TcSeg& s : segs) {
+    if (s.nkt > s.p_nkt || s.nkt > s.q_nkt) {
+      set_error("internal: segment K tiles exceed its operand images");
+      return fail(DMRG_ERR_SHAPE);
+    }
+  }
+
+  // ---- device buffers
+  t->buf_bytes[TB_OPS] = (size_t)ops_alloc.bytes;
+  t->buf_bytes[TB_XA] = (size_t)xa_alloc.bytes;
+  t->buf_bytes[TB_INTER] = (size_t)inter_alloc.bytes;
+  for (int b = 0; b < 4; ++b) {
+    if (t->buf_bytes[b] == 0) continue;
+    if (cudaMalloc((void**)&t->buf[b], t->buf_bytes[b]) != cudaSuccess) {
+      cudaGetLastError();
+      set_error("cudaMalloc of %zu bytes for tensor-core operand images failed", t->buf_bytes[b]);
+      return fail(DMRG_ERR_OOM);
+    }
+    p->device_bytes += t->buf_bytes[b];
+  }
+  t->buf[TB_XB] = t->buf[TB_XA];  // alias: B-form offsets follow the A-form tiles
+  if (t->buf[TB_INTER]) {
+    // intermediate tiles beyond the written rows stay zero
+    DMRG_CUDA_TRY(cudaMemsetAsync(t->buf[TB_INTER], 0, t->buf_bytes[TB_INTER], st));
+  }
+  std::vector<PackChunk> op_chunks, x_chunks;
+  for (size_t jb = 0; jb < op_jobs.size(); ++jb)
+    for (int rt = 0; rt < ceil_div(op_jobs[jb].R, kRows); ++rt)
+      for (int kt = 0; kt < op_jobs[jb].nkt; ++kt) op_chunks.push_back(PackChunk{(int32_t)jb, rt, kt, 0});
+  for (size_t jb = 0; jb < x_jobs.size(); ++jb)
+    for (int rt = 0; rt < ceil_div(x_jobs[jb].R, kRows); ++rt)
+      for (int kt = 0; kt < x_jobs[jb].nkt; ++kt) x_chunks.push_back(PackChunk{(int32_t)jb, rt, kt, 0});
+  PackJob* d_opj = nullptr;
+  PackChunk* d_opc = nullptr;
+  dmrg_status s;
+  if ((s = upload_vec(&d_opj, op_jobs, st)) != DMRG_OK) return fail(s);
+  if ((s = upload_vec(&d_opc, op_chunks, st)) != DMRG_OK) return fail(s);
+  if (tf32) s = launch_pack<1, true>(op_chunks, d_opc, d_opj, p->arena, nullptr, t->buf[TB_OPS], st);
+  else s = launch_pack<3, false>(op_chunks, d_opc, d_opj, p->arena, nullptr, t->buf[TB_OPS], st);
+  cudaStreamSynchronize(st);
+  cudaFree(d_opj);
+  cudaFree(d_opc);
+  if (s != DMRG_OK) return fail(s);
+  if ((s = upload_vec(&t->d_xpack_jobs, x_jobs, st)) != DMRG_OK) return fail(s);
+  if ((s = upload_vec(&t->d_xpack_chunks, x_chunks, st)) != DMRG_OK) return fail(s);
+  t->n_xpack_chunks = (int64_t)x_chunks.size();
+  if ((s = upload_vec(&t->d_jobs, jobs, st)) != DMRG_OK) return fail(s);
+  if ((s = upload_vec(&t->d_segs, segs, st)) != DMRG_OK) return fail(s);
+  if ((s = upload_vec(&t->d_tiles1, tiles1, st)) != DMRG_OK) return fail(s);
+  if ((s = upload_vec(&t->d_tiles2, tiles2, st)) != DMRG_OK) return fail(s);
+  t->ntiles1 = (int64_t)tiles1.size();
+  t->ntiles2 = (int64_t)tiles2.size();
+  if (cudaHostAlloc((void**)&t->h_err, sizeof(int), cudaHostAllocMapped) != cudaSuccess ||
+      cudaHostGetDevicePointer((void**)&t->d_err, t->h_err, 0) != cudaSuccess) {
+    cudaGetLastError();
+    set_error("mapped host allocation for the kernel error word failed");
+    return fail(DMRG_ERR_OOM);
+  }
+  *t->h_err = 0;
+  DMRG_CUDA_TRY(cudaStreamSynchronize(st));
+  *out = t;
+  return DMRG_OK;
+}
+
+template <int PLANES, int STAGES, bool TF32>
+dmrg_status run_tc(dmrg_plan* p, TcPlan* t, const double* x, double* y, cudaStream_t st) {
+  constexpr size_t smem = tc::smem_bytes<PLANES, STAGES, TF32>();
+  static bool configured[64] = {false};
+  int dev = 0;
+  DMRG_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev >= 0 && dev < 64 && !configured[dev]) {
+    DMRG_CUDA_TRY(cudaFuncSetAttribute(tc::tc_gemm_kernel<PLANES, STAGES, TF32>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    configured[dev] = true;
+  }
+  if (*t->h_err != 0) {
+    set_error("tensor-core projection kernel reported error %d (a bounded wait timed out)",
+              *t->h_err);
+    return DMRG_ERR_CUDA;
+  }
+  if (t->n_xpack_chunks > 0) {  // X -> A-form and B-form images
+    tc::pack_kernel<PLANES, TF32><<<(unsigned)t->n_xpack_chunks, 256, 0, st>>>(
+        t->d_xpack_chunks, t->d_xpack_jobs, p->arena, x, t->buf[TB_XA]);
+    DMRG_LAUNCH_CHECK();
+  }
+  if (t->ntiles1 > 0) {
+    const int grid = (int)std::min<int64_t>(t->ntiles1, t->sms);
+    tc::tc_gemm_kernel<PLANES, STAGES, TF32><<<grid, tc::kThreads, smem, st>>>(
+        t->d_tiles1, (int)t->ntiles1, t->d_jobs, t->d_segs, t->buf[TB_OPS], t->buf[TB_XA],
+        t->buf[TB_XB], nullptr, t->buf[TB_INTER], y, x, t->d_err);
+    DMRG_LAUNCH_CHECK();
+  }
+  if (t->ntiles2 > 0) {
+    const int grid = (int)std::min<int64_t>(t->ntiles2, t->sms);
+    tc::tc_gemm_kernel<PLANES, STAGES, TF32><<<grid, tc::kThreads, smem, st>>>(
+        t->d_tiles2, (int)t->ntiles2, t->d_jobs, t->d_segs, t->buf[TB_OPS], t->buf[TB_XA],
+        t->buf[TB_XB], t->buf[TB_INTER], nullptr, y, x, t->d_err);
+    DMRG_LAUNCH_CHECK();
+  }
+  return DMRG_OK;
+}
+
+}  // namespace
+
+bool tc_available(dmrg_precision prec) {
+  return prec == DMRG_PREC_TF32 || prec == DMRG_PREC_BF16X3;
+}
+
+void destroy_tc(dmrg_plan* p) {
+  if (!p) return;
+  for (auto& t : p->tc) {
+    free_tc(t);
+    t = nullptr;
+  }
+}
+
+dmrg_status tc_error_status(dmrg_plan* p) {
+  for (TcPlan* t : p->tc) {
+    if (t && t->h_err && *t->h_err != 0) {
+      set_error("tensor-core projection kernel reported error %d (a bounded wait timed out)",
+                *t->h_err);
+      return DMRG_ERR_CUDA;
+    }
+  }
+  return DMRG_OK;
+}
+
+dmrg_status launch_project_tc(dmrg_plan* p, dmrg_precision prec, const double* x, double* y,
+                              cudaStream_t st) {
+  const int slot = prec == DMRG_PREC_TF32 ? 0 : 1;
+  if (!p->tc[slot]) {
+    TcPlan* t = nullptr;
+    DMRG_TRY(build_tc(p, prec, st, &t));
+    p->tc[slot] = t;
+  }
+  TcPlan* t = p->tc[slot];
+  if (prec == DMRG_PREC_TF32) return run_tc<1, 6, true>(p, t, x, y, st);
+  return run_tc<3, 2, false>(p, t, x, y, st);
+}
 
 }  // namespace dmrg

@@ -132,7 +132,7 @@ struct dmrg_plan {
   int64_t ntiles1 = 0, ntiles2 = 0;
   size_t device_bytes = 0;
 
-  dmrg::TcPlan* tc = nullptr;     // built on first low-precision use
+  dmrg::TcPlan* tc[2] = {nullptr, nullptr};  // TF32, BF16x3; built on first use
 };
 
 namespace dmrg {
@@ -144,6 +144,7 @@ dmrg_status launch_project_tc(dmrg_plan* plan, dmrg_precision prec, const double
                               double* y, cudaStream_t stream);
 void destroy_tc(dmrg_plan* plan);
 bool tc_available(dmrg_precision prec);
+dmrg_status tc_error_status(dmrg_plan* plan);
 
 // vec.cu -- Davidson vector kernels
 constexpr int KMAX = DMRG_MAX_SUBSPACE;
@@ -175,7 +176,7 @@ void vec_work_destroy(VecWork* w);
 // column Bcol of small->B.
 dmrg_status launch_overlap(const VecWork& w, const double* V, int64_t ldv, int64_t n,
                            int k, const double* vec, double* s_out, DevSmall* small,
-                           int Bcol, cudaStream_t st);
+                           int Bcol, cudaStream_t st, const double* w0 = nullptr);
 dmrg_status launch_jacobi(DevSmall* small, int k, cudaStream_t st);
 // r = W y - lambda V y, t = r / (lambda - D) (mode 0) or t = r (mode 1) into tcol;
 // reductions: rnorm2, s[0] = V^T t, tnorm2_before.

@@ -94,33 +94,47 @@ __device__ __forceinline__ double2 ld2cg(const double* p) {
 }
 
 // ---------------------------------------------------------------- overlap  s = V^T w
+// With w0 != NULL (mixed precision with an FP64 anchor in column 0) the coupling between
+// the anchor and column Bcol is taken from the exact anchor projection, v_Bcol . W(:,0),
+// instead of v_0 . W(:,Bcol), whose low-precision error would not shrink with the
+// correction.
 __global__ void __launch_bounds__(kVecThreads)
 overlap_kernel(const double* __restrict__ V, int64_t ldv, int64_t n2, int k,
-               const double* __restrict__ w, double* __restrict__ partials,
-               unsigned int* counter, double* s_out, DevSmall* small, int Bcol) {
-  double acc[KMAX];
+               const double* __restrict__ w, const double* __restrict__ w0,
+               double* __restrict__ partials, unsigned int* counter, double* s_out,
+               DevSmall* small, int Bcol) {
+  double acc[KMAX + 1];
 #pragma unroll
-  for (int j = 0; j < KMAX; ++j) acc[j] = 0.0;
+  for (int j = 0; j < KMAX + 1; ++j) acc[j] = 0.0;
+  const bool anchored = w0 != nullptr && Bcol > 0;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n2;
        e += (int64_t)gridDim.x * blockDim.x) {
     const double2 wv = ld2cg(w + 2 * e);
+    double2 vlast = make_double2(0.0, 0.0);
 #pragma unroll
     for (int j = 0; j < KMAX; ++j) {
       if (j < k) {
         const double2 v = ld2(V + j * ldv + 2 * e);
         acc[j] = fma(v.x, wv.x, fma(v.y, wv.y, acc[j]));
+        if (j == k - 1) vlast = v;
       }
     }
+    if (anchored) {
+      const double2 a = ld2(w0 + 2 * e);
+      acc[KMAX] = fma(vlast.x, a.x, fma(vlast.y, a.y, acc[KMAX]));
+    }
   }
-  block_partials<KMAX, 0>(acc, k, partials);
+  block_partials<KMAX, 1>(acc, k, partials);
   if (Ticket::last_block(counter)) {
-    __shared__ double tot[KMAX];
-    final_sums(partials, k, tot);
+    __shared__ double tot[KMAX + 1];
+    final_sums(partials, k + 1, tot);
     for (int j = threadIdx.x; j < k; j += blockDim.x) {
       if (s_out) s_out[j] = tot[j];
       if (Bcol >= 0) {
-        small->B[j * KMAX + Bcol] = tot[j];
-        small->B[Bcol * KMAX + j] = tot[j];
+        double v = tot[j];
+        if (anchored && j == 0) v = tot[k];
+        small->B[j * KMAX + Bcol] = v;
+        small->B[Bcol * KMAX + j] = v;
       }
     }
     if (threadIdx.x == 0) *counter = 0u;
@@ -480,8 +494,8 @@ void vec_work_destroy(VecWork* w) {
 
 dmrg_status launch_overlap(const VecWork& w, const double* V, int64_t ldv, int64_t n, int k,
                            const double* vec, double* s_out, DevSmall* small, int Bcol,
-                           cudaStream_t st) {
-  overlap_kernel<<<w.grid, kVecThreads, 0, st>>>(V, ldv, (n + 1) / 2, k, vec, w.partials,
+                           cudaStream_t st, const double* w0) {
+  overlap_kernel<<<w.grid, kVecThreads, 0, st>>>(V, ldv, (n + 1) / 2, k, vec, w0, w.partials,
                                                  w.counter, s_out, small, Bcol);
   DMRG_LAUNCH_CHECK();
   return DMRG_OK;

@@ -1,0 +1,97 @@
+"""Tensor-core (tcgen05) projections and the mixed-precision Davidson against the FP64
+oracle, on the GPU.
+
+Tolerances, derived from the arithmetic: BF16x3 keeps 24 significant bits per operand
+(dropped products are below 2^-24 relative) and accumulates in FP32, whose rounding grows
+with the accumulation length; two chained stages with K up to ~900 give a bound of a few
+hundred units of u = 2^-24 relative to max|y|: 2e-5.  TF32 keeps 11 significant bits
+(u = 2^-11 ~ 4.9e-4 per operand) on the small problems tested: 5e-3.
+The mixed Davidson ends only on an FP64 residual, so its energy meets |dE| <= 1e-10.
+"""
+import numpy as np
+import pytest
+
+from dmrg_inputs import warmup
+from oracle import davidson as odav
+from oracle import projection as oproj
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import __graft_entry__  # noqa: E402
+
+__graft_entry__.build()
+from paper_1309_5571_gb300 import Plan, capi  # noqa: E402
+
+from test_gpu_parity import PROBLEMS, problem, rel_err, cuda  # noqa: E402
+
+TOL = {"bf16x3": 2e-5, "tf32": 5e-3}
+E_TOL = 1e-10
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "tf32"])
+@pytest.mark.parametrize("name", list(PROBLEMS))
+def test_projection_tensor_core_matches_oracle(name, prec):
+    sb = problem(name)
+    plan = Plan(sb, prec=prec)
+    for seed in (0, 1):
+        x = np.random.default_rng(seed).standard_normal(sb.n)
+        y = plan.project(cuda(x)).cpu().numpy()
+        y_ref = oproj.project_blocks(sb, x)
+        assert rel_err(y, y_ref) <= TOL[prec], (name, prec, rel_err(y, y_ref))
+
+
+def test_projection_tensor_core_repeatable():
+    sb = problem("hub_L8_m40")
+    plan = Plan(sb, prec="bf16x3")
+    x = cuda(np.random.default_rng(3).standard_normal(sb.n))
+    y1 = plan.project(x).cpu().numpy()
+    y2 = plan.project(x).cpu().numpy()
+    np.testing.assert_array_equal(y1, y2)
+
+
+@pytest.mark.parametrize("name", ["heis_L16_m64", "hub_L8_m40", "hub_quarter_L12_m48", "ragged"])
+@pytest.mark.parametrize("prec", ["bf16x3", "tf32"])
+def test_mixed_davidson_matches_oracle(name, prec):
+    sb = problem(name)
+    x0 = warmup.start_vector(sb.n, seed=0)
+    plan = Plan(sb, prec=prec)
+    x, info = plan.solve(cuda(x0))
+    x = x.cpu().numpy()
+    lam, xo, oinfo = odav.davidson(lambda v: oproj.project_blocks(sb, v), oproj.diagonal(sb), x0)
+    assert info["converged"]
+    assert abs(info["energy"] - lam) <= E_TOL, (info, lam)
+    assert abs(x @ xo) / (np.linalg.norm(x) * np.linalg.norm(xo)) >= 1 - 1e-8
+    r = oproj.project_blocks(sb, x) - info["energy"] * x
+    assert np.linalg.norm(r) <= 1.5e-10
+    assert info["fp64_projections"] >= 1 and info["projections"] >= 1
+
+
+@pytest.fixture(scope="module")
+def hub_L64_m2048():
+    return warmup.workload("hub_L64_m2048")
+
+
+def test_full_size_projection_hubbard_m2048_bf16x3(hub_L64_m2048):
+    sb = hub_L64_m2048
+    plan = Plan(sb, prec="bf16x3")
+    x = warmup.start_vector(sb.n, seed=5)
+    y = plan.project(cuda(x)).cpu().numpy()
+    y_ref = oproj.project_blocks(sb, x)
+    assert rel_err(y, y_ref) <= TOL["bf16x3"]
+    y64 = plan.project(cuda(x), prec="fp64").cpu().numpy()
+    assert rel_err(y64, y_ref) <= 1e-12
+
+
+def test_full_size_mixed_solve_hubbard_m2048_properties(hub_L64_m2048):
+    sb = hub_L64_m2048
+    plan = Plan(sb, prec="bf16x3")
+    x, info = plan.solve(cuda(warmup.start_vector(sb.n, seed=0)))
+    x = x.cpu().numpy()
+    Hx = oproj.project_blocks(sb, x)
+    rq = float(x @ Hx) / float(x @ x)
+    assert abs(rq - info["energy"]) <= E_TOL
+    assert np.linalg.norm(Hx - info["energy"] * x) <= 1.5e-10
