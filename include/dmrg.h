@@ -110,8 +110,9 @@ typedef struct {
   int32_t max_iter;      /* Davidson iterations before DMRG_ERR_NOT_CONVERGED (1000)      */
   int32_t max_subspace;  /* basis size that triggers a restart, <= 24 (20, Sec. 6.1)     */
   int32_t fp64_refine;   /* low-precision modes: re-anchor with FP64 projections (1)      */
-  double refine_ratio;   /* re-anchor when the low-precision residual has fallen by this
-                            factor below the last FP64 residual (1e-3)                   */
+  double refine_ratio;   /* if > 0, also re-anchor when the low-precision residual has
+                            fallen by this factor below the last FP64 residual (0: only
+                            the adaptive floor test and the subspace limit re-anchor)     */
 } dmrg_options;
 
 typedef struct {
@@ -121,6 +122,7 @@ typedef struct {
   int32_t projections;      /* projections in the plan's precision                        */
   int32_t fp64_projections; /* FP64 projections (all of them in FP64 mode)                */
   int32_t restarts;         /* basis collapses (subspace limit or re-anchoring)           */
+  int32_t small_eig_sweeps; /* Jacobi sweeps of the projected eigenproblem, all iterations */
 } dmrg_solve_info;
 
 typedef struct {

@@ -20,7 +20,10 @@ Readings where the paper is silent (Sec. 6 names the Sadkane-Sidje variant only)
   below 1e-10 of the norm before, the raw residual r is used instead, and if that also
   collapses the iteration reports a breakdown;
 * subspace limit: 20 columns (Sec. 6.1); when the basis is full, it is collapsed to the
-  current Ritz vector x with W replaced by W y, before the new direction is added;
+  current Ritz vector x (restart_keep=1, the default, as on the GPU) or to x and the
+  previous iteration's Ritz vector orthogonalised against it (restart_keep=2), with W
+  replaced by the same
+  combinations of its columns, before the new direction is added;
 * convergence: ||r||_2 <= tol on a normalised x; at most ``max_iter`` iterations.
 """
 from __future__ import annotations
@@ -45,7 +48,7 @@ def _cgs2(V: np.ndarray, t: np.ndarray) -> np.ndarray:
 
 
 def davidson(matvec, D: np.ndarray, x0: np.ndarray, tol: float = 1e-10,
-             max_iter: int = 1000, max_subspace: int = 20):
+             max_iter: int = 1000, max_subspace: int = 20, restart_keep: int = 1):
     """Lowest eigenpair of the symmetric operator ``matvec``; returns (lam, x, info)."""
     n = x0.shape[0]
     V = np.zeros((n, max_subspace))
@@ -55,6 +58,7 @@ def davidson(matvec, D: np.ndarray, x0: np.ndarray, tol: float = 1e-10,
     k = 1
     history = []
     lam, x, rn = np.nan, V[:, 0].copy(), np.inf
+    y_prev = None
     for it in range(1, max_iter + 1):
         W[:, k - 1] = matvec(V[:, k - 1])
         col = V[:, :k].T @ W[:, k - 1]
@@ -70,12 +74,23 @@ def davidson(matvec, D: np.ndarray, x0: np.ndarray, tol: float = 1e-10,
         if rn <= tol:
             return lam, x, {"iters": it, "resnorm": rn, "converged": True, "history": history}
         t = correct(r, lam, D)
-        if k == max_subspace:          # restart with the Ritz vector
-            V[:, 0] = x
-            W[:, 0] = wy
+        if k == max_subspace:          # restart with the Ritz vector (and the previous one)
+            C = y[:, None]
+            if restart_keep == 2 and y_prev is not None:
+                c2 = np.zeros(k)
+                c2[:len(y_prev)] = y_prev
+                c2 -= y * (y @ c2)
+                c2 -= y * (y @ c2)
+                if np.linalg.norm(c2) > 1e-8:
+                    C = np.column_stack([y, c2 / np.linalg.norm(c2)])
+            Vn, Wn = V[:, :k] @ C, W[:, :k] @ C
+            Bn = C.T @ B[:k, :k] @ C
+            k = C.shape[1]
+            V[:, :k], W[:, :k] = Vn, Wn
             B[:, :] = 0.0
-            B[0, 0] = lam
-            k = 1
+            B[:k, :k] = Bn
+            y = C.T @ y            # the Ritz vector in the new basis: e_1
+        y_prev = y
         before = np.linalg.norm(t)
         t_o = _cgs2(V[:, :k], t)
         if np.linalg.norm(t_o) < BREAKDOWN * before:

@@ -69,7 +69,7 @@ class Options(C.Structure):
 class SolveInfo(C.Structure):
     _fields_ = [("energy", C.c_double), ("resnorm", C.c_double), ("iters", C.c_int32),
                 ("projections", C.c_int32), ("fp64_projections", C.c_int32),
-                ("restarts", C.c_int32)]
+                ("restarts", C.c_int32), ("small_eig_sweeps", C.c_int32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -207,7 +207,7 @@ def marshal(sb) -> _Marshalled:
 
 
 def options(prec="fp64", tol=1e-10, max_iter=1000, max_subspace=20, fp64_refine=True,
-            refine_ratio=1e-3) -> Options:
+            refine_ratio=0.0) -> Options:
     o = Options()
     load().dmrg_options_default(C.byref(o))
     o.prec = PREC[prec] if isinstance(prec, str) else int(prec)

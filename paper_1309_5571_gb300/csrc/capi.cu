@@ -31,7 +31,7 @@ void dmrg_options_default(dmrg_options* opt) {
   opt->max_iter = 1000;
   opt->max_subspace = 20;
   opt->fp64_refine = 1;
-  opt->refine_ratio = 1e-3;
+  opt->refine_ratio = 0.0;
 }
 
 const char* dmrg_status_string(dmrg_status s) {

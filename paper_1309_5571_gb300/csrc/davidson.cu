@@ -15,12 +15,18 @@
 //
 // Low-precision projections (TF32, BF16X3) carry an error of order eps * ||H||, which
 // bounds how small the computed residual can get.  The mixed mode therefore anchors the
-// iteration with float64 projections: whenever the basis is collapsed (subspace limit,
-// or the low-precision residual fell below refine_ratio times the last exact residual,
-// or below tol), the new single basis vector x is projected in FP64, so lambda = x^T H x
-// is an FP64 Rayleigh quotient and the residual W(:,0) - lambda x is exact.  Only such an
-// exact residual can end the iteration.  Later low-precision columns then only carry
-// the error of the correction x - x_anchor, which shrinks as the iteration converges.
+// iteration with float64 projections: the basis is collapsed to the Ritz vector x, which
+// is projected in FP64, so lambda = x^T H x is an FP64 Rayleigh quotient and the residual
+// W(:,0) - lambda x is exact.  Only such an exact residual can end the iteration.  Later
+// low-precision columns only carry the error of the correction x - x_anchor, which
+// shrinks as the iteration converges; the coupling of the anchor with them is taken from
+// the exact column.  An anchor is taken when the computed residual approaches the
+// estimated low-precision floor eps ||H|| ||y(1:)||, when it falls below tol, and at a
+// subspace-limit restart close to the floor or after a stalled phase (other restarts are
+// plain ones keeping W y).
+#include <stdio.h>
+#include <stdlib.h>
+
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -50,9 +56,23 @@ struct dmrg_davidson_state {
   double anchor_rnorm = INFINITY;
   int ritz_k = 1;  // columns that small->y refers to; 0: V(:,0) holds the Ritz vector
   bool anchored = false;  // column 0 of W is an FP64 projection (mixed mode)
+  int plain_restarts = 0; // subspace-limit restarts since the last FP64 anchor
+  int sweeps = 0;         // Jacobi sweeps over all iterations
+  double floor_est = 0.0; // estimated low-precision residual floor (mixed mode)
+  double restart_rnorm = INFINITY;  // residual at the last subspace-limit restart
 };
 
 namespace {
+
+// DMRG_TRACE=1 in the environment prints one line per Davidson iteration to stderr
+bool trace_on() {
+  static int on = -1;
+  if (on < 0) {
+    const char* e = getenv("DMRG_TRACE");
+    on = (e && e[0] && e[0] != '0') ? 1 : 0;
+  }
+  return on == 1;
+}
 
 dmrg_status read_small(dmrg_davidson_state* s, cudaStream_t st) {
   DMRG_CUDA_TRY(cudaMemcpyAsync(s->hsmall, s->small, sizeof(DevSmall), cudaMemcpyDeviceToHost, st));
@@ -168,6 +188,7 @@ dmrg_status dmrg_davidson_step(dmrg_davidson_state* s, void* stream, int32_t* co
   DMRG_TRY(launch_residual(s->vw, s->V, s->W, s->D, ldv, n, k, tcol, s->small, 0, st));
   DMRG_TRY(read_small(s, st));
   s->iters++;
+  s->sweeps += s->hsmall->jacobi_sweeps;
   s->lambda = s->hsmall->lambda;
   s->rnorm = std::sqrt(std::max(0.0, s->hsmall->rnorm2));
   if (s->hsmall->flags & 2 || !std::isfinite(s->lambda)) {
@@ -185,12 +206,42 @@ dmrg_status dmrg_davidson_step(dmrg_davidson_state* s, void* stream, int32_t* co
     return DMRG_OK;
   }
   bool do_anchor = false, do_restart = false;
-  if (s->mixed &&
-      (s->rnorm <= tol || (k > 1 && s->rnorm <= s->plan->opt.refine_ratio * s->anchor_rnorm)))
-    do_anchor = true;
-  if (k == s->kmax) {
-    if (s->mixed) do_anchor = true;
-    else do_restart = true;
+  if (s->mixed) {
+    // estimated floor of the low-precision residual: eps * ||H|| * ||y(1:)||, the error
+    // the low-precision columns contribute to W y (||y(1:)|| = 1 before the first anchor;
+    // ||H|| from the extreme Ritz values); anchor when the computed residual has come
+    // within a factor 10 of it, or below tol, or (optional) below refine_ratio times the
+    // last exact residual
+    const DevSmall& h = *s->hsmall;
+    double hnorm = 0.0, ytail = 0.0;
+    for (int j = 0; j < k; ++j) hnorm = std::max(hnorm, std::fabs(h.theta[j]));
+    for (int j = 1; j < k; ++j) ytail += h.y[j] * h.y[j];
+    ytail = s->anchored ? std::sqrt(ytail) : 1.0;
+    const double eps = s->plan->opt.prec == DMRG_PREC_TF32 ? 2e-3 : 5e-7;
+    const double floor_est = eps * hnorm * ytail;
+    s->floor_est = floor_est;
+    const double ratio = s->plan->opt.refine_ratio;
+    if (s->rnorm <= tol || (k > 1 && s->rnorm <= 10.0 * floor_est) ||
+        (k > 1 && ratio > 0.0 && s->rnorm <= ratio * s->anchor_rnorm))
+      do_anchor = true;
+    if (trace_on())
+      fprintf(stderr, "dmrg it %4d k %2d %s lambda % .15f r %.3e floor %.3e ytail %.2e sweeps %d%s\n",
+              s->iters, k, anchor ? "FP64" : "lp  ", s->lambda, s->rnorm, floor_est, ytail,
+              h.jacobi_sweeps, do_anchor ? "  -> anchor" : "");
+  } else if (trace_on()) {
+    fprintf(stderr, "dmrg it %4d k %2d lambda % .15f r %.3e sweeps %d\n", s->iters, k, s->lambda,
+            s->rnorm, s->hsmall->jacobi_sweeps);
+  }
+  if (k == s->kmax && !do_anchor) {
+    // subspace limit: a plain restart keeps W y, whose low-precision error is of the
+    // order of the current floor.  It becomes an FP64 anchor instead when the residual
+    // is already within a factor 100 of the floor, or when it has not halved since the
+    // previous subspace-limit restart (a stalled low-precision phase)
+    if (s->mixed && (s->rnorm <= 100.0 * s->floor_est || s->rnorm > 0.5 * s->restart_rnorm))
+      do_anchor = true;
+    else
+      do_restart = true;
+    s->restart_rnorm = s->rnorm;
   }
   if (do_anchor) {
     // collapse to the normalised Ritz vector; its projection is redone in FP64
@@ -199,6 +250,8 @@ dmrg_status dmrg_davidson_step(dmrg_davidson_state* s, void* stream, int32_t* co
     s->k = 1;
     s->restarts++;
     s->anchor_pending = true;
+    s->plain_restarts = 0;
+    s->restart_rnorm = INFINITY;
     s->ritz_k = 0;
     return DMRG_OK;
   }
@@ -211,14 +264,15 @@ dmrg_status dmrg_davidson_step(dmrg_davidson_state* s, void* stream, int32_t* co
     DMRG_TRY(launch_set_B00(s->small, st));
     knew = 1;
     s->restarts++;
+    s->plain_restarts++;
     s->ritz_k = 0;
     DMRG_TRY(launch_overlap(s->vw, s->V, ldv, n, knew, tcol, s->small->s[0], s->small, -1, st));
   }
   // classical Gram-Schmidt, twice, then normalise
   for (int attempt = 0; attempt < 2; ++attempt) {
     DMRG_CUDA_TRY(cudaMemsetAsync(&s->small->flags, 0, sizeof(int32_t), st));
-    DMRG_TRY(launch_cgs(s->vw, s->V, ldv, n, knew, tcol, s->small, 0, 1, st));
-    DMRG_TRY(launch_cgs(s->vw, s->V, ldv, n, knew, tcol, s->small, 1, 2, st));
+    DMRG_TRY(launch_cgs(s->vw, s->V, ldv, n, knew, tcol, s->small, 0, 1, st, 0));
+    DMRG_TRY(launch_cgs(s->vw, s->V, ldv, n, knew, tcol, s->small, 1, 2, st, 1));
     DMRG_TRY(launch_finish(tcol, n, s->small, st));
     DMRG_TRY(read_small(s, st));
     if (!(s->hsmall->flags & 1)) break;
@@ -253,6 +307,7 @@ dmrg_status dmrg_state_get_info(const dmrg_davidson_state* s, dmrg_solve_info* i
   info->projections = s->projections;
   info->fp64_projections = s->fp64_projections;
   info->restarts = s->restarts;
+  info->small_eig_sweeps = s->sweeps;
   return DMRG_OK;
 }
 

@@ -253,32 +253,38 @@ pack_kernel(const PackChunk* __restrict__ chunks, const PackJob* __restrict__ jo
     else { r = idx & (kRows - 1); g = idx >> 7; }
     const int64_t grow = (int64_t)ch.rt * kRows + r;
     const int k0 = ch.kt * KT + g * EPG;
-    double v[EPG];
+    // operands are rounded to FP32 first (one conversion, no further FP64 arithmetic:
+    // FP64 throughput is low on this part); the three BF16 terms of an FP32 value
+    // represent it exactly
+    const bool scaled = jb.scale != 1.0;
+    float v[EPG];
 #pragma unroll
     for (int e = 0; e < EPG; ++e) {
       const int k = k0 + e;
-      v[e] = (grow < jb.R && k < jb.K) ? jb.scale * src[grow * jb.rs + (int64_t)k * jb.cs] : 0.0;
+      double a = 0.0;
+      if (grow < jb.R && k < jb.K) a = src[grow * jb.rs + (int64_t)k * jb.cs];
+      v[e] = (float)(scaled ? jb.scale * a : a);
     }
     const uint32_t off = swz(r, g);
     if constexpr (TF32) {
       uint4 q;
-      q.x = __float_as_uint(to_tf32((float)v[0]));
-      q.y = __float_as_uint(to_tf32((float)v[1]));
-      q.z = __float_as_uint(to_tf32((float)v[2]));
-      q.w = __float_as_uint(to_tf32((float)v[3]));
+      q.x = __float_as_uint(to_tf32(v[0]));
+      q.y = __float_as_uint(to_tf32(v[1]));
+      q.z = __float_as_uint(to_tf32(v[2]));
+      q.w = __float_as_uint(to_tf32(v[3]));
       *reinterpret_cast<uint4*>(base + off) = q;
     } else {
       __nv_bfloat16 h[3][8];
 #pragma unroll
       for (int e = 0; e < 8; ++e) {
-        const double a = v[e];
-        const __nv_bfloat16 h0 = __double2bfloat16(a);
-        const double r1 = a - (double)__bfloat162float(h0);
-        const __nv_bfloat16 h1 = __double2bfloat16(r1);
-        const double r2 = r1 - (double)__bfloat162float(h1);
+        const float a = v[e];
+        const __nv_bfloat16 h0 = __float2bfloat16_rn(a);
+        const float r1 = a - __bfloat162float(h0);
+        const __nv_bfloat16 h1 = __float2bfloat16_rn(r1);
+        const float r2 = r1 - __bfloat162float(h1);
         h[0][e] = h0;
         h[1][e] = h1;
-        h[2][e] = __double2bfloat16(r2);
+        h[2][e] = __float2bfloat16_rn(r2);
       }
 #pragma unroll
       for (int p = 0; p < PLANES; ++p) {

@@ -161,6 +161,10 @@ struct DevSmall {
   double nrm2;            // generic norm result
   int32_t flags;          // bit 0: breakdown, bit 1: non-finite
   int32_t jacobi_sweeps;
+  double Q[KMAX * KMAX];  // eigenvectors of the last k x k B (row-major, columns)
+  double theta[KMAX];     // its eigenvalues
+  int32_t qk;             // order of the stored decomposition (0: none)
+  int32_t pad_;
 };
 
 struct VecWork {
@@ -185,7 +189,8 @@ dmrg_status launch_residual(const VecWork& w, const double* V, const double* W,
                             DevSmall* small, int mode, cudaStream_t st);
 // t -= V s[sin]; s[sout] = V^T t; tnorm2 = ||t||^2
 dmrg_status launch_cgs(const VecWork& w, const double* V, int64_t ldv, int64_t n, int k,
-                       double* tcol, DevSmall* small, int sin, int sout, cudaStream_t st);
+                       double* tcol, DevSmall* small, int sin, int sout, cudaStream_t st,
+                       int second = 0);
 // flags breakdown (tnorm2 < 1e-20 tnorm2_before) else t /= ||t||
 dmrg_status launch_finish(double* tcol, int64_t n, DevSmall* small, cudaStream_t st);
 // x = V y, optionally wy = W y (n elements, written unpadded)

@@ -97,42 +97,40 @@ __device__ __forceinline__ double2 ld2cg(const double* p) {
 // With w0 != NULL (mixed precision with an FP64 anchor in column 0) the coupling between
 // the anchor and column Bcol is taken from the exact anchor projection, v_Bcol . W(:,0),
 // instead of v_0 . W(:,Bcol), whose low-precision error would not shrink with the
-// correction.
+// correction.  K (the number of basis columns) is a compile-time constant in all the
+// kernels below, so loads are issued back to back and accumulators stay in registers.
+template <int K>
 __global__ void __launch_bounds__(kVecThreads)
-overlap_kernel(const double* __restrict__ V, int64_t ldv, int64_t n2, int k,
+overlap_kernel(const double* __restrict__ V, int64_t ldv, int64_t n2,
                const double* __restrict__ w, const double* __restrict__ w0,
                double* __restrict__ partials, unsigned int* counter, double* s_out,
                DevSmall* small, int Bcol) {
-  double acc[KMAX + 1];
+  double acc[K + 1];
 #pragma unroll
-  for (int j = 0; j < KMAX + 1; ++j) acc[j] = 0.0;
+  for (int j = 0; j < K + 1; ++j) acc[j] = 0.0;
   const bool anchored = w0 != nullptr && Bcol > 0;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n2;
        e += (int64_t)gridDim.x * blockDim.x) {
-    const double2 wv = ld2cg(w + 2 * e);
-    double2 vlast = make_double2(0.0, 0.0);
+    double2 v[K];
 #pragma unroll
-    for (int j = 0; j < KMAX; ++j) {
-      if (j < k) {
-        const double2 v = ld2(V + j * ldv + 2 * e);
-        acc[j] = fma(v.x, wv.x, fma(v.y, wv.y, acc[j]));
-        if (j == k - 1) vlast = v;
-      }
-    }
+    for (int j = 0; j < K; ++j) v[j] = ld2(V + j * ldv + 2 * e);
+    const double2 wv = ld2cg(w + 2 * e);
+#pragma unroll
+    for (int j = 0; j < K; ++j) acc[j] = fma(v[j].x, wv.x, fma(v[j].y, wv.y, acc[j]));
     if (anchored) {
       const double2 a = ld2(w0 + 2 * e);
-      acc[KMAX] = fma(vlast.x, a.x, fma(vlast.y, a.y, acc[KMAX]));
+      acc[K] = fma(v[K - 1].x, a.x, fma(v[K - 1].y, a.y, acc[K]));
     }
   }
-  block_partials<KMAX, 1>(acc, k, partials);
+  block_partials<K, 1>(acc, K, partials);
   if (Ticket::last_block(counter)) {
-    __shared__ double tot[KMAX + 1];
-    final_sums(partials, k + 1, tot);
-    for (int j = threadIdx.x; j < k; j += blockDim.x) {
+    __shared__ double tot[K + 1];
+    final_sums(partials, K + 1, tot);
+    for (int j = threadIdx.x; j < K; j += blockDim.x) {
       if (s_out) s_out[j] = tot[j];
       if (Bcol >= 0) {
         double v = tot[j];
-        if (anchored && j == 0) v = tot[k];
+        if (anchored && j == 0) v = tot[K];
         small->B[j * KMAX + Bcol] = v;
         small->B[Bcol * KMAX + j] = v;
       }
@@ -166,108 +164,175 @@ gemv_trans_kernel(const double* __restrict__ V, int64_t ldv, int64_t n, int k,
 }
 
 // ---------------------------------------------------------------- residual + correction
+// r = W y - lambda V y and its norm; t = r / (lambda - D) (mode 0, the diagonal
+// correction) or t = r (mode 1); V^T t and ||t||^2.  The preconditioner is a direction,
+// not a value that must be exact: its reciprocal is formed in FP32 (an FP64 division costs
+// as much as a dozen FP64 operations on this part), the product r * (1/(lambda - D)) in
+// FP64.
+template <int K>
 __global__ void __launch_bounds__(kVecThreads)
 residual_kernel(const double* __restrict__ V, const double* __restrict__ W,
-                const double* __restrict__ D, int64_t ldv, int64_t n2, int k,
+                const double* __restrict__ D, int64_t ldv, int64_t n2,
                 double* __restrict__ tcol, double* __restrict__ partials,
                 unsigned int* counter, DevSmall* small, int mode) {
-  __shared__ double ys[KMAX];
+  __shared__ double ys[K];
   __shared__ double lam_s;
-  if (threadIdx.x < KMAX) ys[threadIdx.x] = threadIdx.x < k ? small->y[threadIdx.x] : 0.0;
+  if (threadIdx.x < K) ys[threadIdx.x] = small->y[threadIdx.x];
   if (threadIdx.x == 0) lam_s = small->lambda;
   __syncthreads();
   const double lam = lam_s;
-  double acc[KMAX + 2];  // [0..k): V^T t, [k]: ||r||^2, [k+1]: ||t||^2
+  double y[K];
 #pragma unroll
-  for (int j = 0; j < KMAX + 2; ++j) acc[j] = 0.0;
+  for (int j = 0; j < K; ++j) y[j] = ys[j];
+  double acc[K + 2];  // [0..K): V^T t, [K]: ||r||^2, [K+1]: ||t||^2
+#pragma unroll
+  for (int j = 0; j < K + 2; ++j) acc[j] = 0.0;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n2;
        e += (int64_t)gridDim.x * blockDim.x) {
-    double2 v[KMAX];
+    double2 v[K];
     double x0 = 0.0, x1 = 0.0, w0 = 0.0, w1 = 0.0;
 #pragma unroll
-    for (int j = 0; j < KMAX; ++j) {
-      if (j < k) {
-        v[j] = ld2(V + j * ldv + 2 * e);
-        const double2 wv = ld2(W + j * ldv + 2 * e);
-        x0 = fma(ys[j], v[j].x, x0);
-        x1 = fma(ys[j], v[j].y, x1);
-        w0 = fma(ys[j], wv.x, w0);
-        w1 = fma(ys[j], wv.y, w1);
-      }
+    for (int j = 0; j < K; ++j) v[j] = ld2(V + j * ldv + 2 * e);
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+      const double2 wv = ld2(W + j * ldv + 2 * e);
+      x0 = fma(y[j], v[j].x, x0);
+      x1 = fma(y[j], v[j].y, x1);
+      w0 = fma(y[j], wv.x, w0);
+      w1 = fma(y[j], wv.y, w1);
     }
-    const double r0 = w0 - lam * x0, r1 = w1 - lam * x1;
+    const double r0 = fma(-lam, x0, w0), r1 = fma(-lam, x1, w1);
     double t0 = r0, t1 = r1;
     if (mode == 0) {
       const double2 d = ld2(D + 2 * e);
-      double q0 = lam - d.x, q1 = lam - d.y;
-      if (fabs(q0) < 1e-8) q0 = q0 >= 0.0 ? 1e-8 : -1e-8;
-      if (fabs(q1) < 1e-8) q1 = q1 >= 0.0 ? 1e-8 : -1e-8;
-      t0 = r0 / q0;
-      t1 = r1 / q1;
+      float q0 = (float)(lam - d.x), q1 = (float)(lam - d.y);
+      if (fabsf(q0) < 1e-8f) q0 = q0 >= 0.0f ? 1e-8f : -1e-8f;
+      if (fabsf(q1) < 1e-8f) q1 = q1 >= 0.0f ? 1e-8f : -1e-8f;
+      t0 = r0 * (double)(1.0f / q0);
+      t1 = r1 * (double)(1.0f / q1);
     }
     reinterpret_cast<double2*>(tcol)[e] = make_double2(t0, t1);
 #pragma unroll
-    for (int j = 0; j < KMAX; ++j)
-      if (j < k) acc[j] = fma(v[j].x, t0, fma(v[j].y, t1, acc[j]));
-    acc[KMAX] = fma(r0, r0, fma(r1, r1, acc[KMAX]));
-    acc[KMAX + 1] = fma(t0, t0, fma(t1, t1, acc[KMAX + 1]));
+    for (int j = 0; j < K; ++j) acc[j] = fma(v[j].x, t0, fma(v[j].y, t1, acc[j]));
+    acc[K] = fma(r0, r0, fma(r1, r1, acc[K]));
+    acc[K + 1] = fma(t0, t0, fma(t1, t1, acc[K + 1]));
   }
-  block_partials<KMAX, 2>(acc, k, partials);
+  block_partials<K, 2>(acc, K, partials);
   if (Ticket::last_block(counter)) {
-    __shared__ double tot[KMAX + 2];
-    final_sums(partials, k + 2, tot);
-    for (int j = threadIdx.x; j < k; j += blockDim.x) small->s[0][j] = tot[j];
+    __shared__ double tot[K + 2];
+    final_sums(partials, K + 2, tot);
+    for (int j = threadIdx.x; j < K; j += blockDim.x) small->s[0][j] = tot[j];
     if (threadIdx.x == 0) {
-      small->rnorm2 = tot[k];
-      small->tnorm2_before = tot[k + 1];
-      small->tnorm2 = tot[k + 1];
-      if (!isfinite(tot[k]) || !isfinite(tot[k + 1])) small->flags |= 2;
+      small->rnorm2 = tot[K];
+      small->tnorm2_before = tot[K + 1];
+      small->tnorm2 = tot[K + 1];
+      if (!isfinite(tot[K]) || !isfinite(tot[K + 1])) small->flags |= 2;
       *counter = 0u;
     }
   }
 }
 
 // ---------------------------------------------------------------- Gram-Schmidt pass
+// t -= V s[sin]; with DOT also s[sout] = V^T t; always ||t||^2.  A second pass
+// (second = 1) runs only when the first removed more than half of ||t||^2 -- the
+// "twice is enough" test -- and otherwise returns at once; the decision is read from the
+// device, so the host launches both passes without waiting.
+template <int K, bool DOT>
 __global__ void __launch_bounds__(kVecThreads)
-cgs_kernel(const double* __restrict__ V, int64_t ldv, int64_t n2, int k, double* tcol,
+cgs_kernel(const double* __restrict__ V, int64_t ldv, int64_t n2, double* tcol,
            double* __restrict__ partials, unsigned int* counter, DevSmall* small, int sin,
-           int sout) {
-  __shared__ double ss[KMAX];
-  if (threadIdx.x < KMAX) ss[threadIdx.x] = threadIdx.x < k ? small->s[sin][threadIdx.x] : 0.0;
+           int sout, int second) {
+  if (second && small->tnorm2 >= 0.5 * small->tnorm2_before) return;
+  __shared__ double ss[K];
+  if (threadIdx.x < K) ss[threadIdx.x] = small->s[sin][threadIdx.x];
   __syncthreads();
-  double acc[KMAX + 1];
+  double s[K];
 #pragma unroll
-  for (int j = 0; j < KMAX + 1; ++j) acc[j] = 0.0;
+  for (int j = 0; j < K; ++j) s[j] = ss[j];
+  double acc[K + 1];
+#pragma unroll
+  for (int j = 0; j < K + 1; ++j) acc[j] = 0.0;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n2;
        e += (int64_t)gridDim.x * blockDim.x) {
-    double2 t = reinterpret_cast<const double2*>(tcol)[e];
-    double2 v[KMAX];
+    double2 v[K];
 #pragma unroll
-    for (int j = 0; j < KMAX; ++j) {
-      if (j < k) {
-        v[j] = ld2(V + j * ldv + 2 * e);
-        t.x = fma(-ss[j], v[j].x, t.x);
-        t.y = fma(-ss[j], v[j].y, t.y);
-      }
+    for (int j = 0; j < K; ++j) v[j] = ld2(V + j * ldv + 2 * e);
+    double2 t = reinterpret_cast<const double2*>(tcol)[e];
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+      t.x = fma(-s[j], v[j].x, t.x);
+      t.y = fma(-s[j], v[j].y, t.y);
     }
     reinterpret_cast<double2*>(tcol)[e] = t;
+    if (DOT) {
 #pragma unroll
-    for (int j = 0; j < KMAX; ++j)
-      if (j < k) acc[j] = fma(v[j].x, t.x, fma(v[j].y, t.y, acc[j]));
-    acc[KMAX] = fma(t.x, t.x, fma(t.y, t.y, acc[KMAX]));
+      for (int j = 0; j < K; ++j) acc[j] = fma(v[j].x, t.x, fma(v[j].y, t.y, acc[j]));
+    }
+    acc[K] = fma(t.x, t.x, fma(t.y, t.y, acc[K]));
   }
-  block_partials<KMAX, 1>(acc, k, partials);
+  if (DOT) {
+    block_partials<K, 1>(acc, K, partials);
+  } else {
+    double a1[1] = {acc[K]};
+    block_partials<0, 1>(a1, 0, partials);
+  }
   if (Ticket::last_block(counter)) {
-    __shared__ double tot[KMAX + 1];
-    final_sums(partials, k + 1, tot);
-    for (int j = threadIdx.x; j < k; j += blockDim.x) small->s[sout][j] = tot[j];
+    __shared__ double tot[K + 1];
+    const int nv = DOT ? K + 1 : 1;
+    final_sums(partials, nv, tot);
+    if (DOT)
+      for (int j = threadIdx.x; j < K; j += blockDim.x) small->s[sout][j] = tot[j];
     if (threadIdx.x == 0) {
-      small->tnorm2 = tot[k];
-      if (!isfinite(tot[k])) small->flags |= 2;
+      const double nrm = tot[nv - 1];
+      small->tnorm2 = nrm;
+      if (!isfinite(nrm)) small->flags |= 2;
       *counter = 0u;
     }
   }
 }
+
+// compile-time dispatch over K = 1 .. KMAX
+template <template <int> class F, int K = 1>
+struct KDispatch {
+  template <typename... A>
+  static void run(int k, A... a) {
+    if (k == K) F<K>::go(a...);
+    else KDispatch<F, K + 1>::run(k, a...);
+  }
+};
+template <template <int> class F>
+struct KDispatch<F, KMAX + 1> {
+  template <typename... A>
+  static void run(int, A...) {}
+};
+
+template <int K>
+struct OverlapL {
+  static void go(int grid, cudaStream_t st, const double* V, int64_t ldv, int64_t n2,
+                 const double* w, const double* w0, double* part, unsigned int* cnt,
+                 double* s_out, DevSmall* small, int Bcol) {
+    overlap_kernel<K><<<grid, kVecThreads, 0, st>>>(V, ldv, n2, w, w0, part, cnt, s_out, small, Bcol);
+  }
+};
+template <int K>
+struct ResidualL {
+  static void go(int grid, cudaStream_t st, const double* V, const double* W, const double* D,
+                 int64_t ldv, int64_t n2, double* tcol, double* part, unsigned int* cnt,
+                 DevSmall* small, int mode) {
+    residual_kernel<K><<<grid, kVecThreads, 0, st>>>(V, W, D, ldv, n2, tcol, part, cnt, small, mode);
+  }
+};
+template <int K>
+struct CgsL {
+  static void go(int grid, cudaStream_t st, const double* V, int64_t ldv, int64_t n2,
+                 double* tcol, double* part, unsigned int* cnt, DevSmall* small, int sin,
+                 int sout, int second) {
+    if (second)
+      cgs_kernel<K, false><<<grid, kVecThreads, 0, st>>>(V, ldv, n2, tcol, part, cnt, small, sin, sout, 1);
+    else
+      cgs_kernel<K, true><<<grid, kVecThreads, 0, st>>>(V, ldv, n2, tcol, part, cnt, small, sin, sout, 0);
+  }
+};
 
 // ---------------------------------------------------------------- normalise new column
 __global__ void finish_kernel(double* tcol, int64_t n2, DevSmall* small) {
@@ -334,10 +399,15 @@ __global__ void scale_copy_kernel(const double* __restrict__ src, double* __rest
 }
 
 __global__ void set_B00_kernel(DevSmall* small) {
-  // after a restart the basis is the single Ritz vector x with B = [lambda]
+  // after a restart the basis is the single Ritz vector x with B = [lambda] = 1 x 1
   for (int j = threadIdx.x; j < KMAX * KMAX; j += blockDim.x) small->B[j] = 0.0;
   __syncthreads();
-  if (threadIdx.x == 0) small->B[0] = small->lambda;
+  if (threadIdx.x == 0) {
+    small->B[0] = small->lambda;
+    small->Q[0] = 1.0;
+    small->theta[0] = small->lambda;
+    small->qk = 1;
+  }
 }
 
 // ---------------------------------------------------------------- small eigenproblem
@@ -345,66 +415,74 @@ __global__ void set_B00_kernel(DevSmall* small) {
 // Jacobi method with the round-robin ordering: each of the k-1 steps of a sweep applies
 // k/2 disjoint rotations at once.  A rotation (p, q) uses the symmetric Schur
 // decomposition of the 2 x 2 block: tau = (a_qq - a_pp) / (2 a_pq),
-// t = sign(tau) / (|tau| + sqrt(1 + tau^2)), c = 1 / sqrt(1 + t^2), s = t c, which
-// zeroes a_pq in J^T A J.  Sweeps stop when the off-diagonal mass is below 1e-30 of the
-// total (or after 30 sweeps).
-__global__ void __launch_bounds__(256) jacobi_kernel(DevSmall* small, int k) {
+// t = sign(tau) / (|tau| + sqrt(1 + tau^2)), c = 1 / sqrt(1 + t^2), s = t c, which zeroes
+// a_pq in J^T A J.  A rotation is skipped when |a_pq| <= 1e-15 sqrt(|a_pp a_qq|) (the
+// entry is at the rounding level of the diagonal); the sweeps stop after a sweep
+// without any rotation (at most 40 sweeps).  The angle of each rotation is computed in
+// FP32 and its cosine and sine in FP64 (see below).
+// Warm start: B_k differs from B_{k-1} by its last row and column, and the previous call
+// stored the eigendecomposition B_{k-1} = Q diag(theta) Q^T.  With Q~ = diag(Q, 1) the
+// matrix Q~^T B_k Q~ is diagonal except for its last row and column (an arrowhead), so a
+// few sweeps finish it; the eigenvectors are Q~ times the accumulated rotations.
+__global__ void __launch_bounds__(128) jacobi_kernel(DevSmall* small, int k) {
   __shared__ double A[KMAX][KMAX + 1];
   __shared__ double Q[KMAX][KMAX + 1];
   __shared__ double cs[KMAX / 2], sn[KMAX / 2];
   __shared__ int pp[KMAX / 2], qq[KMAX / 2];
   __shared__ int perm[KMAX];
-  __shared__ double red[256];
-  __shared__ int done;
+  __shared__ int rotated, best;
   const int tid = threadIdx.x;
   const int kk = (k + 1) & ~1;  // even number of players; the extra one is a dummy
+  const bool warm = k > 1 && small->qk == k - 1;
   for (int e = tid; e < KMAX * KMAX; e += blockDim.x) {
     const int r = e / KMAX, c = e % KMAX;
-    A[r][c] = (r < k && c < k) ? small->B[r * KMAX + c] : 0.0;
-    Q[r][c] = (r == c) ? 1.0 : 0.0;
+    double a = 0.0, q = (r == c) ? 1.0 : 0.0;
+    if (r < k && c < k) {
+      if (!warm) {
+        a = small->B[r * KMAX + c];
+      } else if (r < k - 1 && c < k - 1) {
+        a = (r == c) ? small->theta[r] : 0.0;
+        q = small->Q[r * KMAX + c];
+      } else if (r == k - 1 && c == k - 1) {
+        a = small->B[(k - 1) * KMAX + (k - 1)];
+      } else {  // arrow entries: (Q^T b)_i with b = B(0:k-1, k-1)
+        const int i = r < k - 1 ? r : c;
+        double z = 0.0;
+        for (int m = 0; m < k - 1; ++m) z = fma(small->Q[m * KMAX + i], small->B[m * KMAX + (k - 1)], z);
+        a = z;
+      }
+    }
+    A[r][c] = a;
+    Q[r][c] = q;
   }
   if (tid < kk) perm[tid] = tid;
   __syncthreads();
   int sweep = 0;
-  for (; sweep < 30; ++sweep) {
-    // convergence test: off-diagonal vs total Frobenius mass
-    double off = 0.0, tot = 0.0;
-    for (int e = tid; e < k * k; e += blockDim.x) {
-      const int r = e / k, c = e % k;
-      const double v = A[r][c] * A[r][c];
-      tot += v;
-      if (r != c) off += v;
-    }
-    red[tid] = off;
+  for (; sweep < 40 && k > 1; ++sweep) {
+    if (tid == 0) rotated = 0;
     __syncthreads();
-    for (int s = 128; s > 0; s >>= 1) {
-      if (tid < s) red[tid] += red[tid + s];
-      __syncthreads();
-    }
-    const double offsum = red[0];
-    __syncthreads();
-    red[tid] = tot;
-    __syncthreads();
-    for (int s = 128; s > 0; s >>= 1) {
-      if (tid < s) red[tid] += red[tid + s];
-      __syncthreads();
-    }
-    if (tid == 0) done = (offsum <= 1e-30 * red[0]) || k <= 1;
-    __syncthreads();
-    if (done) break;
     for (int step = 0; step < kk - 1; ++step) {
-      // pairs of this round: (perm[i], perm[kk-1-i])
       if (tid < kk / 2) {
         int p = perm[tid], q = perm[kk - 1 - tid];
         if (p > q) { const int t = p; p = q; q = t; }
         double c = 1.0, s = 0.0;
         if (q < k) {
-          const double apq = A[p][q];
-          if (apq != 0.0) {
-            const double tau = (A[q][q] - A[p][p]) / (2.0 * apq);
-            const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-            c = 1.0 / sqrt(1.0 + t * t);
-            s = t * c;
+          const double apq = A[p][q], app = A[p][p], aqq = A[q][q];
+          if (fabs(apq) > 1e-15 * sqrt(fabs(app * aqq)) && apq != 0.0) {
+            // the angle only needs to be close to the annihilating one (the next sweep
+            // removes what is left), so tau and t are formed in FP32; c and s are then
+            // derived in FP64 from the same t, so the rotation is orthogonal to FP64
+            // rounding (c^2 + s^2 = 1).  This keeps the sequential FP64 chain short.
+            const float tau = (float)(aqq - app) / (2.0f * (float)apq);
+            const float tf = (tau >= 0.0f ? 1.0f : -1.0f) / (fabsf(tau) + sqrtf(1.0f + tau * tau));
+            const double t = (double)tf;
+            const double u = fma(t, t, 1.0);
+            double cc = (double)rsqrtf((float)u);
+            cc = cc * fma(-0.5 * u, cc * cc, 1.5);   // one Newton step to FP64 accuracy
+            cc = cc * fma(-0.5 * u, cc * cc, 1.5);
+            c = cc;
+            s = t * cc;
+            rotated = 1;
           }
         }
         pp[tid] = p;
@@ -416,9 +494,11 @@ __global__ void __launch_bounds__(256) jacobi_kernel(DevSmall* small, int k) {
       // rows: A <- J^T A
       for (int e = tid; e < (kk / 2) * kk; e += blockDim.x) {
         const int pr = e / kk, col = e % kk;
+        const double s = sn[pr];
+        if (s == 0.0) continue;
         const int p = pp[pr], q = qq[pr];
-        if (q >= k || col >= k) continue;
-        const double c = cs[pr], s = sn[pr];
+        if (col >= k) continue;
+        const double c = cs[pr];
         const double ap = A[p][col], aq = A[q][col];
         A[p][col] = c * ap - s * aq;
         A[q][col] = s * ap + c * aq;
@@ -427,9 +507,11 @@ __global__ void __launch_bounds__(256) jacobi_kernel(DevSmall* small, int k) {
       // columns: A <- A J, Q <- Q J
       for (int e = tid; e < (kk / 2) * kk; e += blockDim.x) {
         const int pr = e / kk, row = e % kk;
+        const double s = sn[pr];
+        if (s == 0.0) continue;
         const int p = pp[pr], q = qq[pr];
-        if (q >= k || row >= k) continue;
-        const double c = cs[pr], s = sn[pr];
+        if (row >= k) continue;
+        const double c = cs[pr];
         const double ap = A[row][p], aq = A[row][q];
         A[row][p] = c * ap - s * aq;
         A[row][q] = s * ap + c * aq;
@@ -438,30 +520,31 @@ __global__ void __launch_bounds__(256) jacobi_kernel(DevSmall* small, int k) {
         Q[row][q] = s * qp + c * qv;
       }
       __syncthreads();
-      // exact zero for the annihilated entries
-      if (tid < kk / 2) {
-        const int p = pp[tid], q = qq[tid];
-        if (q < k && sn[tid] != 0.0) { A[p][q] = 0.0; A[q][p] = 0.0; }
-      }
-      // rotate the tournament (player 0 fixed)
-      if (tid == 0) {
+      if (tid == 0) {  // rotate the tournament (player 0 fixed)
         const int last = perm[kk - 1];
         for (int i = kk - 1; i > 1; --i) perm[i] = perm[i - 1];
         perm[1] = last;
       }
       __syncthreads();
     }
+    if (!rotated) break;
   }
   if (tid == 0) {
-    int best = 0;
+    int b = 0;
     for (int i = 1; i < k; ++i)
-      if (A[i][i] < A[best][best]) best = i;
-    small->lambda = A[best][best];
+      if (A[i][i] < A[b][b]) b = i;
+    best = b;
+    small->lambda = A[b][b];
     small->jacobi_sweeps = sweep;
-    done = best;
+    small->qk = k;
   }
   __syncthreads();
-  if (tid < KMAX) small->y[tid] = tid < k ? Q[tid][done] : 0.0;
+  for (int e = tid; e < k * k; e += blockDim.x) {
+    const int r = e / k, c = e % k;
+    small->Q[r * KMAX + c] = Q[r][c];
+  }
+  if (tid < k) small->theta[tid] = A[tid][tid];
+  if (tid < KMAX) small->y[tid] = tid < k ? Q[tid][best] : 0.0;
 }
 
 }  // namespace
@@ -495,14 +578,14 @@ void vec_work_destroy(VecWork* w) {
 dmrg_status launch_overlap(const VecWork& w, const double* V, int64_t ldv, int64_t n, int k,
                            const double* vec, double* s_out, DevSmall* small, int Bcol,
                            cudaStream_t st, const double* w0) {
-  overlap_kernel<<<w.grid, kVecThreads, 0, st>>>(V, ldv, (n + 1) / 2, k, vec, w0, w.partials,
-                                                 w.counter, s_out, small, Bcol);
+  KDispatch<OverlapL>::run(k, w.grid, st, V, ldv, (int64_t)((n + 1) / 2), vec, w0, w.partials,
+                           w.counter, s_out, small, Bcol);
   DMRG_LAUNCH_CHECK();
   return DMRG_OK;
 }
 
 dmrg_status launch_jacobi(DevSmall* small, int k, cudaStream_t st) {
-  jacobi_kernel<<<1, 256, 0, st>>>(small, k);
+  jacobi_kernel<<<1, 128, 0, st>>>(small, k);
   DMRG_LAUNCH_CHECK();
   return DMRG_OK;
 }
@@ -510,16 +593,17 @@ dmrg_status launch_jacobi(DevSmall* small, int k, cudaStream_t st) {
 dmrg_status launch_residual(const VecWork& w, const double* V, const double* W,
                             const double* D, int64_t ldv, int64_t n, int k, double* tcol,
                             DevSmall* small, int mode, cudaStream_t st) {
-  residual_kernel<<<w.grid, kVecThreads, 0, st>>>(V, W, D, ldv, (n + 1) / 2, k, tcol,
-                                                  w.partials, w.counter, small, mode);
+  KDispatch<ResidualL>::run(k, w.grid, st, V, W, D, ldv, (int64_t)((n + 1) / 2), tcol,
+                            w.partials, w.counter, small, mode);
   DMRG_LAUNCH_CHECK();
   return DMRG_OK;
 }
 
 dmrg_status launch_cgs(const VecWork& w, const double* V, int64_t ldv, int64_t n, int k,
-                       double* tcol, DevSmall* small, int sin, int sout, cudaStream_t st) {
-  cgs_kernel<<<w.grid, kVecThreads, 0, st>>>(V, ldv, (n + 1) / 2, k, tcol, w.partials,
-                                             w.counter, small, sin, sout);
+                       double* tcol, DevSmall* small, int sin, int sout, cudaStream_t st,
+                       int second) {
+  KDispatch<CgsL>::run(k, w.grid, st, V, ldv, (int64_t)((n + 1) / 2), tcol, w.partials,
+                       w.counter, small, sin, sout, second);
   DMRG_LAUNCH_CHECK();
   return DMRG_OK;
 }
