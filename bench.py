@@ -9,6 +9,8 @@ The reported value is H*psi throughput over the whole solve: algorithmic project
 FLOPs of all projections of the step divided by the step time.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--prec P]
+  python bench.py --mode project [--prec P] [--workload NAME]   projections only (profiling)
+  python bench.py --mode peaks                                  matmul peak probe
 
 Under torchrun (N > 1) every rank solves its own replica of the workload (no data-path
 collective; weak scaling), timed with a barrier and the max over ranks.
@@ -159,6 +161,64 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_peaks():
+    """torch.matmul 8192^3 in float64, float32 (SIMT), TF32 and BF16: best of N CUDA-event
+    timings.  Used for the FP64 and TF32 roofline denominators."""
+    import torch
+    torch.cuda.set_device(0)
+    out = {}
+    for name, dtype, tf32, n, reps in (("fp64", torch.float64, False, 8192, 3),
+                                       ("fp32_simt", torch.float32, False, 8192, 5),
+                                       ("tf32", torch.float32, True, 8192, 10),
+                                       ("bf16", torch.bfloat16, False, 8192, 10)):
+        torch.backends.cuda.matmul.allow_tf32 = tf32
+        a = torch.randn(n, n, device="cuda", dtype=dtype)
+        b = torch.randn(n, n, device="cuda", dtype=dtype)
+        for _ in range(2):
+            a @ b
+        torch.cuda.synchronize()
+        best = 1e30
+        for _ in range(reps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            a @ b
+            e1.record()
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1) / 1e3)
+        out[name] = 2 * n ** 3 / best / 1e12
+        del a, b
+    print(json.dumps({"mode": "peaks", "unit": "TFLOP/s", **out}), flush=True)
+
+
+def run_project(args):
+    """Projections only, in one precision, on one workload (the launch used for ncu)."""
+    import torch
+    torch.cuda.set_device(0)
+    import __graft_entry__
+    __graft_entry__.build()
+    from dmrg_inputs import warmup
+    from paper_1309_5571_gb300 import Plan
+    prec = "bf16x3" if args.prec == "auto" else args.prec
+    sb = warmup.workload(args.workload)
+    x = torch.from_numpy(warmup.start_vector(sb.n, 0)).cuda()
+    y = torch.empty_like(x)
+    plan = Plan(sb, prec=prec)
+    for _ in range(args.warmup):
+        plan.project(x, y, prec=prec)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        plan.project(x, y, prec=prec)
+    e1.record()
+    torch.cuda.synchronize()
+    t = e0.elapsed_time(e1) / 1e3 / args.steps
+    print(json.dumps({"mode": "project", "workload": args.workload, "prec": prec, "n": sb.n,
+                      "ms": t * 1e3, "tflops": plan.stats["flops"] / t / 1e12}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -168,9 +228,15 @@ def main():
     ap.add_argument("--prec", default="auto", choices=["auto", "fp64", "tf32", "bf16x3"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--proj-reps", type=int, default=10)
+    ap.add_argument("--mode", default="solve", choices=["solve", "project", "peaks"])
+    ap.add_argument("--workload", default=WORKLOAD)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.mode == "peaks":
+        return run_peaks()
+    if args.mode == "project":
+        return run_project(args)
 
     import numpy as np
     import torch
@@ -190,7 +256,7 @@ def main():
     prec = args.prec
     if prec == "auto":
         prec = "bf16x3" if capi.tc_available() else "fp64"
-    sb = warmup.workload(WORKLOAD)
+    sb = warmup.workload(args.workload)
     x0 = warmup.start_vector(sb.n, seed=rank)
     x0_t = torch.from_numpy(x0).cuda()
     stream = torch.cuda.current_stream()

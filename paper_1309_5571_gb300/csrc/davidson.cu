@@ -60,6 +60,8 @@ struct dmrg_davidson_state {
   int sweeps = 0;         // Jacobi sweeps over all iterations
   double floor_est = 0.0; // estimated low-precision residual floor (mixed mode)
   double restart_rnorm = INFINITY;  // residual at the last subspace-limit restart
+  double baked_err = 0.0; // low-precision error folded into W(:,0) by plain restarts
+  double cur_err = 0.0;   // low-precision error of the current W y
 };
 
 namespace {
@@ -217,9 +219,14 @@ dmrg_status dmrg_davidson_step(dmrg_davidson_state* s, void* stream, int32_t* co
     for (int j = 0; j < k; ++j) hnorm = std::max(hnorm, std::fabs(h.theta[j]));
     for (int j = 1; j < k; ++j) ytail += h.y[j] * h.y[j];
     ytail = s->anchored ? std::sqrt(ytail) : 1.0;
-    const double eps = s->plan->opt.prec == DMRG_PREC_TF32 ? 2e-3 : 5e-7;
-    const double floor_est = eps * hnorm * ytail;
+    // relative error of one low-precision projection, measured against FP64 at the full
+    // workload sizes (BF16x3: 5e-6 of max|y|, FP32 accumulation over K ~ 1e3; TF32: 1e-3)
+    const double eps = s->plan->opt.prec == DMRG_PREC_TF32 ? 2e-3 : 5e-6;
+    // a plain restart folds the current low-precision error of W y into W(:,0): it stays
+    // in the floor until the next FP64 anchor
+    const double floor_est = eps * hnorm * ytail + s->baked_err;
     s->floor_est = floor_est;
+    s->cur_err = eps * hnorm * ytail;
     const double ratio = s->plan->opt.refine_ratio;
     if (s->rnorm <= tol || (k > 1 && s->rnorm <= 10.0 * floor_est) ||
         (k > 1 && ratio > 0.0 && s->rnorm <= ratio * s->anchor_rnorm))
@@ -252,6 +259,7 @@ dmrg_status dmrg_davidson_step(dmrg_davidson_state* s, void* stream, int32_t* co
     s->anchor_pending = true;
     s->plain_restarts = 0;
     s->restart_rnorm = INFINITY;
+    s->baked_err = 0.0;
     s->ritz_k = 0;
     return DMRG_OK;
   }
@@ -265,6 +273,7 @@ dmrg_status dmrg_davidson_step(dmrg_davidson_state* s, void* stream, int32_t* co
     knew = 1;
     s->restarts++;
     s->plain_restarts++;
+    s->baked_err += s->cur_err;
     s->ritz_k = 0;
     DMRG_TRY(launch_overlap(s->vw, s->V, ldv, n, knew, tcol, s->small->s[0], s->small, -1, st));
   }
