@@ -219,6 +219,44 @@ def run_project(args):
                       "ms": t * 1e3, "tflops": plan.stats["flops"] / t / 1e12}), flush=True)
 
 
+def run_batched(args):
+    """Uneven batch of independent Heisenberg superblocks (L = 100, m drawn from
+    {256, 512, 1024, 2048} with seed 1234): one batched solve versus the same solves one
+    after the other."""
+    import torch
+    torch.cuda.set_device(0)
+    import __graft_entry__
+    __graft_entry__.build()
+    from dmrg_inputs import warmup
+    from paper_1309_5571_gb300 import Plan, solve_batched
+    prec = "bf16x3" if args.prec == "auto" else args.prec
+    sbs, ms, x0s = warmup.batched_workload(count=args.batch)
+    plist = [Plan(sb, prec=prec) for sb in sbs]   # one plan (and scratch) per problem
+    xs = [torch.from_numpy(x).cuda() for x in x0s]
+    flops = sum(p.stats["flops"] for p in plist)
+    solve_batched(plist, xs, raise_on_nonconvergence=False)  # warm-up (operand images)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    outs, infos = solve_batched(plist, xs, raise_on_nonconvergence=False)
+    torch.cuda.synchronize()
+    t_b = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    for p, x in zip(plist, xs):
+        p.solve(x, raise_on_nonconvergence=False)
+    torch.cuda.synchronize()
+    t_s = time.perf_counter() - t0
+    proj = sum(i["projections"] + i["fp64_projections"] for i in infos)
+    print(json.dumps({"mode": "batched", "problems": len(plist), "m": sorted(set(ms)),
+                      "m_counts": {int(m): ms.count(m) for m in sorted(set(ms))},
+                      "prec": prec, "batched_s": t_b, "sequential_s": t_s,
+                      "speedup": t_s / t_b, "all_converged": all(i["converged"] for i in infos),
+                      "projections": proj,
+                      "hpsi_tflops_batched": sum(i["projections"] + i["fp64_projections"]
+                                                 for i in infos) and
+                      sum((i["projections"] + i["fp64_projections"]) * p.stats["flops"]
+                          for i, p in zip(infos, plist)) / t_b / 1e12}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -228,7 +266,8 @@ def main():
     ap.add_argument("--prec", default="auto", choices=["auto", "fp64", "tf32", "bf16x3"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--proj-reps", type=int, default=10)
-    ap.add_argument("--mode", default="solve", choices=["solve", "project", "peaks"])
+    ap.add_argument("--mode", default="solve", choices=["solve", "project", "peaks", "batched"])
+    ap.add_argument("--batch", type=int, default=64)
     ap.add_argument("--workload", default=WORKLOAD)
     args = ap.parse_args()
     if args.impl == "reference":
@@ -237,6 +276,8 @@ def main():
         return run_peaks()
     if args.mode == "project":
         return run_project(args)
+    if args.mode == "batched":
+        return run_batched(args)
 
     import numpy as np
     import torch

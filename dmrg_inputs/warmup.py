@@ -374,3 +374,21 @@ WORKLOADS = {
 
 def workload(name: str) -> Superblock:
     return warmup_superblock(**WORKLOADS[name])
+
+
+def batched_workload(count: int = 64, ms=(256, 512, 1024, 2048), L: int = 100, seed: int = 1234,
+                     model: str = "heisenberg"):
+    """Independent superblocks of uneven size: m_i drawn uniformly from ``ms`` (NumPy
+    PCG64, ``seed``).  Problems that draw the same m share the (deterministic) operator
+    blocks; each problem has its own start vector (seed i).  Returns (superblocks, m list,
+    start vectors)."""
+    rng = np.random.default_rng(seed)
+    draws = [int(m) for m in rng.choice(np.asarray(ms), size=count)]
+    cache = {}
+    sbs, x0s = [], []
+    for i, m in enumerate(draws):
+        if m not in cache:
+            cache[m] = warmup_superblock(model, L, m)
+        sbs.append(cache[m])
+        x0s.append(start_vector(cache[m].n, seed=i))
+    return sbs, draws, x0s

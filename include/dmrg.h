@@ -38,6 +38,9 @@
  *    DMRG_ERR_SHAPE before any device work is enqueued.
  *  - Single GPU.  A plan lives on the device that was current when it was created; use
  *    it with that device current.
+ *  - A plan owns the scratch of its projections (operand images, intermediates): calls
+ *    that use the same plan must be ordered (one stream, or events); create one plan per
+ *    problem to run problems concurrently.
  */
 #ifndef DMRG_GB300_H
 #define DMRG_GB300_H
@@ -123,6 +126,7 @@ typedef struct {
   int32_t fp64_projections; /* FP64 projections (all of them in FP64 mode)                */
   int32_t restarts;         /* basis collapses (subspace limit or re-anchoring)           */
   int32_t small_eig_sweeps; /* Jacobi sweeps of the projected eigenproblem, all iterations */
+  int32_t converged;        /* 1 if ||r|| <= tol was reached                               */
 } dmrg_solve_info;
 
 typedef struct {
@@ -197,6 +201,18 @@ dmrg_status dmrg_state_ritz(dmrg_davidson_state* st, double* x_out, void* stream
  * DMRG_ERR_NOT_CONVERGED with x_out and info filled when max_iter is reached. */
 dmrg_status dmrg_davidson_solve(dmrg_plan* plan, const double* x0, double* x_out,
                                 dmrg_solve_info* info, void* stream);
+/* Many independent superblock problems (each with its own plan, sector spectrum and size)
+ * solved together: every Davidson iteration of all unconverged problems is enqueued, each
+ * problem on its own stream, before one host wait for the whole batch, so small problems
+ * overlap on the GPU and share the host round trips.  plans, x0 and x_out are host arrays
+ * of nb pointers (x0[i], x_out[i] device vectors of plans[i]'s n); infos, if not NULL, has
+ * nb entries.  Problems that share a plan run in order on one stream (a plan's scratch is
+ * shared); give problems their own plans to let them overlap.  Work is ordered after the
+ * caller's stream and the caller's stream waits for it.  Returns DMRG_ERR_NOT_CONVERGED if any problem stopped at its max_iter (the others'
+ * results are valid; see infos[i].converged), or the first error met. */
+dmrg_status dmrg_davidson_solve_batched(dmrg_plan* const* plans, int32_t nb,
+                                        const double* const* x0, double* const* x_out,
+                                        dmrg_solve_info* infos, void* stream);
 /* Same, with x0 and x_out in host memory: the host-to-device copy of x0 and the
  * device-to-host copy of x_out are part of the call. */
 dmrg_status dmrg_davidson_solve_host(dmrg_plan* plan, const double* x0_host,

@@ -4,6 +4,8 @@ The compute path is the CUDA shared library built from ``csrc/`` (C ABI in
 ``include/dmrg.h``); ``capi`` is its ctypes binding.  Importing this package does not
 build or load anything; ``capi.load()`` raises if the library has not been built.
 """
-from .capi import DavidsonState, DmrgError, NotConverged, Plan, gemv_trans, load  # noqa: F401
+from .capi import (DavidsonState, DmrgError, NotConverged, Plan, gemv_trans, load,  # noqa: F401
+                   solve_batched)
 
-__all__ = ["Plan", "DavidsonState", "DmrgError", "NotConverged", "gemv_trans", "load"]
+__all__ = ["Plan", "DavidsonState", "DmrgError", "NotConverged", "gemv_trans", "load",
+           "solve_batched"]

@@ -69,7 +69,8 @@ class Options(C.Structure):
 class SolveInfo(C.Structure):
     _fields_ = [("energy", C.c_double), ("resnorm", C.c_double), ("iters", C.c_int32),
                 ("projections", C.c_int32), ("fp64_projections", C.c_int32),
-                ("restarts", C.c_int32), ("small_eig_sweeps", C.c_int32)]
+                ("restarts", C.c_int32), ("small_eig_sweeps", C.c_int32),
+                ("converged", C.c_int32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -107,6 +108,9 @@ SIGNATURES = {
                                       C.c_void_p]),
     "dmrg_davidson_solve_host": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p,
                                            C.POINTER(SolveInfo), C.c_void_p]),
+    "dmrg_davidson_solve_batched": (C.c_int, [C.POINTER(C.c_void_p), C.c_int32,
+                                              C.POINTER(C.c_void_p), C.POINTER(C.c_void_p),
+                                              C.POINTER(SolveInfo), C.c_void_p]),
     "dmrg_precision_available": (C.c_int32, [C.c_int]),
     "dmrg_kernel_launches": (C.c_int64, []),
     "dmrg_status_string": (C.c_char_p, [C.c_int]),
@@ -275,9 +279,9 @@ class Plan:
         st = self.lib.dmrg_davidson_solve(self.handle, x0.data_ptr(), x_out.data_ptr(),
                                           C.byref(info), _stream_ptr(stream))
         if st == 5 and not raise_on_nonconvergence:
-            return x_out, dict(info.as_dict(), converged=False)
+            return x_out, info.as_dict()
         _check(st)
-        return x_out, dict(info.as_dict(), converged=True)
+        return x_out, info.as_dict()
 
     def solve_host(self, x0: np.ndarray, x_out: Optional[np.ndarray] = None, stream=None):
         """Solve with host buffers: the copies in and out are part of the call."""
@@ -289,7 +293,7 @@ class Plan:
         info = SolveInfo()
         _check(self.lib.dmrg_davidson_solve_host(self.handle, x0.ctypes.data, x_out.ctypes.data,
                                                  C.byref(info), _stream_ptr(stream)))
-        return x_out, dict(info.as_dict(), converged=True)
+        return x_out, info.as_dict()
 
     def state(self, x0, stream=None) -> "DavidsonState":
         return DavidsonState(self, x0, stream)
@@ -330,6 +334,27 @@ class DavidsonState:
             self.close()
         except Exception:
             pass
+
+
+def solve_batched(plans, x0s, x_outs=None, stream=None, raise_on_nonconvergence=True):
+    """dmrg_davidson_solve_batched over a list of plans and device start vectors."""
+    torch = _torch()
+    nb = len(plans)
+    if len(x0s) != nb:
+        raise ValueError("one start vector per plan")
+    if x_outs is None:
+        x_outs = [torch.empty_like(x) for x in x0s]
+    for p, x, y in zip(plans, x0s, x_outs):
+        _check_vec(x, p.n, "x0")
+        _check_vec(y, p.n, "x_out")
+    hp = (C.c_void_p * max(1, nb))(*[p.handle.value for p in plans])
+    hx = (C.c_void_p * max(1, nb))(*[x.data_ptr() for x in x0s])
+    hy = (C.c_void_p * max(1, nb))(*[y.data_ptr() for y in x_outs])
+    infos = (SolveInfo * max(1, nb))()
+    st = load().dmrg_davidson_solve_batched(hp, nb, hx, hy, infos, _stream_ptr(stream))
+    if not (st == 5 and not raise_on_nonconvergence):
+        _check(st)
+    return x_outs, [infos[i].as_dict() for i in range(nb)]
 
 
 def tc_available(prec: str = "bf16x3") -> bool:

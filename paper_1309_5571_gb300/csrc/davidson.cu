@@ -30,6 +30,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <vector>
 
 #include "internal.h"
 
@@ -62,6 +63,9 @@ struct dmrg_davidson_state {
   double restart_rnorm = INFINITY;  // residual at the last subspace-limit restart
   double baked_err = 0.0; // low-precision error folded into W(:,0) by plain restarts
   double cur_err = 0.0;   // low-precision error of the current W y
+  bool cur_anchor = false;  // this iteration projects an FP64 anchor
+  int knew = 1;             // basis size after a restart decided in phase_b
+  bool did_restart = false;
 };
 
 namespace {
@@ -167,18 +171,22 @@ void dmrg_state_destroy(dmrg_davidson_state* s) {
   delete s;
 }
 
-dmrg_status dmrg_davidson_step(dmrg_davidson_state* s, void* stream, int32_t* converged) {
-  if (!s) {
-    set_error("NULL state");
-    return DMRG_ERR_INVALID_ARG;
-  }
-  cudaStream_t st = (cudaStream_t)stream;
-  if (converged) *converged = s->converged ? 1 : 0;
-  if (s->converged) return DMRG_OK;
+}  // extern "C"
+
+namespace {
+
+// A Davidson iteration runs in three host phases so that a batch of problems can share
+// each host synchronisation:
+//   phase_a  enqueue projection, overlap, Jacobi, residual; copy the small state back
+//   phase_b  (after a sync) read lambda, ||r||; decide convergence / anchor / restart;
+//            enqueue Gram-Schmidt and normalisation; copy the small state back
+//   phase_c  (after a sync) check for a basis breakdown, append the new column
+dmrg_status phase_a(dmrg_davidson_state* s, cudaStream_t st) {
   const int64_t ldv = s->ldv, n = s->n;
   const int k = s->k, col = k - 1;
   const bool anchor = s->mixed && s->anchor_pending;
   if (anchor) s->anchored = true;
+  s->cur_anchor = anchor;
   const bool fp64 = !s->mixed && s->plan->opt.prec == DMRG_PREC_FP64;
   DMRG_TRY(project_col(s, col, fp64 || anchor, st));
   s->anchor_pending = false;
@@ -186,9 +194,19 @@ dmrg_status dmrg_davidson_step(dmrg_davidson_state* s, void* stream, int32_t* co
   const double* w0 = (s->mixed && s->anchored) ? s->W : nullptr;
   DMRG_TRY(launch_overlap(s->vw, s->V, ldv, n, k, s->W + col * ldv, nullptr, s->small, col, st, w0));
   DMRG_TRY(launch_jacobi(s->small, k, st));
+  DMRG_TRY(launch_residual(s->vw, s->V, s->W, s->D, ldv, n, k, s->V + (int64_t)k * ldv, s->small, 0, st));
+  DMRG_CUDA_TRY(cudaMemcpyAsync(s->hsmall, s->small, sizeof(DevSmall), cudaMemcpyDeviceToHost, st));
+  return DMRG_OK;
+}
+
+dmrg_status phase_b(dmrg_davidson_state* s, cudaStream_t st, bool* need_c) {
+  *need_c = false;
+  DMRG_TRY(tc_error_status(s->plan));
+  const int64_t ldv = s->ldv, n = s->n;
+  const int k = s->k;
+  const bool anchor = s->cur_anchor;
+  const bool fp64 = !s->mixed && s->plan->opt.prec == DMRG_PREC_FP64;
   double* tcol = s->V + (int64_t)k * ldv;
-  DMRG_TRY(launch_residual(s->vw, s->V, s->W, s->D, ldv, n, k, tcol, s->small, 0, st));
-  DMRG_TRY(read_small(s, st));
   s->iters++;
   s->sweeps += s->hsmall->jacobi_sweeps;
   s->lambda = s->hsmall->lambda;
@@ -204,7 +222,6 @@ dmrg_status dmrg_davidson_step(dmrg_davidson_state* s, void* stream, int32_t* co
   s->ritz_k = k;
   if (s->rnorm <= tol && (exact || lowprec_plain)) {
     s->converged = true;
-    if (converged) *converged = 1;
     return DMRG_OK;
   }
   bool do_anchor = false, do_restart = false;
@@ -277,31 +294,69 @@ dmrg_status dmrg_davidson_step(dmrg_davidson_state* s, void* stream, int32_t* co
     s->ritz_k = 0;
     DMRG_TRY(launch_overlap(s->vw, s->V, ldv, n, knew, tcol, s->small->s[0], s->small, -1, st));
   }
-  // classical Gram-Schmidt, twice, then normalise
-  for (int attempt = 0; attempt < 2; ++attempt) {
+  s->knew = knew;
+  s->did_restart = do_restart;
+  // classical Gram-Schmidt (second pass only when needed), then normalise
+  DMRG_CUDA_TRY(cudaMemsetAsync(&s->small->flags, 0, sizeof(int32_t), st));
+  DMRG_TRY(launch_cgs(s->vw, s->V, ldv, n, knew, tcol, s->small, 0, 1, st, 0));
+  DMRG_TRY(launch_cgs(s->vw, s->V, ldv, n, knew, tcol, s->small, 1, 2, st, 1));
+  DMRG_TRY(launch_finish(tcol, n, s->small, st));
+  DMRG_CUDA_TRY(cudaMemcpyAsync(s->hsmall, s->small, sizeof(DevSmall), cudaMemcpyDeviceToHost, st));
+  *need_c = true;
+  return DMRG_OK;
+}
+
+dmrg_status phase_c(dmrg_davidson_state* s, cudaStream_t st) {
+  const int64_t ldv = s->ldv, n = s->n;
+  const int k = s->k, knew = s->knew;
+  double* tcol = s->V + (int64_t)k * ldv;
+  if (s->hsmall->flags & 1) {
+    // breakdown: fall back to the raw residual r (mode 1 writes t = r); after a restart
+    // the basis is [x] with W = [W y], so r = W(:,0) - lambda V(:,0)
+    if (s->did_restart) {
+      static const double e1[KMAX] = {1.0};
+      DMRG_CUDA_TRY(cudaMemcpyAsync(s->small->y, e1, sizeof(e1), cudaMemcpyHostToDevice, st));
+    }
+    DMRG_TRY(launch_residual(s->vw, s->V, s->W, s->D, ldv, n, knew, tcol, s->small, 1, st));
     DMRG_CUDA_TRY(cudaMemsetAsync(&s->small->flags, 0, sizeof(int32_t), st));
     DMRG_TRY(launch_cgs(s->vw, s->V, ldv, n, knew, tcol, s->small, 0, 1, st, 0));
     DMRG_TRY(launch_cgs(s->vw, s->V, ldv, n, knew, tcol, s->small, 1, 2, st, 1));
     DMRG_TRY(launch_finish(tcol, n, s->small, st));
     DMRG_TRY(read_small(s, st));
-    if (!(s->hsmall->flags & 1)) break;
-    if (attempt == 1) {
+    if (s->hsmall->flags & 1) {
       set_error("Davidson basis breakdown at iteration %d (||r|| = %g)", s->iters, s->rnorm);
       return DMRG_ERR_NUMERIC;
     }
-    // fall back to the raw residual r (mode 1 writes t = r) and orthogonalise again;
-    // after a restart the basis is [x] with W = [W y], so r = W(:,0) - lambda V(:,0)
-    if (do_restart) {
-      static const double e1[KMAX] = {1.0};
-      DMRG_CUDA_TRY(cudaMemcpyAsync(s->small->y, e1, sizeof(e1), cudaMemcpyHostToDevice, st));
-    }
-    DMRG_TRY(launch_residual(s->vw, s->V, s->W, s->D, ldv, n, knew, tcol, s->small, 1, st));
   }
   if (knew != k) {
     DMRG_CUDA_TRY(cudaMemcpyAsync(s->V + (int64_t)knew * ldv, tcol, sizeof(double) * ldv,
                                   cudaMemcpyDeviceToDevice, st));
   }
   s->k = knew + 1;
+  return DMRG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+dmrg_status dmrg_davidson_step(dmrg_davidson_state* s, void* stream, int32_t* converged) {
+  if (!s) {
+    set_error("NULL state");
+    return DMRG_ERR_INVALID_ARG;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  if (converged) *converged = s->converged ? 1 : 0;
+  if (s->converged) return DMRG_OK;
+  DMRG_TRY(phase_a(s, st));
+  DMRG_CUDA_TRY(cudaStreamSynchronize(st));
+  bool need_c = false;
+  DMRG_TRY(phase_b(s, st, &need_c));
+  if (need_c) {
+    DMRG_CUDA_TRY(cudaStreamSynchronize(st));
+    DMRG_TRY(phase_c(s, st));
+  }
+  if (converged) *converged = s->converged ? 1 : 0;
   return DMRG_OK;
 }
 
@@ -317,6 +372,7 @@ dmrg_status dmrg_state_get_info(const dmrg_davidson_state* s, dmrg_solve_info* i
   info->fp64_projections = s->fp64_projections;
   info->restarts = s->restarts;
   info->small_eig_sweeps = s->sweeps;
+  info->converged = s->converged ? 1 : 0;
   return DMRG_OK;
 }
 
@@ -401,6 +457,132 @@ dmrg_status dmrg_gemv_trans(const double* V, int64_t ldv, int64_t n, int32_t k,
     return DMRG_ERR_INVALID_ARG;
   }
   return launch_gemv_trans_public(V, ldv, n, k, w, s, (cudaStream_t)stream);
+}
+
+
+dmrg_status dmrg_davidson_solve_batched(dmrg_plan* const* plans, int32_t nb,
+                                        const double* const* x0, double* const* x_out,
+                                        dmrg_solve_info* infos, void* stream) {
+  if (nb < 0 || (nb > 0 && (!plans || !x0 || !x_out))) {
+    set_error("dmrg_davidson_solve_batched: bad argument");
+    return DMRG_ERR_INVALID_ARG;
+  }
+  for (int i = 0; i < nb; ++i) {
+    if (!plans[i] || !x0[i] || !x_out[i]) {
+      set_error("dmrg_davidson_solve_batched: NULL plan or vector at index %d", i);
+      return DMRG_ERR_INVALID_ARG;
+    }
+  }
+  if (nb == 0) return DMRG_OK;
+  cudaStream_t caller = (cudaStream_t)stream;
+  std::vector<cudaStream_t> sts(nb, nullptr);
+  std::vector<dmrg_davidson_state*> states(nb, nullptr);
+  std::vector<char> active(nb, 1);
+  std::vector<dmrg_status> status(nb, DMRG_OK);
+  cudaEvent_t start_ev = nullptr;
+  dmrg_status err = DMRG_OK;
+  if (cudaEventCreateWithFlags(&start_ev, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventRecord(start_ev, caller) != cudaSuccess) {
+    set_error("dmrg_davidson_solve_batched: event creation failed");
+    cudaEventDestroy(start_ev);
+    return DMRG_ERR_CUDA;
+  }
+  // one stream per distinct plan: a plan's projection scratch (operand images,
+  // intermediates) is shared by every projection made with it, so problems that share a
+  // plan are kept in order on one stream; problems with their own plans overlap
+  std::vector<cudaStream_t> owned;
+  std::vector<const dmrg_plan*> owner;
+  for (int i = 0; i < nb && err == DMRG_OK; ++i) {
+    int found = -1;
+    for (size_t u = 0; u < owner.size(); ++u)
+      if (owner[u] == plans[i]) found = (int)u;
+    if (found < 0) {
+      cudaStream_t ns = nullptr;
+      if (cudaStreamCreateWithFlags(&ns, cudaStreamNonBlocking) != cudaSuccess ||
+          cudaStreamWaitEvent(ns, start_ev, 0) != cudaSuccess) {
+        set_error("dmrg_davidson_solve_batched: stream creation failed");
+        if (ns) cudaStreamDestroy(ns);
+        err = DMRG_ERR_CUDA;
+        break;
+      }
+      owned.push_back(ns);
+      owner.push_back(plans[i]);
+      found = (int)owned.size() - 1;
+    }
+    sts[i] = owned[found];
+    err = dmrg_state_create(plans[i], x0[i], sts[i], &states[i]);
+  }
+  // lockstep: every phase is enqueued for all active problems before one wait for all
+  for (int it = 0; err == DMRG_OK; ++it) {
+    bool any = false;
+    for (int i = 0; i < nb; ++i) {
+      if (!active[i]) continue;
+      if (states[i]->converged || states[i]->iters >= plans[i]->opt.max_iter) {
+        active[i] = 0;
+        continue;
+      }
+      any = true;
+      status[i] = phase_a(states[i], sts[i]);
+      if (status[i] != DMRG_OK) active[i] = 0;
+    }
+    if (!any) break;
+    std::vector<char> need_c(nb, 0);
+    for (int i = 0; i < nb; ++i) {
+      if (!active[i]) continue;
+      if (cudaStreamSynchronize(sts[i]) != cudaSuccess) {
+        set_error("dmrg_davidson_solve_batched: %s", cudaGetErrorString(cudaGetLastError()));
+        err = DMRG_ERR_CUDA;
+        break;
+      }
+      bool c = false;
+      status[i] = phase_b(states[i], sts[i], &c);
+      need_c[i] = c;
+      if (status[i] != DMRG_OK) active[i] = 0;
+    }
+    if (err != DMRG_OK) break;
+    for (int i = 0; i < nb; ++i) {
+      if (!active[i] || !need_c[i]) continue;
+      if (cudaStreamSynchronize(sts[i]) != cudaSuccess) {
+        set_error("dmrg_davidson_solve_batched: %s", cudaGetErrorString(cudaGetLastError()));
+        err = DMRG_ERR_CUDA;
+        break;
+      }
+      status[i] = phase_c(states[i], sts[i]);
+      if (status[i] != DMRG_OK) active[i] = 0;
+    }
+  }
+  bool all_converged = true;
+  for (int i = 0; i < nb; ++i) {
+    if (!states[i]) {
+      all_converged = false;
+      continue;
+    }
+    dmrg_status r = dmrg_state_ritz(states[i], x_out[i], sts[i]);
+    if (status[i] == DMRG_OK) status[i] = r;
+    if (infos) {
+      dmrg_state_get_info(states[i], &infos[i]);
+      infos[i].converged = states[i]->converged ? 1 : 0;
+    }
+    if (!states[i]->converged) all_converged = false;
+    if (err == DMRG_OK && status[i] != DMRG_OK) err = status[i];
+  }
+  for (cudaStream_t os : owned) {
+    cudaEvent_t done = nullptr;
+    if (cudaEventCreateWithFlags(&done, cudaEventDisableTiming) == cudaSuccess) {
+      cudaEventRecord(done, os);
+      cudaStreamWaitEvent(caller, done, 0);
+      cudaEventDestroy(done);
+    }
+    cudaStreamSynchronize(os);
+  }
+  for (int i = 0; i < nb; ++i) dmrg_state_destroy(states[i]);
+  for (cudaStream_t os : owned) cudaStreamDestroy(os);
+  cudaEventDestroy(start_ev);
+  if (err == DMRG_OK && !all_converged) {
+    set_error("dmrg_davidson_solve_batched: at least one problem did not converge");
+    err = DMRG_ERR_NOT_CONVERGED;
+  }
+  return err;
 }
 
 }  // extern "C"
