@@ -263,11 +263,13 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--prec", default="auto", choices=["auto", "fp64", "tf32", "bf16x3"])
+    ap.add_argument("--prec", default="auto", choices=["auto", "fp64", "tf32", "bf16x3", "fp64tc"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--proj-reps", type=int, default=10)
     ap.add_argument("--mode", default="solve", choices=["solve", "project", "peaks", "batched"])
     ap.add_argument("--batch", type=int, default=64)
+    ap.add_argument("--anchor", default="fp64tc", choices=["fp64", "fp64tc"],
+                    help="FP64-accurate projections of the mixed modes")
     ap.add_argument("--workload", default=WORKLOAD)
     args = ap.parse_args()
     if args.impl == "reference":
@@ -303,7 +305,7 @@ def main():
     stream = torch.cuda.current_stream()
 
     t0 = time.perf_counter()
-    plan = Plan(sb, prec=prec, tol=1e-10)
+    plan = Plan(sb, prec=prec, tol=1e-10, anchor_prec=args.anchor)
     torch.cuda.synchronize()
     plan_ms = (time.perf_counter() - t0) * 1e3
     flops = plan.stats["flops"]
@@ -350,7 +352,7 @@ def main():
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     y = torch.empty_like(x0_t)
     proj = {}
-    for p in sorted({prec, "fp64"}):
+    for p in sorted({prec, "fp64", "fp64tc"}):
         for _ in range(2):
             plan.project(x0_t, y, prec=p)
         times = []

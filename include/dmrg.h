@@ -62,13 +62,22 @@ typedef enum {
   DMRG_ERR_UNSUPPORTED = 7    /* option not available in this build                    */
 } dmrg_status;
 
-/* Arithmetic of the projection GEMMs.  FP64: float64 operands and accumulation.
- * TF32: operands rounded to TF32 on the tensor cores, FP32 accumulation.
+/* Arithmetic of the projection GEMMs.  FP64: float64 operands and accumulation on the
+ * FP64 units.  TF32: operands rounded to TF32 on the tensor cores, FP32 accumulation.
  * BF16X3: every operand split into three BF16 terms x = x0 + x1 + x2, the six products
- * with i + j <= 2 accumulated in FP32 on the tensor cores.  The Davidson vector work
- * (overlaps, Gram-Schmidt, Rayleigh quotient, residual, small eigenproblem) is always
+ * with i + j <= 2 accumulated in FP32 on the tensor cores.  FP64_TC: FP64-accurate
+ * products on the tensor cores: every operand row chunk (256 K elements) is split into a
+ * power-of-two scale and seven integer base-128 digits held exactly in BF16; digit
+ * products sharing a scale are summed exactly in FP32 and the scaled sums are combined in
+ * FP32-pair (about 48-bit) arithmetic, then converted to float64.  The Davidson vector
+ * work (overlaps, Gram-Schmidt, Rayleigh quotient, residual, small eigenproblem) is always
  * float64. */
-typedef enum { DMRG_PREC_FP64 = 0, DMRG_PREC_TF32 = 1, DMRG_PREC_BF16X3 = 2 } dmrg_precision;
+typedef enum {
+  DMRG_PREC_FP64 = 0,
+  DMRG_PREC_TF32 = 1,
+  DMRG_PREC_BF16X3 = 2,
+  DMRG_PREC_FP64_TC = 3
+} dmrg_precision;
 
 enum { DMRG_HOST_DATA = 0, DMRG_DEVICE_DATA = 1 };
 enum { DMRG_IDENTITY_OP = -1 };
@@ -116,6 +125,8 @@ typedef struct {
   double refine_ratio;   /* if > 0, also re-anchor when the low-precision residual has
                             fallen by this factor below the last FP64 residual (0: only
                             the adaptive floor test and the subspace limit re-anchor)     */
+  dmrg_precision anchor_prec; /* FP64-accurate projections of the mixed modes: DMRG_PREC_FP64
+                            (FP64 units, default) or DMRG_PREC_FP64_TC (tensor cores)     */
 } dmrg_options;
 
 typedef struct {

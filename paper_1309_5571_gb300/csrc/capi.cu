@@ -32,6 +32,7 @@ void dmrg_options_default(dmrg_options* opt) {
   opt->max_subspace = 20;
   opt->fp64_refine = 1;
   opt->refine_ratio = 0.0;
+  opt->anchor_prec = DMRG_PREC_FP64;
 }
 
 const char* dmrg_status_string(dmrg_status s) {

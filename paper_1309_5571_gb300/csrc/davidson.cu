@@ -87,9 +87,12 @@ dmrg_status read_small(dmrg_davidson_state* s, cudaStream_t st) {
 }
 
 dmrg_status project_col(dmrg_davidson_state* s, int col, bool fp64, cudaStream_t st) {
-  dmrg_precision prec = fp64 ? DMRG_PREC_FP64 : s->plan->opt.prec;
+  // FP64-accurate projections (FP64 mode, or an anchor of a mixed mode) use FP64 units
+  // or the FP64-emulating tensor-core path, as the options say
+  dmrg_precision prec = s->plan->opt.prec;
+  if (fp64) prec = s->plan->opt.prec == DMRG_PREC_FP64_TC ? DMRG_PREC_FP64_TC : s->plan->opt.anchor_prec;
   DMRG_TRY(dmrg_project_prec(s->plan, prec, s->V + col * s->ldv, s->W + col * s->ldv, st));
-  if (prec == DMRG_PREC_FP64) s->fp64_projections++;
+  if (prec == DMRG_PREC_FP64 || prec == DMRG_PREC_FP64_TC) s->fp64_projections++;
   else s->projections++;
   return DMRG_OK;
 }
@@ -119,7 +122,8 @@ dmrg_status dmrg_state_create(dmrg_plan* plan, const double* x0, void* stream,
   s->n = plan->n;
   s->ldv = round_up(plan->n, 32);
   s->kmax = plan->opt.max_subspace;
-  s->mixed = plan->opt.prec != DMRG_PREC_FP64 && plan->opt.fp64_refine;
+  s->mixed = plan->opt.prec != DMRG_PREC_FP64 && plan->opt.prec != DMRG_PREC_FP64_TC &&
+             plan->opt.fp64_refine;
   auto fail = [&](dmrg_status e) { dmrg_state_destroy(s); return e; };
   const size_t col = sizeof(double) * (size_t)s->ldv;
   if (cudaMalloc((void**)&s->V, col * (s->kmax + 1)) != cudaSuccess ||
@@ -187,7 +191,8 @@ dmrg_status phase_a(dmrg_davidson_state* s, cudaStream_t st) {
   const bool anchor = s->mixed && s->anchor_pending;
   if (anchor) s->anchored = true;
   s->cur_anchor = anchor;
-  const bool fp64 = !s->mixed && s->plan->opt.prec == DMRG_PREC_FP64;
+  const bool fp64 = !s->mixed && (s->plan->opt.prec == DMRG_PREC_FP64 ||
+                                   s->plan->opt.prec == DMRG_PREC_FP64_TC);
   DMRG_TRY(project_col(s, col, fp64 || anchor, st));
   s->anchor_pending = false;
   // after an FP64 anchor, the anchor row of B comes from the exact column W(:,0)
@@ -205,7 +210,8 @@ dmrg_status phase_b(dmrg_davidson_state* s, cudaStream_t st, bool* need_c) {
   const int64_t ldv = s->ldv, n = s->n;
   const int k = s->k;
   const bool anchor = s->cur_anchor;
-  const bool fp64 = !s->mixed && s->plan->opt.prec == DMRG_PREC_FP64;
+  const bool fp64 = !s->mixed && (s->plan->opt.prec == DMRG_PREC_FP64 ||
+                                   s->plan->opt.prec == DMRG_PREC_FP64_TC);
   double* tcol = s->V + (int64_t)k * ldv;
   s->iters++;
   s->sweeps += s->hsmall->jacobi_sweeps;

@@ -103,6 +103,7 @@ struct HostBlock {
 };
 
 struct TcPlan;           // tensor-core (low precision) part, see gemm_tc.cu
+struct OzPlan;           // FP64-accurate tensor-core part, see gemm_oz.cu
 
 }  // namespace dmrg
 
@@ -133,6 +134,7 @@ struct dmrg_plan {
   size_t device_bytes = 0;
 
   dmrg::TcPlan* tc[2] = {nullptr, nullptr};  // TF32, BF16x3; built on first use
+  dmrg::OzPlan* oz = nullptr;                 // FP64 emulation; built on first use
 };
 
 namespace dmrg {
@@ -145,6 +147,10 @@ dmrg_status launch_project_tc(dmrg_plan* plan, dmrg_precision prec, const double
 void destroy_tc(dmrg_plan* plan);
 bool tc_available(dmrg_precision prec);
 dmrg_status tc_error_status(dmrg_plan* plan);
+// gemm_oz.cu
+dmrg_status launch_project_oz(dmrg_plan* plan, const double* x, double* y, cudaStream_t stream);
+void destroy_oz(dmrg_plan* plan);
+dmrg_status oz_error_status(dmrg_plan* plan);
 
 // vec.cu -- Davidson vector kernels
 constexpr int KMAX = DMRG_MAX_SUBSPACE;

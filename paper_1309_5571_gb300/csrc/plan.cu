@@ -425,7 +425,8 @@ dmrg_status dmrg_plan_create(const dmrg_superblock_desc* desc, const dmrg_option
   if (opt) p->opt = *opt; else dmrg_options_default(&p->opt);
   if (p->opt.max_subspace < 2 || p->opt.max_subspace > DMRG_MAX_SUBSPACE ||
       p->opt.max_iter < 1 || !(p->opt.tol >= 0.0) ||
-      (int)p->opt.prec < 0 || (int)p->opt.prec > 2) {
+      (int)p->opt.prec < 0 || (int)p->opt.prec > 3 ||
+      (p->opt.anchor_prec != DMRG_PREC_FP64 && p->opt.anchor_prec != DMRG_PREC_FP64_TC)) {
     set_error("options out of range (max_subspace must be in [2, %d])", DMRG_MAX_SUBSPACE);
     delete p;
     return DMRG_ERR_INVALID_ARG;
@@ -483,6 +484,7 @@ dmrg_status dmrg_plan_create(const dmrg_superblock_desc* desc, const dmrg_option
 void dmrg_plan_destroy(dmrg_plan* p) {
   if (!p) return;
   destroy_tc(p);
+  destroy_oz(p);
   cudaFree(p->arena);
   cudaFree(p->T);
   cudaFree(p->D);
@@ -531,6 +533,7 @@ dmrg_status dmrg_project_prec(dmrg_plan* p, dmrg_precision prec, const double* x
   }
   cudaStream_t st = (cudaStream_t)stream;
   if (prec == DMRG_PREC_FP64) return launch_project_fp64(p, x, y, st);
+  if (prec == DMRG_PREC_FP64_TC) return launch_project_oz(p, x, y, st);
   if (prec == DMRG_PREC_TF32 || prec == DMRG_PREC_BF16X3) return launch_project_tc(p, prec, x, y, st);
   set_error("unknown precision %d", (int)prec);
   return DMRG_ERR_INVALID_ARG;

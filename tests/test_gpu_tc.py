@@ -95,3 +95,53 @@ def test_full_size_mixed_solve_hubbard_m2048_properties(hub_L64_m2048):
     rq = float(x @ Hx) / float(x @ x)
     assert abs(rq - info["energy"]) <= E_TOL
     assert np.linalg.norm(Hx - info["energy"] * x) <= 1.5e-10
+
+
+# ---------------------------------------------------------------- FP64-accurate tensor cores
+@pytest.mark.parametrize("name", list(PROBLEMS))
+def test_projection_fp64tc_matches_oracle(name):
+    # exact digit products: the FP64 bar of 1e-12 (relative to max|y|) applies
+    sb = problem(name)
+    plan = Plan(sb, prec="fp64tc")
+    for seed in (0, 1):
+        x = np.random.default_rng(seed).standard_normal(sb.n)
+        y = plan.project(cuda(x)).cpu().numpy()
+        assert rel_err(y, oproj.project_blocks(sb, x)) <= 1e-12
+
+
+def test_projection_fp64tc_scaled_inputs():
+    # rows whose magnitudes differ by many orders: per-row, per-chunk scales
+    sb = problem("hub_L8_m40")
+    plan = Plan(sb, prec="fp64tc")
+    x = np.random.default_rng(9).standard_normal(sb.n) * np.exp(np.random.default_rng(8).uniform(-20, 20, sb.n))
+    y = plan.project(cuda(x)).cpu().numpy()
+    y_ref = oproj.project_blocks(sb, x)
+    assert rel_err(y, y_ref) <= 1e-12
+
+
+@pytest.mark.parametrize("name", ["heis_L16_m64", "hub_quarter_L12_m48", "ragged"])
+def test_davidson_fp64tc_matches_oracle(name):
+    sb = problem(name)
+    x0 = warmup.start_vector(sb.n, seed=0)
+    x, info = Plan(sb, prec="fp64tc").solve(cuda(x0))
+    lam, xo, _ = odav.davidson(lambda v: oproj.project_blocks(sb, v), oproj.diagonal(sb), x0)
+    assert abs(info["energy"] - lam) <= E_TOL
+    x = x.cpu().numpy()
+    assert np.linalg.norm(oproj.project_blocks(sb, x) - info["energy"] * x) <= 1.5e-10
+
+
+@pytest.mark.parametrize("name", ["heis_L16_m64", "hub_L8_m40"])
+def test_mixed_davidson_with_fp64tc_anchors(name):
+    sb = problem(name)
+    x0 = warmup.start_vector(sb.n, seed=0)
+    x, info = Plan(sb, prec="bf16x3", anchor_prec="fp64tc").solve(cuda(x0))
+    lam = odav.davidson(lambda v: oproj.project_blocks(sb, v), oproj.diagonal(sb), x0)[0]
+    assert abs(info["energy"] - lam) <= E_TOL and info["fp64_projections"] >= 1
+
+
+def test_full_size_projection_hubbard_m2048_fp64tc(hub_L64_m2048):
+    sb = hub_L64_m2048
+    plan = Plan(sb, prec="fp64tc")
+    x = warmup.start_vector(sb.n, seed=5)
+    y = plan.project(cuda(x)).cpu().numpy()
+    assert rel_err(y, oproj.project_blocks(sb, x)) <= 1e-12
