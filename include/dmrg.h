@@ -127,6 +127,10 @@ typedef struct {
                             the adaptive floor test and the subspace limit re-anchor)     */
   dmrg_precision anchor_prec; /* FP64-accurate projections of the mixed modes: DMRG_PREC_FP64
                             (FP64 units, default) or DMRG_PREC_FP64_TC (tensor cores)     */
+  int32_t vector_fp64;   /* Davidson vector passes on the FP64 units (1, default) or in
+                            double-float FP32-pair arithmetic, ~48 bits, on the FP32 units
+                            (0; measured slower on GB300 at the sizes tested, kept as an
+                            option); vectors are float64 in memory either way             */
 } dmrg_options;
 
 typedef struct {

@@ -63,7 +63,8 @@ class SuperblockDesc(C.Structure):
 class Options(C.Structure):
     _fields_ = [("prec", C.c_int32), ("tol", C.c_double), ("max_iter", C.c_int32),
                 ("max_subspace", C.c_int32), ("fp64_refine", C.c_int32),
-                ("refine_ratio", C.c_double), ("anchor_prec", C.c_int32)]
+                ("refine_ratio", C.c_double), ("anchor_prec", C.c_int32),
+                ("vector_fp64", C.c_int32)]
 
 
 class SolveInfo(C.Structure):
@@ -211,7 +212,7 @@ def marshal(sb) -> _Marshalled:
 
 
 def options(prec="fp64", tol=1e-10, max_iter=1000, max_subspace=20, fp64_refine=True,
-            refine_ratio=0.0, anchor_prec="fp64") -> Options:
+            refine_ratio=0.0, anchor_prec="fp64", vector_fp64=True) -> Options:
     o = Options()
     load().dmrg_options_default(C.byref(o))
     o.prec = PREC[prec] if isinstance(prec, str) else int(prec)
@@ -221,6 +222,7 @@ def options(prec="fp64", tol=1e-10, max_iter=1000, max_subspace=20, fp64_refine=
     o.fp64_refine = int(bool(fp64_refine))
     o.refine_ratio = refine_ratio
     o.anchor_prec = PREC[anchor_prec] if isinstance(anchor_prec, str) else int(anchor_prec)
+    o.vector_fp64 = int(bool(vector_fp64))
     return o
 
 

@@ -86,6 +86,25 @@ dmrg_status read_small(dmrg_davidson_state* s, cudaStream_t st) {
   return tc_error_status(s->plan);
 }
 
+// vector passes: FP64 units or double-float arithmetic on the FP32 units (vec_df.cu)
+dmrg_status ov(dmrg_davidson_state* s, int k, const double* vec, double* s_out, int Bcol,
+               cudaStream_t st, const double* w0 = nullptr) {
+  if (s->plan->opt.vector_fp64)
+    return launch_overlap(s->vw, s->V, s->ldv, s->n, k, vec, s_out, s->small, Bcol, st, w0);
+  return launch_overlap_df(s->vw, s->V, s->ldv, s->n, k, vec, s_out, s->small, Bcol, st, w0);
+}
+dmrg_status res(dmrg_davidson_state* s, int k, double* tcol, int mode, cudaStream_t st) {
+  if (s->plan->opt.vector_fp64)
+    return launch_residual(s->vw, s->V, s->W, s->D, s->ldv, s->n, k, tcol, s->small, mode, st);
+  return launch_residual_df(s->vw, s->V, s->W, s->D, s->ldv, s->n, k, tcol, s->small, mode, st);
+}
+dmrg_status cgs(dmrg_davidson_state* s, int k, double* tcol, int sin, int sout, int second,
+                cudaStream_t st) {
+  if (s->plan->opt.vector_fp64)
+    return launch_cgs(s->vw, s->V, s->ldv, s->n, k, tcol, s->small, sin, sout, st, second);
+  return launch_cgs_df(s->vw, s->V, s->ldv, s->n, k, tcol, s->small, sin, sout, st, second);
+}
+
 dmrg_status project_col(dmrg_davidson_state* s, int col, bool fp64, cudaStream_t st) {
   // FP64-accurate projections (FP64 mode, or an anchor of a mixed mode) use FP64 units
   // or the FP64-emulating tensor-core path, as the options say
@@ -197,9 +216,9 @@ dmrg_status phase_a(dmrg_davidson_state* s, cudaStream_t st) {
   s->anchor_pending = false;
   // after an FP64 anchor, the anchor row of B comes from the exact column W(:,0)
   const double* w0 = (s->mixed && s->anchored) ? s->W : nullptr;
-  DMRG_TRY(launch_overlap(s->vw, s->V, ldv, n, k, s->W + col * ldv, nullptr, s->small, col, st, w0));
+  DMRG_TRY(ov(s, k, s->W + col * ldv, nullptr, col, st, w0));
   DMRG_TRY(launch_jacobi(s->small, k, st));
-  DMRG_TRY(launch_residual(s->vw, s->V, s->W, s->D, ldv, n, k, s->V + (int64_t)k * ldv, s->small, 0, st));
+  DMRG_TRY(res(s, k, s->V + (int64_t)k * ldv, 0, st));
   DMRG_CUDA_TRY(cudaMemcpyAsync(s->hsmall, s->small, sizeof(DevSmall), cudaMemcpyDeviceToHost, st));
   return DMRG_OK;
 }
@@ -298,14 +317,14 @@ dmrg_status phase_b(dmrg_davidson_state* s, cudaStream_t st, bool* need_c) {
     s->plain_restarts++;
     s->baked_err += s->cur_err;
     s->ritz_k = 0;
-    DMRG_TRY(launch_overlap(s->vw, s->V, ldv, n, knew, tcol, s->small->s[0], s->small, -1, st));
+    DMRG_TRY(ov(s, knew, tcol, s->small->s[0], -1, st));
   }
   s->knew = knew;
   s->did_restart = do_restart;
   // classical Gram-Schmidt (second pass only when needed), then normalise
   DMRG_CUDA_TRY(cudaMemsetAsync(&s->small->flags, 0, sizeof(int32_t), st));
-  DMRG_TRY(launch_cgs(s->vw, s->V, ldv, n, knew, tcol, s->small, 0, 1, st, 0));
-  DMRG_TRY(launch_cgs(s->vw, s->V, ldv, n, knew, tcol, s->small, 1, 2, st, 1));
+  DMRG_TRY(cgs(s, knew, tcol, 0, 1, 0, st));
+  DMRG_TRY(cgs(s, knew, tcol, 1, 2, 1, st));
   DMRG_TRY(launch_finish(tcol, n, s->small, st));
   DMRG_CUDA_TRY(cudaMemcpyAsync(s->hsmall, s->small, sizeof(DevSmall), cudaMemcpyDeviceToHost, st));
   *need_c = true;
@@ -323,10 +342,10 @@ dmrg_status phase_c(dmrg_davidson_state* s, cudaStream_t st) {
       static const double e1[KMAX] = {1.0};
       DMRG_CUDA_TRY(cudaMemcpyAsync(s->small->y, e1, sizeof(e1), cudaMemcpyHostToDevice, st));
     }
-    DMRG_TRY(launch_residual(s->vw, s->V, s->W, s->D, ldv, n, knew, tcol, s->small, 1, st));
+    DMRG_TRY(res(s, knew, tcol, 1, st));
     DMRG_CUDA_TRY(cudaMemsetAsync(&s->small->flags, 0, sizeof(int32_t), st));
-    DMRG_TRY(launch_cgs(s->vw, s->V, ldv, n, knew, tcol, s->small, 0, 1, st, 0));
-    DMRG_TRY(launch_cgs(s->vw, s->V, ldv, n, knew, tcol, s->small, 1, 2, st, 1));
+    DMRG_TRY(cgs(s, knew, tcol, 0, 1, 0, st));
+    DMRG_TRY(cgs(s, knew, tcol, 1, 2, 1, st));
     DMRG_TRY(launch_finish(tcol, n, s->small, st));
     DMRG_TRY(read_small(s, st));
     if (s->hsmall->flags & 1) {

@@ -207,6 +207,16 @@ dmrg_status launch_ritz(const double* V, const double* W, int64_t ldv, int64_t n
 dmrg_status launch_normalize(const VecWork& w, const double* src, double* dst, int64_t n,
                              DevSmall* small, cudaStream_t st);
 dmrg_status launch_set_B00(DevSmall* small, cudaStream_t st);
+// vec_df.cu -- the same passes in double-float (FP32 pair) arithmetic
+dmrg_status launch_overlap_df(const VecWork& w, const double* V, int64_t ldv, int64_t n, int k,
+                              const double* vec, double* s_out, DevSmall* small, int Bcol,
+                              cudaStream_t st, const double* w0 = nullptr);
+dmrg_status launch_residual_df(const VecWork& w, const double* V, const double* W,
+                               const double* D, int64_t ldv, int64_t n, int k, double* tcol,
+                               DevSmall* small, int mode, cudaStream_t st);
+dmrg_status launch_cgs_df(const VecWork& w, const double* V, int64_t ldv, int64_t n, int k,
+                          double* tcol, DevSmall* small, int sin, int sout, cudaStream_t st,
+                          int second = 0);
 dmrg_status launch_gemv_trans_public(const double* V, int64_t ldv, int64_t n, int k,
                                      const double* w, double* s, cudaStream_t st);
 

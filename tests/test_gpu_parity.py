@@ -205,3 +205,15 @@ def test_full_size_solve_heisenberg_m1024_properties(heis_L100_m1024):
     rq = float(x @ Hx) / float(x @ x)
     assert abs(rq - info["energy"]) <= E_TOL
     assert np.linalg.norm(Hx - info["energy"] * x) <= 1.5e-10
+
+
+@pytest.mark.parametrize("vector_fp64", [True, False])
+def test_vector_arithmetic_options_match_oracle(vector_fp64):
+    # Davidson vector passes on the FP64 units or in double-float FP32-pair arithmetic
+    sb = problem("hub_quarter_L12_m48")
+    x0 = warmup.start_vector(sb.n, seed=2)
+    x, info = Plan(sb, prec="fp64", vector_fp64=vector_fp64).solve(cuda(x0))
+    lam = odav.davidson(lambda v: oproj.project_blocks(sb, v), oproj.diagonal(sb), x0)[0]
+    assert abs(info["energy"] - lam) <= E_TOL
+    x = x.cpu().numpy()
+    assert np.linalg.norm(oproj.project_blocks(sb, x) - info["energy"] * x) <= 1.5e-10
