@@ -113,6 +113,22 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(value: float, device=None) -> float:
+    """The slowest rank's time (weak scaling: every rank solves its own replica)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return value
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank: float, world: int, seconds: float) -> float:
+    """Whole-job throughput: the units all ranks processed divided by the max time."""
+    return units_per_rank * world / seconds
+
+
 def cpu_oracle_projection_sample(sb, x, budget_s=15.0):
     """Time the FP64 oracle's projection (Eq. 11 in NumPy) on the host cores."""
     from oracle import projection as oproj
@@ -333,13 +349,9 @@ def main():
         ev1.record(stream)
         barrier()
     launches = capi.kernel_launches() - launches0
-    t_step = ev0.elapsed_time(ev1) / 1e3 / args.steps
-    if ws > 1:
-        tt = torch.tensor([t_step], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_step = float(tt.item())
+    t_step = max_over_ranks(ev0.elapsed_time(ev1) / 1e3 / args.steps, device="cuda")
     proj_per_step = statistics.mean(i["projections"] + i["fp64_projections"] for i in infos)
-    value = ws * proj_per_step * flops / t_step / 1e12
+    value = job_throughput(proj_per_step * flops, ws, t_step) / 1e12
 
     # ---- end to end through the host-buffer entry point (copies inside the timing)
     torch.cuda.synchronize()
@@ -390,8 +402,11 @@ def main():
         bound, peak, unit = "tensor", pk["bf16_tflops"] / 6.0, "TFLOP/s"
         peak_note = f"{pk_kind} bf16 burst / 6 products (algorithmic FLOPs of a BF16x3 GEMM)"
     achieved = flops / proj[prec] / 1e12
+    # DRAM bytes of one BF16x3 projection (pack + two tcgen05 launches) from the ncu capture
+    # in profiles/tc_gemm_bf16x3_hub_L64_m2048.md (same kernels as timed here)
+    traffic = 517.6e6 if (prec == "bf16x3" and args.workload == WORKLOAD) else None
     roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
-                "frac": achieved / peak, "traffic": None, "kernel": f"projection ({prec})",
+                "frac": achieved / peak, "traffic": traffic, "kernel": f"projection ({prec})",
                 "peak_source": peak_note}
 
     # ---- CPU oracle baseline (rank 0, N = 1 only), bounded sample
