@@ -116,6 +116,23 @@ typedef struct {
   int32_t data_location;          /* DMRG_HOST_DATA or DMRG_DEVICE_DATA               */
 } dmrg_superblock_desc;
 
+/* Arithmetic of the Davidson vector passes (overlap, residual, Gram-Schmidt; the paper
+   runs them in FP64, Sec. 6.1).  GB300 executes about 0.55 T FP64 FMA/s against 6.8 TB/s
+   of HBM, so the FP64 passes are bound by the FP64 units.
+   DMRG_VEC_FP64          FP64 units throughout.
+   DMRG_VEC_DOUBLE_FLOAT  double-float (FP32 pairs, ~48 bits) on the FP32 units; measured
+                          slower than FP64 at the sizes tested, kept as an option.
+   DMRG_VEC_SPLIT         mixed modes only (TF32/BF16X3 with fp64_refine): basis column 0
+                          (the FP64 anchor) in FP64, the low-precision columns in FP32
+                          arithmetic, whose rounding stays far below their projection
+                          error; anchor iterations and the convergence test stay FP64.
+                          In FP64 and FP64_TC solves this is DMRG_VEC_FP64.             */
+typedef enum {
+  DMRG_VEC_FP64 = 0,
+  DMRG_VEC_DOUBLE_FLOAT = 1,
+  DMRG_VEC_SPLIT = 2
+} dmrg_vector_arith;
+
 typedef struct {
   dmrg_precision prec;   /* projection arithmetic inside Davidson (default FP64)          */
   double tol;            /* stop when ||H x - lambda x||_2 <= tol, ||x|| = 1 (1e-10)      */
@@ -127,10 +144,9 @@ typedef struct {
                             the adaptive floor test and the subspace limit re-anchor)     */
   dmrg_precision anchor_prec; /* FP64-accurate projections of the mixed modes: DMRG_PREC_FP64
                             (FP64 units, default) or DMRG_PREC_FP64_TC (tensor cores)     */
-  int32_t vector_fp64;   /* Davidson vector passes on the FP64 units (1, default) or in
-                            double-float FP32-pair arithmetic, ~48 bits, on the FP32 units
-                            (0; measured slower on GB300 at the sizes tested, kept as an
-                            option); vectors are float64 in memory either way             */
+  int32_t vector_arith;  /* arithmetic of the Davidson vector passes (dmrg_vector_arith);
+                            vectors are float64 in memory in every mode (default
+                            DMRG_VEC_SPLIT)                                              */
 } dmrg_options;
 
 typedef struct {

@@ -18,6 +18,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libdmrg_gb300.so")
 
 PREC = {"fp64": 0, "tf32": 1, "bf16x3": 2, "fp64tc": 3}
+VEC = {"fp64": 0, "df": 1, "split": 2}
 IDENTITY = -1
 MAX_SUBSPACE = 24
 
@@ -64,7 +65,7 @@ class Options(C.Structure):
     _fields_ = [("prec", C.c_int32), ("tol", C.c_double), ("max_iter", C.c_int32),
                 ("max_subspace", C.c_int32), ("fp64_refine", C.c_int32),
                 ("refine_ratio", C.c_double), ("anchor_prec", C.c_int32),
-                ("vector_fp64", C.c_int32)]
+                ("vector_arith", C.c_int32)]
 
 
 class SolveInfo(C.Structure):
@@ -212,7 +213,7 @@ def marshal(sb) -> _Marshalled:
 
 
 def options(prec="fp64", tol=1e-10, max_iter=1000, max_subspace=20, fp64_refine=True,
-            refine_ratio=0.0, anchor_prec="fp64", vector_fp64=True) -> Options:
+            refine_ratio=0.0, anchor_prec="fp64", vector_arith="split") -> Options:
     o = Options()
     load().dmrg_options_default(C.byref(o))
     o.prec = PREC[prec] if isinstance(prec, str) else int(prec)
@@ -222,7 +223,7 @@ def options(prec="fp64", tol=1e-10, max_iter=1000, max_subspace=20, fp64_refine=
     o.fp64_refine = int(bool(fp64_refine))
     o.refine_ratio = refine_ratio
     o.anchor_prec = PREC[anchor_prec] if isinstance(anchor_prec, str) else int(anchor_prec)
-    o.vector_fp64 = int(bool(vector_fp64))
+    o.vector_arith = VEC[vector_arith] if isinstance(vector_arith, str) else int(vector_arith)
     return o
 
 

@@ -33,7 +33,7 @@ void dmrg_options_default(dmrg_options* opt) {
   opt->fp64_refine = 1;
   opt->refine_ratio = 0.0;
   opt->anchor_prec = DMRG_PREC_FP64;
-  opt->vector_fp64 = 1;
+  opt->vector_arith = DMRG_VEC_SPLIT;
 }
 
 const char* dmrg_status_string(dmrg_status s) {

@@ -86,23 +86,50 @@ dmrg_status read_small(dmrg_davidson_state* s, cudaStream_t st) {
   return tc_error_status(s->plan);
 }
 
-// vector passes: FP64 units or double-float arithmetic on the FP32 units (vec_df.cu)
+// vector passes: FP64 units, double-float arithmetic on the FP32 units (vec_df.cu), or,
+// in the mixed modes, FP64 for the anchor column and FP32 for the others (vec_split.cu)
+int vec_mode(const dmrg_davidson_state* s) {
+  const int a = s->plan->opt.vector_arith;
+  if (a == DMRG_VEC_SPLIT) return s->mixed ? DMRG_VEC_SPLIT : DMRG_VEC_FP64;
+  return a;
+}
 dmrg_status ov(dmrg_davidson_state* s, int k, const double* vec, double* s_out, int Bcol,
                cudaStream_t st, const double* w0 = nullptr) {
-  if (s->plan->opt.vector_fp64)
-    return launch_overlap(s->vw, s->V, s->ldv, s->n, k, vec, s_out, s->small, Bcol, st, w0);
-  return launch_overlap_df(s->vw, s->V, s->ldv, s->n, k, vec, s_out, s->small, Bcol, st, w0);
+  switch (vec_mode(s)) {
+    case DMRG_VEC_SPLIT:
+      return launch_overlap_split(s->vw, s->V, s->ldv, s->n, k, vec, s_out, s->small, Bcol, st, w0);
+    case DMRG_VEC_DOUBLE_FLOAT:
+      return launch_overlap_df(s->vw, s->V, s->ldv, s->n, k, vec, s_out, s->small, Bcol, st, w0);
+    default:
+      return launch_overlap(s->vw, s->V, s->ldv, s->n, k, vec, s_out, s->small, Bcol, st, w0);
+  }
 }
 dmrg_status res(dmrg_davidson_state* s, int k, double* tcol, int mode, cudaStream_t st) {
-  if (s->plan->opt.vector_fp64)
-    return launch_residual(s->vw, s->V, s->W, s->D, s->ldv, s->n, k, tcol, s->small, mode, st);
-  return launch_residual_df(s->vw, s->V, s->W, s->D, s->ldv, s->n, k, tcol, s->small, mode, st);
+  switch (vec_mode(s)) {
+    case DMRG_VEC_SPLIT:
+      return launch_residual_split(s->vw, s->V, s->W, s->D, s->ldv, s->n, k, tcol, s->small, mode, st);
+    case DMRG_VEC_DOUBLE_FLOAT:
+      return launch_residual_df(s->vw, s->V, s->W, s->D, s->ldv, s->n, k, tcol, s->small, mode, st);
+    default:
+      return launch_residual(s->vw, s->V, s->W, s->D, s->ldv, s->n, k, tcol, s->small, mode, st);
+  }
 }
 dmrg_status cgs(dmrg_davidson_state* s, int k, double* tcol, int sin, int sout, int second,
                 cudaStream_t st) {
-  if (s->plan->opt.vector_fp64)
-    return launch_cgs(s->vw, s->V, s->ldv, s->n, k, tcol, s->small, sin, sout, st, second);
-  return launch_cgs_df(s->vw, s->V, s->ldv, s->n, k, tcol, s->small, sin, sout, st, second);
+  switch (vec_mode(s)) {
+    case DMRG_VEC_SPLIT:
+      return launch_cgs_split(s->vw, s->V, s->ldv, s->n, k, tcol, s->small, sin, sout, st, second);
+    case DMRG_VEC_DOUBLE_FLOAT:
+      return launch_cgs_df(s->vw, s->V, s->ldv, s->n, k, tcol, s->small, sin, sout, st, second);
+    default:
+      return launch_cgs(s->vw, s->V, s->ldv, s->n, k, tcol, s->small, sin, sout, st, second);
+  }
+}
+
+dmrg_status fin(dmrg_davidson_state* s, int k, double* tcol, cudaStream_t st) {
+  if (vec_mode(s) == DMRG_VEC_SPLIT)
+    return launch_finish_split(s->vw, s->V, tcol, s->n, k, s->small, st);
+  return launch_finish(tcol, s->n, s->small, st);
 }
 
 dmrg_status project_col(dmrg_davidson_state* s, int col, bool fp64, cudaStream_t st) {
@@ -325,7 +352,7 @@ dmrg_status phase_b(dmrg_davidson_state* s, cudaStream_t st, bool* need_c) {
   DMRG_CUDA_TRY(cudaMemsetAsync(&s->small->flags, 0, sizeof(int32_t), st));
   DMRG_TRY(cgs(s, knew, tcol, 0, 1, 0, st));
   DMRG_TRY(cgs(s, knew, tcol, 1, 2, 1, st));
-  DMRG_TRY(launch_finish(tcol, n, s->small, st));
+  DMRG_TRY(fin(s, knew, tcol, st));
   DMRG_CUDA_TRY(cudaMemcpyAsync(s->hsmall, s->small, sizeof(DevSmall), cudaMemcpyDeviceToHost, st));
   *need_c = true;
   return DMRG_OK;
@@ -346,7 +373,7 @@ dmrg_status phase_c(dmrg_davidson_state* s, cudaStream_t st) {
     DMRG_CUDA_TRY(cudaMemsetAsync(&s->small->flags, 0, sizeof(int32_t), st));
     DMRG_TRY(cgs(s, knew, tcol, 0, 1, 0, st));
     DMRG_TRY(cgs(s, knew, tcol, 1, 2, 1, st));
-    DMRG_TRY(launch_finish(tcol, n, s->small, st));
+    DMRG_TRY(fin(s, knew, tcol, st));
     DMRG_TRY(read_small(s, st));
     if (s->hsmall->flags & 1) {
       set_error("Davidson basis breakdown at iteration %d (||r|| = %g)", s->iters, s->rnorm);

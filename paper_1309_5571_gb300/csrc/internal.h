@@ -165,7 +165,8 @@ struct DevSmall {
   double tnorm2_before;   // ||t||^2 before orthogonalisation
   double tnorm2;          // ||t||^2 after the latest Gram-Schmidt pass
   double nrm2;            // generic norm result
-  int32_t flags;          // bit 0: breakdown, bit 1: non-finite
+  int32_t flags;          // bit 0: breakdown, bit 1: non-finite, bit 2: second
+                          // Gram-Schmidt pass ran
   int32_t jacobi_sweeps;
   double Q[KMAX * KMAX];  // eigenvectors of the last k x k B (row-major, columns)
   double theta[KMAX];     // its eigenvalues
@@ -217,6 +218,19 @@ dmrg_status launch_residual_df(const VecWork& w, const double* V, const double* 
 dmrg_status launch_cgs_df(const VecWork& w, const double* V, int64_t ldv, int64_t n, int k,
                           double* tcol, DevSmall* small, int sin, int sout, cudaStream_t st,
                           int second = 0);
+// vec_split.cu -- mixed modes: column 0 in FP64, low-precision columns in FP32
+dmrg_status launch_overlap_split(const VecWork& w, const double* V, int64_t ldv, int64_t n,
+                                 int k, const double* vec, double* s_out, DevSmall* small,
+                                 int Bcol, cudaStream_t st, const double* w0 = nullptr);
+dmrg_status launch_residual_split(const VecWork& w, const double* V, const double* W,
+                                  const double* D, int64_t ldv, int64_t n, int k, double* tcol,
+                                  DevSmall* small, int mode, cudaStream_t st);
+dmrg_status launch_cgs_split(const VecWork& w, const double* V, int64_t ldv, int64_t n, int k,
+                             double* tcol, DevSmall* small, int sin, int sout, cudaStream_t st,
+                             int second = 0);
+// flags breakdown, else t = (t - s[1][0] v_0) / norm unless the second pass ran (k >= 2)
+dmrg_status launch_finish_split(const VecWork& w, const double* V, double* tcol, int64_t n,
+                                int k, DevSmall* small, cudaStream_t st);
 dmrg_status launch_gemv_trans_public(const double* V, int64_t ldv, int64_t n, int k,
                                      const double* w, double* s, cudaStream_t st);
 

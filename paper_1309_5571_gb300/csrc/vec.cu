@@ -21,77 +21,7 @@
 namespace dmrg {
 namespace {
 
-constexpr int kGridPerSM = 4;
-constexpr int kSlots = KMAX + 4;
-
-struct Ticket {
-  // returns true in every thread of the last block to arrive
-  __device__ static bool last_block(unsigned int* counter) {
-    __shared__ bool is_last;
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      unsigned int t = atomicAdd(counter, 1u);
-      is_last = (t == gridDim.x - 1);
-    }
-    __syncthreads();
-    return is_last;
-  }
-};
-
-// Block-reduce the per-thread values acc[0..NDOT+NEXTRA): the first NDOT are dot
-// products of which only kdots < NDOT are live (slots 0..kdots), the last NEXTRA are
-// always live and go to slots kdots..kdots+NEXTRA.  Every index into acc is a
-// compile-time constant, so acc stays in registers.  Stores this block's partial sums at
-// partials[blockIdx.x * kSlots + slot].
-template <int NDOT, int NEXTRA>
-__device__ void block_partials(double (&acc)[NDOT + NEXTRA], int kdots, double* partials) {
-  __shared__ double red[kVecThreads / 32][kSlots];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-  for (int j = 0; j < NDOT + NEXTRA; ++j) {
-    const bool live = j < NDOT ? (j < kdots) : true;
-    const int slot = j < NDOT ? j : kdots + (j - NDOT);
-    if (live) {
-      double v = acc[j];
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-      if (lane == 0) red[warp][slot] = v;
-    }
-  }
-  __syncthreads();
-  const int nv = kdots + NEXTRA;
-  for (int j = threadIdx.x; j < nv; j += blockDim.x) {
-    double v = 0.0;
-    for (int w = 0; w < kVecThreads / 32; ++w) v += red[w][j];
-    partials[(int64_t)blockIdx.x * kSlots + j] = v;
-  }
-}
-
-// In the last block: total[j] = sum over blocks (fixed order) of partials, j < nv.
-__device__ void final_sums(const double* partials, int nv, double* total) {
-  __shared__ double tmp[kVecThreads];
-  for (int j = 0; j < nv; ++j) {
-    double v = 0.0;
-    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
-      v += __ldcg(&partials[(int64_t)b * kSlots + j]);
-    tmp[threadIdx.x] = v;
-    __syncthreads();
-    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-      if (threadIdx.x < s) tmp[threadIdx.x] += tmp[threadIdx.x + s];
-      __syncthreads();
-    }
-    if (threadIdx.x == 0) total[j] = tmp[0];
-    __syncthreads();
-  }
-}
-
-__device__ __forceinline__ double2 ld2(const double* p) {
-  return __ldg(reinterpret_cast<const double2*>(p));
-}
-__device__ __forceinline__ double2 ld2cg(const double* p) {
-  return __ldcg(reinterpret_cast<const double2*>(p));
-}
+#include "vec_common.cuh"
 
 // ---------------------------------------------------------------- overlap  s = V^T w
 // With w0 != NULL (mixed precision with an FP64 anchor in column 0) the coupling between
@@ -243,6 +173,7 @@ cgs_kernel(const double* __restrict__ V, int64_t ldv, int64_t n2, double* tcol,
            double* __restrict__ partials, unsigned int* counter, DevSmall* small, int sin,
            int sout, int second) {
   if (second && small->tnorm2 >= 0.5 * small->tnorm2_before) return;
+  if (second && blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&small->flags, 4);  // pass 2 ran
   __shared__ double ss[K];
   if (threadIdx.x < K) ss[threadIdx.x] = small->s[sin][threadIdx.x];
   __syncthreads();
@@ -285,7 +216,7 @@ cgs_kernel(const double* __restrict__ V, int64_t ldv, int64_t n2, double* tcol,
     if (threadIdx.x == 0) {
       const double nrm = tot[nv - 1];
       small->tnorm2 = nrm;
-      if (!isfinite(nrm)) small->flags |= 2;
+      if (!isfinite(nrm)) atomicOr(&small->flags, 2);
       *counter = 0u;
     }
   }
@@ -416,7 +347,7 @@ __global__ void set_B00_kernel(DevSmall* small) {
 // k/2 disjoint rotations at once.  A rotation (p, q) uses the symmetric Schur
 // decomposition of the 2 x 2 block: tau = (a_qq - a_pp) / (2 a_pq),
 // t = sign(tau) / (|tau| + sqrt(1 + tau^2)), c = 1 / sqrt(1 + t^2), s = t c, which zeroes
-// a_pq in J^T A J.  A rotation is skipped when |a_pq| <= 1e-15 sqrt(|a_pp a_qq|) (the
+// a_pq in J^T A J.  A rotation is skipped when a_pq^2 <= 1e-30 |a_pp a_qq| (the
 // entry is at the rounding level of the diagonal); the sweeps stop after a sweep
 // without any rotation (at most 40 sweeps).  The angle of each rotation is computed in
 // FP32 and its cosine and sine in FP64 (see below).
@@ -468,17 +399,21 @@ __global__ void __launch_bounds__(128) jacobi_kernel(DevSmall* small, int k) {
         double c = 1.0, s = 0.0;
         if (q < k) {
           const double apq = A[p][q], app = A[p][p], aqq = A[q][q];
-          if (fabs(apq) > 1e-15 * sqrt(fabs(app * aqq)) && apq != 0.0) {
+          // rotate unless a_pq^2 <= 1e-30 |a_pp a_qq| (no square root: FP64 chains are
+          // slow on this part)
+          if (apq != 0.0 && apq * apq > 1e-30 * fabs(app * aqq)) {
             // the angle only needs to be close to the annihilating one (the next sweep
             // removes what is left), so tau and t are formed in FP32; c and s are then
             // derived in FP64 from the same t, so the rotation is orthogonal to FP64
-            // rounding (c^2 + s^2 = 1).  This keeps the sequential FP64 chain short.
+            // rounding (c^2 + s^2 = 1): two Newton steps for 1/sqrt(1 + t^2) from the FP32
+            // estimate (one step leaves ~1e-14, which accumulates over the rotations of
+            // the warm-started decomposition).  This keeps the sequential FP64 chain short.
             const float tau = (float)(aqq - app) / (2.0f * (float)apq);
             const float tf = (tau >= 0.0f ? 1.0f : -1.0f) / (fabsf(tau) + sqrtf(1.0f + tau * tau));
             const double t = (double)tf;
             const double u = fma(t, t, 1.0);
             double cc = (double)rsqrtf((float)u);
-            cc = cc * fma(-0.5 * u, cc * cc, 1.5);   // one Newton step to FP64 accuracy
+            cc = cc * fma(-0.5 * u, cc * cc, 1.5);
             cc = cc * fma(-0.5 * u, cc * cc, 1.5);
             c = cc;
             s = t * cc;

@@ -1,0 +1,108 @@
+// Building blocks shared by the Davidson vector kernels (vec.cu, vec_split.cu): the
+// deterministic one-pass cross-block reduction and 16-byte vector loads.  Included inside
+// an anonymous namespace of each translation unit.
+#pragma once
+
+constexpr int kGridPerSM = 4;
+constexpr int kSlots = KMAX + 4;
+
+struct Ticket {
+  // returns true in every thread of the last block to arrive
+  __device__ static bool last_block(unsigned int* counter) {
+    __shared__ bool is_last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      unsigned int t = atomicAdd(counter, 1u);
+      is_last = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    return is_last;
+  }
+};
+
+// Block-reduce the per-thread values acc[0..NDOT+NEXTRA): the first NDOT are dot
+// products of which only kdots < NDOT are live (slots 0..kdots), the last NEXTRA are
+// always live and go to slots kdots..kdots+NEXTRA.  Every index into acc is a
+// compile-time constant, so acc stays in registers.  Stores this block's partial sums at
+// partials[blockIdx.x * kSlots + slot].
+template <int NDOT, int NEXTRA>
+__device__ void block_partials(double (&acc)[NDOT + NEXTRA], int kdots, double* partials) {
+  __shared__ double red[kVecThreads / 32][kSlots];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int j = 0; j < NDOT + NEXTRA; ++j) {
+    const bool live = j < NDOT ? (j < kdots) : true;
+    const int slot = j < NDOT ? j : kdots + (j - NDOT);
+    if (live) {
+      double v = acc[j];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == 0) red[warp][slot] = v;
+    }
+  }
+  __syncthreads();
+  const int nv = kdots + NEXTRA;
+  for (int j = threadIdx.x; j < nv; j += blockDim.x) {
+    double v = 0.0;
+    for (int w = 0; w < kVecThreads / 32; ++w) v += red[w][j];
+    partials[(int64_t)blockIdx.x * kSlots + j] = v;
+  }
+}
+
+// In the last block: total[j] = sum over blocks (fixed order) of partials, j < nv.
+__device__ void final_sums(const double* partials, int nv, double* total) {
+  __shared__ double tmp[kVecThreads];
+  for (int j = 0; j < nv; ++j) {
+    double v = 0.0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
+      v += __ldcg(&partials[(int64_t)b * kSlots + j]);
+    tmp[threadIdx.x] = v;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+      if (threadIdx.x < s) tmp[threadIdx.x] += tmp[threadIdx.x + s];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) total[j] = tmp[0];
+    __syncthreads();
+  }
+}
+
+__device__ __forceinline__ double2 ld2(const double* p) {
+  return __ldg(reinterpret_cast<const double2*>(p));
+}
+__device__ __forceinline__ double2 ld2cg(const double* p) {
+  return __ldcg(reinterpret_cast<const double2*>(p));
+}
+
+
+// float64 -> float32 with integer operations only (conversions through the FP64 units
+// are slow on this part): the significand is truncated to 24 bits (relative error below
+// 2^-23); magnitudes below 2^-126 become zero, magnitudes of 2^128 and above (and NaN)
+// become an infinity of the same sign.
+__device__ __forceinline__ float f64_to_f32(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned int hi = (unsigned int)(b >> 32), lo = (unsigned int)b;
+  const unsigned int e = (hi >> 20) & 0x7ffu;
+  const unsigned int sign = hi & 0x80000000u;
+  // exponent re-biased in place (1023 -> 127), then the 8-bit exponent and 23
+  // significand bits shifted into position (3 of them from the low word)
+  const unsigned int h = hi - (896u << 20);
+  unsigned int f = sign | (__funnelshift_l(lo, h, 3) & 0x7fffffffu);
+  f = e >= 1151u ? (sign | 0x7f800000u) : f;
+  f = e <= 896u ? 0u : f;
+  return __uint_as_float(f);
+}
+
+// float32 -> float64, exact for normal numbers, integer operations only; zero and
+// subnormals give 0, infinities and NaN keep their class.
+__device__ __forceinline__ double f32_to_f64(float f) {
+  const unsigned int b = __float_as_uint(f);
+  const unsigned int e = (b >> 23) & 0xffu;
+  const unsigned int e64 = e == 255u ? 2047u : e + 896u;
+  unsigned int hi = (b & 0x80000000u) | (e64 << 20) | ((b & 0x7fffffu) >> 3);
+  unsigned int lo = b << 29;
+  hi = e == 0u ? 0u : hi;
+  lo = e == 0u ? 0u : lo;
+  return __hiloint2double((int)hi, (int)lo);
+}

@@ -10,7 +10,7 @@
 // arithmetic keeps the Davidson quantities accurate far below the 1e-10 residual
 // tolerance (2^-48 = 3.6e-15 relative).  Measured on GB300 these passes are issue-bound and
 // not faster than the FP64 ones at the sizes tested, so they are an option
-// (dmrg_options.vector_fp64 = 0), not the default.
+// (dmrg_options.vector_arith = DMRG_VEC_DOUBLE_FLOAT), not the default.
 //
 //   residual:  x = V y, W y, r = W y - lambda x, ||r||^2, t = r / (lambda - D) (the
 //              reciprocal rounded to FP32, the product in double-float), V^T t, ||t||^2

@@ -207,12 +207,13 @@ def test_full_size_solve_heisenberg_m1024_properties(heis_L100_m1024):
     assert np.linalg.norm(Hx - info["energy"] * x) <= 1.5e-10
 
 
-@pytest.mark.parametrize("vector_fp64", [True, False])
-def test_vector_arithmetic_options_match_oracle(vector_fp64):
+@pytest.mark.parametrize("vector_arith", ["fp64", "df", "split"])
+def test_vector_arithmetic_options_match_oracle(vector_arith):
     # Davidson vector passes on the FP64 units or in double-float FP32-pair arithmetic
+    # ("split" is the FP64 path in an FP64 solve)
     sb = problem("hub_quarter_L12_m48")
     x0 = warmup.start_vector(sb.n, seed=2)
-    x, info = Plan(sb, prec="fp64", vector_fp64=vector_fp64).solve(cuda(x0))
+    x, info = Plan(sb, prec="fp64", vector_arith=vector_arith).solve(cuda(x0))
     lam = odav.davidson(lambda v: oproj.project_blocks(sb, v), oproj.diagonal(sb), x0)[0]
     assert abs(info["energy"] - lam) <= E_TOL
     x = x.cpu().numpy()

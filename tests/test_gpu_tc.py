@@ -70,6 +70,23 @@ def test_mixed_davidson_matches_oracle(name, prec):
     assert info["fp64_projections"] >= 1 and info["projections"] >= 1
 
 
+@pytest.mark.parametrize("name", ["heis_L16_m64", "hub_quarter_L12_m48", "ragged"])
+def test_mixed_davidson_vector_arithmetic(name):
+    # split arithmetic (FP64 anchor column, FP32 low-precision columns) reaches the same
+    # FP64 answer as FP64 vector passes, in about the same number of iterations
+    sb = problem(name)
+    x0 = warmup.start_vector(sb.n, seed=0)
+    lam = odav.davidson(lambda v: oproj.project_blocks(sb, v), oproj.diagonal(sb), x0)[0]
+    iters = {}
+    for arith in ("fp64", "split", "df"):
+        x, info = Plan(sb, prec="bf16x3", vector_arith=arith).solve(cuda(x0))
+        assert info["converged"] and abs(info["energy"] - lam) <= E_TOL, (arith, info, lam)
+        x = x.cpu().numpy()
+        assert np.linalg.norm(oproj.project_blocks(sb, x) - info["energy"] * x) <= 1.5e-10
+        iters[arith] = info["iters"]
+    assert iters["split"] <= 1.25 * iters["fp64"] + 3, iters
+
+
 @pytest.fixture(scope="module")
 def hub_L64_m2048():
     return warmup.workload("hub_L64_m2048")
