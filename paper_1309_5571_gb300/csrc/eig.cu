@@ -1,0 +1,317 @@
+// The small projected eigenproblem of Algorithm 3 (line 4): the lowest eigenpair (lambda, y)
+// of the symmetric k x k matrix B = V^T H V, k <= 24, computed by one CTA.
+//
+// This part executes FP64 at about 2 FMA per clock per SM, so a cyclic Jacobi solve in
+// FP64 (~10^4 FP64 operations per sweep at k = 20, several sweeps) costs ~100 us per call,
+// as much as a BF16x3 projection.  The solver therefore splits the work:
+//   1. cyclic Jacobi in FP32 on the FP32 units (round-robin ordering: the k/2 rotations of a
+//      step are disjoint; every 2 x 2 block of J^T A J is updated by one thread), warm-
+//      started from the previous call's eigendecomposition: B_k differs from B_{k-1} by its
+//      last row and column, so in the basis diag(Q_{k-1}, 1) it is diagonal except for that
+//      row and column (an arrowhead), which a few sweeps finish;
+//   2. refinement of the lowest pair in FP64 on B itself, with the FP32 eigenvectors U and
+//      eigenvalues theta as the approximate inverse:
+//          lambda = y^T B y / y^T y,  rho = B y - lambda y,
+//          y <- y - sum_{i != b} u_i (u_i^T rho) / (theta_i - lambda)
+//      (b the lowest index); each step multiplies the error by about the FP32
+//      decomposition error over the eigenvalue gap, until ||rho|| reaches the FP64 level;
+//   3. if ||rho|| does not reach that level (eigenvalues closer than the FP32 resolution),
+//      a cold Jacobi solve with FP64 rotations replaces steps 1-2.
+// Jacobi rotation (p, q): tau = (a_qq - a_pp) / (2 a_pq), t = sign(tau) / (|tau| +
+// sqrt(1 + tau^2)), c = 1 / sqrt(1 + t^2), s = t c zeroes a_pq of J^T A J (the symmetric
+// Schur decomposition of the 2 x 2 block).
+#include <math.h>
+
+#include "internal.h"
+
+namespace dmrg {
+namespace {
+
+constexpr int kEigThreads = 128;
+constexpr double kEps = 1.1102230246251565e-16;  // 2^-53
+
+// player at position j of step `step` of the round-robin tournament over kk (even)
+// players: position 0 stays, the others rotate; pairs are positions (i, kk - 1 - i)
+__device__ __forceinline__ int rr_player(int j, int step, int kk) {
+  return j == 0 ? 0 : 1 + (j - 1 + step) % (kk - 1);
+}
+
+// Rotation parameters of pair (p, q) from the current A.  FP32: the exact annihilating
+// rotation in FP32.  FP64: the angle in FP32 (it only needs to be close to the
+// annihilating one; the next sweep removes what is left), c and s in FP64 from the same
+// t, so c^2 + s^2 = 1 to FP64 rounding (two Newton steps for 1 / sqrt(1 + t^2) from the
+// FP32 estimate).
+__device__ __forceinline__ float absval(float x) { return fabsf(x); }
+__device__ __forceinline__ double absval(double x) { return fabs(x); }
+
+template <typename T>
+__device__ __forceinline__ void rotation(T app, T aqq, T apq, T& c, T& s) {
+  const float tau = (float)(aqq - app) / (2.0f * (float)apq);
+  const float tf = (tau >= 0.0f ? 1.0f : -1.0f) / (fabsf(tau) + sqrtf(1.0f + tau * tau));
+  if constexpr (sizeof(T) == 4) {
+    c = rsqrtf(1.0f + tf * tf);
+    s = tf * c;
+  } else {
+    const double t = (double)tf;
+    const double u = fma(t, t, 1.0);
+    double cc = (double)rsqrtf((float)u);
+    cc = cc * fma(-0.5 * u, cc * cc, 1.5);
+    cc = cc * fma(-0.5 * u, cc * cc, 1.5);
+    c = cc;
+    s = t * cc;
+  }
+}
+
+// Cyclic Jacobi on A (k x k in shared memory, rows and columns k..kk-1 zero), accumulating
+// Q <- Q J.  A rotation is skipped when a_pq^2 <= rel2 |a_pp a_qq| + abs2; sweeps stop
+// after one without rotations.  Returns the number of sweeps.  All threads call it.
+template <typename T>
+__device__ int jacobi_sweeps(T (*A)[KMAX + 1], T (*Q)[KMAX + 1], int k, T rel2, T abs2,
+                             int max_sweeps, T* cs, T* sn, int* pp, int* qq, int* rotated) {
+  const int tid = threadIdx.x;
+  const int kk = (k + 1) & ~1;
+  const int half = kk / 2;
+  int sweep = 0;
+  for (; sweep < max_sweeps && k > 1; ++sweep) {
+    if (tid == 0) *rotated = 0;
+    __syncthreads();
+    for (int step = 0; step < kk - 1; ++step) {
+      if (tid < half) {
+        int p = rr_player(tid, step, kk), q = rr_player(kk - 1 - tid, step, kk);
+        if (p > q) { const int t = p; p = q; q = t; }
+        T c = (T)1, s = (T)0;
+        if (q < k) {
+          const T apq = A[p][q], app = A[p][p], aqq = A[q][q];
+          if (apq != (T)0 && apq * apq > rel2 * absval(app * aqq) + abs2) {
+            rotation<T>(app, aqq, apq, c, s);
+            *rotated = 1;
+          }
+        }
+        pp[tid] = p;
+        qq[tid] = q;
+        cs[tid] = c;
+        sn[tid] = s;
+      }
+      __syncthreads();
+      // A <- J^T A J: the 2 x 2 block (rows of pair I, columns of pair J) depends only on
+      // itself, so each thread updates its blocks in place
+      for (int e = tid; e < half * half; e += blockDim.x) {
+        const int I = e / half, J = e - (e / half) * half;
+        const T sI = sn[I], sJ = sn[J];
+        if (sI == (T)0 && sJ == (T)0) continue;
+        const int a0 = pp[I], a1 = qq[I], b0 = pp[J], b1 = qq[J];
+        const T cI = cs[I], cJ = cs[J];
+        const T x00 = A[a0][b0], x01 = A[a0][b1], x10 = A[a1][b0], x11 = A[a1][b1];
+        const T y00 = cI * x00 - sI * x10, y01 = cI * x01 - sI * x11;
+        const T y10 = sI * x00 + cI * x10, y11 = sI * x01 + cI * x11;
+        T z01 = sJ * y00 + cJ * y01, z10 = cJ * y10 - sJ * y11;
+        if (sizeof(T) == 4 && I == J) z01 = z10 = (T)0;  // the FP32 rotation annihilates a_pq
+        A[a0][b0] = cJ * y00 - sJ * y01;
+        A[a0][b1] = z01;
+        A[a1][b0] = z10;
+        A[a1][b1] = sJ * y10 + cJ * y11;
+      }
+      // Q <- Q J
+      for (int e = tid; e < k * half; e += blockDim.x) {
+        const int r = e / half, J = e - (e / half) * half;
+        const T sJ = sn[J];
+        if (sJ == (T)0) continue;
+        const int b0 = pp[J], b1 = qq[J];
+        const T cJ = cs[J];
+        const T q0 = Q[r][b0], q1 = Q[r][b1];
+        Q[r][b0] = cJ * q0 - sJ * q1;
+        Q[r][b1] = sJ * q0 + cJ * q1;
+      }
+      __syncthreads();
+    }
+    const int any = *rotated;
+    __syncthreads();
+    if (!any) {
+      ++sweep;
+      break;
+    }
+  }
+  return sweep;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__global__ void __launch_bounds__(kEigThreads) small_eig_kernel(DevSmall* small, int k) {
+  __shared__ double Bs[KMAX][KMAX + 1];
+  __shared__ float A32[KMAX][KMAX + 1];
+  __shared__ float Q32[KMAX][KMAX + 1];
+  __shared__ float cs32[KMAX / 2], sn32[KMAX / 2];
+  __shared__ double A64[KMAX][KMAX + 1];
+  __shared__ double Q64[KMAX][KMAX + 1];
+  __shared__ double cs64[KMAX / 2], sn64[KMAX / 2];
+  __shared__ int pp[KMAX / 2], qq[KMAX / 2];
+  __shared__ int rotated, best, refined_ok;
+  __shared__ double yref[KMAX];
+  __shared__ double lam_ref;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const bool warm = k > 1 && small->qk == k - 1;
+
+  // ---- B, and the FP32 start: the arrowhead in the previous eigenbasis, or B itself
+  for (int e = tid; e < KMAX * KMAX; e += blockDim.x) {
+    const int r = e / KMAX, c = e - (e / KMAX) * KMAX;
+    const double b = (r < k && c < k) ? small->B[r * KMAX + c] : 0.0;
+    Bs[r][c] = b;
+    float q = (r == c) ? 1.0f : 0.0f;
+    if (warm && r < k - 1 && c < k - 1) q = (float)small->Q[r * KMAX + c];
+    Q32[r][c] = q;
+  }
+  __syncthreads();
+  for (int e = tid; e < KMAX * KMAX; e += blockDim.x) {
+    const int r = e / KMAX, c = e - (e / KMAX) * KMAX;
+    float a = 0.0f;
+    if (r < k && c < k) {
+      if (!warm) {
+        a = (float)Bs[r][c];
+      } else if (r < k - 1 && c < k - 1) {
+        a = r == c ? (float)small->theta[r] : 0.0f;
+      } else if (r == k - 1 && c == k - 1) {
+        a = (float)Bs[k - 1][k - 1];
+      } else {  // arrow: (Q^T b)_i, b = B(0:k-1, k-1)
+        const int i = r < k - 1 ? r : c;
+        float z = 0.0f;
+        for (int m = 0; m < k - 1; ++m) z = fmaf(Q32[m][i], (float)Bs[m][k - 1], z);
+        a = z;
+      }
+    }
+    A32[r][c] = a;
+  }
+  __syncthreads();
+
+  // ---- 1. FP32 Jacobi; rotations stop at the FP32 resolution of the largest diagonal
+  __shared__ float scale32;
+  if (tid == 0) {
+    float sc = 0.0f;
+    for (int i = 0; i < k; ++i) sc = fmaxf(sc, fabsf(A32[i][i]));
+    for (int i = 0; i < k; ++i)
+      for (int j = 0; j < k; ++j) sc = fmaxf(sc, fabsf(A32[i][j]));
+    scale32 = sc;
+  }
+  __syncthreads();
+  const float tol32 = 2e-7f * scale32;
+  int sweeps = jacobi_sweeps<float>(A32, Q32, k, 0.0f, tol32 * tol32, 30, cs32, sn32, pp, qq, &rotated);
+  if (tid == 0) {
+    int b = 0;
+    for (int i = 1; i < k; ++i)
+      if (A32[i][i] < A32[b][b]) b = i;
+    best = b;
+    refined_ok = 0;
+  }
+  __syncthreads();
+
+  // ---- 2. FP64 refinement of the lowest pair (warp 0, lane i owns row i).  B y, the
+  // Rayleigh quotient and rho are FP64; the correction U D^-1 U^T rho only has to be
+  // accurate relative to the (small) error it removes, so it runs in FP32 (no FP64
+  // conversions or FMAs in its inner loops).  y is normalised once, at the end.
+  if (warp == 0) {
+    const int b = best;
+    const bool act = lane < k;
+    double scale = 0.0;
+    for (int i = 0; i < k; ++i) scale = fmax(scale, fabs((double)A32[i][i]));
+    scale = fmax(scale, 1e-300);
+    const double tol = 8.0 * kEps * scale * sqrt((double)k);
+    const double accept = 64.0 * kEps * scale * sqrt((double)k);
+    const double theta = act ? (double)A32[lane][lane] : 0.0;
+    double y = act ? (double)Q32[lane][b] : 0.0;
+    double lam = 0.0, rel2 = INFINITY, yy = 1.0;
+    for (int it = 0; it < 6; ++it) {
+      double w = 0.0;
+      for (int j = 0; j < k; ++j) {
+        const double yj = __shfl_sync(0xffffffffu, y, j);
+        if (act) w = fma(Bs[lane][j], yj, w);
+      }
+      yy = warp_sum(y * y);
+      lam = warp_sum(y * w) / yy;
+      const double rho = act ? fma(-lam, y, w) : 0.0;
+      rel2 = warp_sum(rho * rho) / yy;  // ||rho||^2 / ||y||^2
+      if (rel2 <= tol * tol || it == 5) break;
+      const float rf = (float)rho;
+      float c = 0.0f;
+      for (int j = 0; j < k; ++j) {
+        const float rj = __shfl_sync(0xffffffffu, rf, j);
+        if (act) c = fmaf(Q32[j][lane], rj, c);
+      }
+      const double d = theta - lam;
+      c = (!act || lane == b || fabs(d) < 1e-6 * scale) ? 0.0f : c / (float)d;
+      float dy = 0.0f;
+      for (int i = 0; i < k; ++i) {
+        const float ci = __shfl_sync(0xffffffffu, c, i);
+        if (act) dy = fmaf(Q32[lane][i], ci, dy);
+      }
+      y -= (double)dy;
+    }
+    if (act) yref[lane] = y / sqrt(yy);
+    if (lane == 0) {
+      lam_ref = lam;
+      refined_ok = (rel2 <= accept * accept) ? 1 : 0;
+    }
+  }
+  __syncthreads();
+
+  if (refined_ok) {
+    if (tid == 0) {
+      small->lambda = lam_ref;
+      small->jacobi_sweeps = sweeps;
+      small->qk = k;
+    }
+    for (int e = tid; e < k * k; e += blockDim.x) {
+      const int r = e / k, c = e - (e / k) * k;
+      small->Q[r * KMAX + c] = (double)Q32[r][c];
+    }
+    if (tid < k) small->theta[tid] = (double)A32[tid][tid];
+    if (tid < KMAX) small->y[tid] = tid < k ? yref[tid] : 0.0;
+    return;
+  }
+
+  // ---- 3. fallback: cold Jacobi with FP64 rotations
+  for (int e = tid; e < KMAX * KMAX; e += blockDim.x) {
+    const int r = e / KMAX, c = e - (e / KMAX) * KMAX;
+    A64[r][c] = Bs[r][c];
+    Q64[r][c] = (r == c) ? 1.0 : 0.0;
+  }
+  __shared__ double scale64;
+  if (tid == 0) {
+    double sc = 0.0;
+    for (int i = 0; i < k; ++i)
+      for (int j = 0; j < k; ++j) sc = fmax(sc, fabs(Bs[i][j]));
+    scale64 = sc;
+  }
+  __syncthreads();
+  const double abs64 = 1e-17 * scale64;
+  sweeps += jacobi_sweeps<double>(A64, Q64, k, 1e-30, abs64 * abs64, 40, cs64, sn64, pp, qq, &rotated);
+  if (tid == 0) {
+    int b = 0;
+    for (int i = 1; i < k; ++i)
+      if (A64[i][i] < A64[b][b]) b = i;
+    best = b;
+    small->eig_fallbacks += 1;
+    small->lambda = A64[b][b];
+    small->jacobi_sweeps = sweeps;
+    small->qk = k;
+  }
+  __syncthreads();
+  for (int e = tid; e < k * k; e += blockDim.x) {
+    const int r = e / k, c = e - (e / k) * k;
+    small->Q[r * KMAX + c] = Q64[r][c];
+  }
+  if (tid < k) small->theta[tid] = A64[tid][tid];
+  if (tid < KMAX) small->y[tid] = tid < k ? Q64[tid][best] : 0.0;
+}
+
+}  // namespace
+
+dmrg_status launch_jacobi(DevSmall* small, int k, cudaStream_t st) {
+  small_eig_kernel<<<1, kEigThreads, 0, st>>>(small, k);
+  DMRG_LAUNCH_CHECK();
+  return DMRG_OK;
+}
+
+}  // namespace dmrg

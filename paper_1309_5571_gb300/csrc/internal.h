@@ -152,7 +152,7 @@ dmrg_status launch_project_oz(dmrg_plan* plan, const double* x, double* y, cudaS
 void destroy_oz(dmrg_plan* plan);
 dmrg_status oz_error_status(dmrg_plan* plan);
 
-// vec.cu -- Davidson vector kernels
+// vec.cu -- Davidson vector kernels (the small eigenproblem: eig.cu)
 constexpr int KMAX = DMRG_MAX_SUBSPACE;
 constexpr int kVecThreads = 256;
 
@@ -171,7 +171,7 @@ struct DevSmall {
   double Q[KMAX * KMAX];  // eigenvectors of the last k x k B (row-major, columns)
   double theta[KMAX];     // its eigenvalues
   int32_t qk;             // order of the stored decomposition (0: none)
-  int32_t pad_;
+  int32_t eig_fallbacks;  // small eigenproblems that needed the FP64 Jacobi fallback
 };
 
 struct VecWork {

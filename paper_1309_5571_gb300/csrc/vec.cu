@@ -341,147 +341,6 @@ __global__ void set_B00_kernel(DevSmall* small) {
   }
 }
 
-// ---------------------------------------------------------------- small eigenproblem
-// Smallest eigenpair of the symmetric k x k matrix B (Algorithm 3 line 4) by the cyclic
-// Jacobi method with the round-robin ordering: each of the k-1 steps of a sweep applies
-// k/2 disjoint rotations at once.  A rotation (p, q) uses the symmetric Schur
-// decomposition of the 2 x 2 block: tau = (a_qq - a_pp) / (2 a_pq),
-// t = sign(tau) / (|tau| + sqrt(1 + tau^2)), c = 1 / sqrt(1 + t^2), s = t c, which zeroes
-// a_pq in J^T A J.  A rotation is skipped when a_pq^2 <= 1e-30 |a_pp a_qq| (the
-// entry is at the rounding level of the diagonal); the sweeps stop after a sweep
-// without any rotation (at most 40 sweeps).  The angle of each rotation is computed in
-// FP32 and its cosine and sine in FP64 (see below).
-// Warm start: B_k differs from B_{k-1} by its last row and column, and the previous call
-// stored the eigendecomposition B_{k-1} = Q diag(theta) Q^T.  With Q~ = diag(Q, 1) the
-// matrix Q~^T B_k Q~ is diagonal except for its last row and column (an arrowhead), so a
-// few sweeps finish it; the eigenvectors are Q~ times the accumulated rotations.
-__global__ void __launch_bounds__(128) jacobi_kernel(DevSmall* small, int k) {
-  __shared__ double A[KMAX][KMAX + 1];
-  __shared__ double Q[KMAX][KMAX + 1];
-  __shared__ double cs[KMAX / 2], sn[KMAX / 2];
-  __shared__ int pp[KMAX / 2], qq[KMAX / 2];
-  __shared__ int perm[KMAX];
-  __shared__ int rotated, best;
-  const int tid = threadIdx.x;
-  const int kk = (k + 1) & ~1;  // even number of players; the extra one is a dummy
-  const bool warm = k > 1 && small->qk == k - 1;
-  for (int e = tid; e < KMAX * KMAX; e += blockDim.x) {
-    const int r = e / KMAX, c = e % KMAX;
-    double a = 0.0, q = (r == c) ? 1.0 : 0.0;
-    if (r < k && c < k) {
-      if (!warm) {
-        a = small->B[r * KMAX + c];
-      } else if (r < k - 1 && c < k - 1) {
-        a = (r == c) ? small->theta[r] : 0.0;
-        q = small->Q[r * KMAX + c];
-      } else if (r == k - 1 && c == k - 1) {
-        a = small->B[(k - 1) * KMAX + (k - 1)];
-      } else {  // arrow entries: (Q^T b)_i with b = B(0:k-1, k-1)
-        const int i = r < k - 1 ? r : c;
-        double z = 0.0;
-        for (int m = 0; m < k - 1; ++m) z = fma(small->Q[m * KMAX + i], small->B[m * KMAX + (k - 1)], z);
-        a = z;
-      }
-    }
-    A[r][c] = a;
-    Q[r][c] = q;
-  }
-  if (tid < kk) perm[tid] = tid;
-  __syncthreads();
-  int sweep = 0;
-  for (; sweep < 40 && k > 1; ++sweep) {
-    if (tid == 0) rotated = 0;
-    __syncthreads();
-    for (int step = 0; step < kk - 1; ++step) {
-      if (tid < kk / 2) {
-        int p = perm[tid], q = perm[kk - 1 - tid];
-        if (p > q) { const int t = p; p = q; q = t; }
-        double c = 1.0, s = 0.0;
-        if (q < k) {
-          const double apq = A[p][q], app = A[p][p], aqq = A[q][q];
-          // rotate unless a_pq^2 <= 1e-30 |a_pp a_qq| (no square root: FP64 chains are
-          // slow on this part)
-          if (apq != 0.0 && apq * apq > 1e-30 * fabs(app * aqq)) {
-            // the angle only needs to be close to the annihilating one (the next sweep
-            // removes what is left), so tau and t are formed in FP32; c and s are then
-            // derived in FP64 from the same t, so the rotation is orthogonal to FP64
-            // rounding (c^2 + s^2 = 1): two Newton steps for 1/sqrt(1 + t^2) from the FP32
-            // estimate (one step leaves ~1e-14, which accumulates over the rotations of
-            // the warm-started decomposition).  This keeps the sequential FP64 chain short.
-            const float tau = (float)(aqq - app) / (2.0f * (float)apq);
-            const float tf = (tau >= 0.0f ? 1.0f : -1.0f) / (fabsf(tau) + sqrtf(1.0f + tau * tau));
-            const double t = (double)tf;
-            const double u = fma(t, t, 1.0);
-            double cc = (double)rsqrtf((float)u);
-            cc = cc * fma(-0.5 * u, cc * cc, 1.5);
-            cc = cc * fma(-0.5 * u, cc * cc, 1.5);
-            c = cc;
-            s = t * cc;
-            rotated = 1;
-          }
-        }
-        pp[tid] = p;
-        qq[tid] = q;
-        cs[tid] = c;
-        sn[tid] = s;
-      }
-      __syncthreads();
-      // rows: A <- J^T A
-      for (int e = tid; e < (kk / 2) * kk; e += blockDim.x) {
-        const int pr = e / kk, col = e % kk;
-        const double s = sn[pr];
-        if (s == 0.0) continue;
-        const int p = pp[pr], q = qq[pr];
-        if (col >= k) continue;
-        const double c = cs[pr];
-        const double ap = A[p][col], aq = A[q][col];
-        A[p][col] = c * ap - s * aq;
-        A[q][col] = s * ap + c * aq;
-      }
-      __syncthreads();
-      // columns: A <- A J, Q <- Q J
-      for (int e = tid; e < (kk / 2) * kk; e += blockDim.x) {
-        const int pr = e / kk, row = e % kk;
-        const double s = sn[pr];
-        if (s == 0.0) continue;
-        const int p = pp[pr], q = qq[pr];
-        if (row >= k) continue;
-        const double c = cs[pr];
-        const double ap = A[row][p], aq = A[row][q];
-        A[row][p] = c * ap - s * aq;
-        A[row][q] = s * ap + c * aq;
-        const double qp = Q[row][p], qv = Q[row][q];
-        Q[row][p] = c * qp - s * qv;
-        Q[row][q] = s * qp + c * qv;
-      }
-      __syncthreads();
-      if (tid == 0) {  // rotate the tournament (player 0 fixed)
-        const int last = perm[kk - 1];
-        for (int i = kk - 1; i > 1; --i) perm[i] = perm[i - 1];
-        perm[1] = last;
-      }
-      __syncthreads();
-    }
-    if (!rotated) break;
-  }
-  if (tid == 0) {
-    int b = 0;
-    for (int i = 1; i < k; ++i)
-      if (A[i][i] < A[b][b]) b = i;
-    best = b;
-    small->lambda = A[b][b];
-    small->jacobi_sweeps = sweep;
-    small->qk = k;
-  }
-  __syncthreads();
-  for (int e = tid; e < k * k; e += blockDim.x) {
-    const int r = e / k, c = e % k;
-    small->Q[r * KMAX + c] = Q[r][c];
-  }
-  if (tid < k) small->theta[tid] = A[tid][tid];
-  if (tid < KMAX) small->y[tid] = tid < k ? Q[tid][best] : 0.0;
-}
-
 }  // namespace
 
 static int vec_grid() {
@@ -515,12 +374,6 @@ dmrg_status launch_overlap(const VecWork& w, const double* V, int64_t ldv, int64
                            cudaStream_t st, const double* w0) {
   KDispatch<OverlapL>::run(k, w.grid, st, V, ldv, (int64_t)((n + 1) / 2), vec, w0, w.partials,
                            w.counter, s_out, small, Bcol);
-  DMRG_LAUNCH_CHECK();
-  return DMRG_OK;
-}
-
-dmrg_status launch_jacobi(DevSmall* small, int k, cudaStream_t st) {
-  jacobi_kernel<<<1, 128, 0, st>>>(small, k);
   DMRG_LAUNCH_CHECK();
   return DMRG_OK;
 }

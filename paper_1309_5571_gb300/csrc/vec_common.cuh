@@ -50,22 +50,20 @@ __device__ void block_partials(double (&acc)[NDOT + NEXTRA], int kdots, double* 
   }
 }
 
-// In the last block: total[j] = sum over blocks (fixed order) of partials, j < nv.
+// In the last block: total[j] = sum over blocks of partials, j < nv.  One warp per slot:
+// the lanes add block-strided partials (independent loads, one round trip), then a
+// shuffle tree; the order is fixed, so the result is deterministic.
 __device__ void final_sums(const double* partials, int nv, double* total) {
-  __shared__ double tmp[kVecThreads];
-  for (int j = 0; j < nv; ++j) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int j = warp; j < nv; j += nw) {
     double v = 0.0;
-    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
-      v += __ldcg(&partials[(int64_t)b * kSlots + j]);
-    tmp[threadIdx.x] = v;
-    __syncthreads();
-    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-      if (threadIdx.x < s) tmp[threadIdx.x] += tmp[threadIdx.x + s];
-      __syncthreads();
-    }
-    if (threadIdx.x == 0) total[j] = tmp[0];
-    __syncthreads();
+#pragma unroll 4
+    for (int b = lane; b < (int)gridDim.x; b += 32) v += __ldcg(&partials[(int64_t)b * kSlots + j]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) total[j] = v;
   }
+  __syncthreads();
 }
 
 __device__ __forceinline__ double2 ld2(const double* p) {
@@ -75,6 +73,34 @@ __device__ __forceinline__ double2 ld2cg(const double* p) {
   return __ldcg(reinterpret_cast<const double2*>(p));
 }
 
+
+// Split-precision block reduction: each warp reduces its FP32 values with FP32 shuffles
+// and its FP64 values with FP64 shuffles (FP64 adds run at about 1/64 of the FP32 rate on
+// this part, so a full FP64 warp reduction of ~20 values per thread would cost more than
+// the streaming pass itself); the per-warp results are combined in FP64 and stored as
+// this block's partial sums, in the slot layout of block_partials.
+struct SplitReduce {
+  double (*red)[kSlots];
+  int lane, warp;
+  __device__ void f32(float v, int slot) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) red[warp][slot] = (double)v;
+  }
+  __device__ void f64(double v, int slot) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) red[warp][slot] = v;
+  }
+  __device__ void store(int nv, double* partials) {
+    __syncthreads();
+    for (int j = threadIdx.x; j < nv; j += blockDim.x) {
+      double v = 0.0;
+      for (int w = 0; w < kVecThreads / 32; ++w) v += red[w][j];
+      partials[(int64_t)blockIdx.x * kSlots + j] = v;
+    }
+  }
+};
 
 // float64 -> float32 with integer operations only (conversions through the FP64 units
 // are slow on this part): the significand is truncated to 24 bits (relative error below

@@ -14,8 +14,9 @@
 // low-precision projection itself leaves in that column.  The column-0 terms therefore
 // run on the FP64 units (a few operations per element), the columns j >= 1 on the FP32
 // units (loaded as float64, converted with integer operations, accumulated in FP32 per
-// thread and in FP64 across threads).  The passes are then bound by HBM rather than by
-// the FP64 units (about 0.55 T FMA/s on this part).  The anchor iteration itself (k = 1)
+// thread and warp, in FP64 across warps and blocks).  The passes are then bound by HBM
+// rather than by the FP64 units (about 0.55 T FMA/s on this part); hardware FP64<->FP32
+// conversions would run on the FP64 units too.  The anchor iteration itself (k = 1)
 // and the final convergence test are entirely float64: with one column (k = 1) the FP64
 // kernels of vec.cu run.
 //
@@ -41,7 +42,7 @@ __device__ __forceinline__ float2 cvt2(double2 v) {
 
 // ---------------------------------------------------------------- overlap
 template <int K>
-__global__ void __launch_bounds__(kVecThreads)
+__global__ void __launch_bounds__(kVecThreads, 2)
 overlap_split_kernel(const double* __restrict__ V, int64_t ldv, int64_t n2,
                      const double* __restrict__ w, const double* __restrict__ w0,
                      double* __restrict__ partials, unsigned int* counter, double* s_out,
@@ -74,12 +75,13 @@ overlap_split_kernel(const double* __restrict__ V, int64_t ldv, int64_t n2,
       ac = fma(vl.x, a.x, fma(vl.y, a.y, ac));
     }
   }
-  double acc[K + 1];
-  acc[0] = a0;
+  __shared__ double red[kVecThreads / 32][kSlots];
+  SplitReduce sr{red, (int)(threadIdx.x & 31), (int)(threadIdx.x >> 5)};
+  sr.f64(a0, 0);
 #pragma unroll
-  for (int j = 1; j < K; ++j) acc[j] = (double)acc32[j - 1];
-  acc[K] = ac;
-  block_partials<K, 1>(acc, K, partials);
+  for (int j = 1; j < K; ++j) sr.f32(acc32[j - 1], j);
+  sr.f64(ac, K);
+  sr.store(K + 1, partials);
   if (Ticket::last_block(counter)) {
     __shared__ double tot[K + 1];
     final_sums(partials, K + 1, tot);
@@ -98,7 +100,7 @@ overlap_split_kernel(const double* __restrict__ V, int64_t ldv, int64_t n2,
 
 // ---------------------------------------------------------------- residual + correction
 template <int K>
-__global__ void __launch_bounds__(kVecThreads)
+__global__ void __launch_bounds__(kVecThreads, 2)
 residual_split_kernel(const double* __restrict__ V, const double* __restrict__ W,
                       const double* __restrict__ D, int64_t ldv, int64_t n2,
                       double* __restrict__ tcol, double* __restrict__ partials,
@@ -158,13 +160,15 @@ residual_split_kernel(const double* __restrict__ V, const double* __restrict__ W
 #pragma unroll
     for (int j = 0; j < K - 1; ++j) acc32[j] = fmaf(vf[j].x, tf0, fmaf(vf[j].y, tf1, acc32[j]));
   }
-  double acc[K + 2];  // [0..K): V^T t, [K]: ||r||^2, [K+1]: ||t||^2
-  acc[0] = d0;
+  // slots [0..K): V^T t, [K]: ||r||^2, [K+1]: ||t||^2
+  __shared__ double red[kVecThreads / 32][kSlots];
+  SplitReduce sr{red, (int)(threadIdx.x & 31), (int)(threadIdx.x >> 5)};
+  sr.f64(d0, 0);
 #pragma unroll
-  for (int j = 1; j < K; ++j) acc[j] = (double)acc32[j - 1];
-  acc[K] = (double)rr;
-  acc[K + 1] = (double)tt;
-  block_partials<K, 2>(acc, K, partials);
+  for (int j = 1; j < K; ++j) sr.f32(acc32[j - 1], j);
+  sr.f32(rr, K);
+  sr.f32(tt, K + 1);
+  sr.store(K + 2, partials);
   if (Ticket::last_block(counter)) {
     __shared__ double tot[K + 2];
     final_sums(partials, K + 2, tot);
@@ -183,7 +187,7 @@ residual_split_kernel(const double* __restrict__ V, const double* __restrict__ W
 // Same protocol as the FP64 pass: the second pass (second = 1) runs only when the first
 // removed more than half of ||t||^2.
 template <int K, bool DOT>
-__global__ void __launch_bounds__(kVecThreads)
+__global__ void __launch_bounds__(kVecThreads, 2)
 cgs_split_kernel(const double* __restrict__ V, int64_t ldv, int64_t n2, double* tcol,
                  double* __restrict__ partials, unsigned int* counter, DevSmall* small,
                  int sin, int sout, int second) {
@@ -229,16 +233,17 @@ cgs_split_kernel(const double* __restrict__ V, int64_t ldv, int64_t n2, double* 
       for (int j = 0; j < K - 1; ++j) acc32[j] = fmaf(vf[j].x, tf0, fmaf(vf[j].y, tf1, acc32[j]));
     }
   }
+  __shared__ double red[kVecThreads / 32][kSlots];
+  SplitReduce sr{red, (int)(threadIdx.x & 31), (int)(threadIdx.x >> 5)};
   if (DOT) {
-    double acc[K + 1];
-    acc[0] = d0;
+    sr.f64(d0, 0);
 #pragma unroll
-    for (int j = 1; j < K; ++j) acc[j] = (double)acc32[j - 1];
-    acc[K] = (double)tt;
-    block_partials<K, 1>(acc, K, partials);
+    for (int j = 1; j < K; ++j) sr.f32(acc32[j - 1], j);
+    sr.f32(tt, K);
+    sr.store(K + 1, partials);
   } else {
-    double a1[1] = {(double)tt};
-    block_partials<0, 1>(a1, 0, partials);
+    sr.f32(tt, 0);
+    sr.store(1, partials);
   }
   if (Ticket::last_block(counter)) {
     __shared__ double tot[K + 1];
@@ -297,6 +302,9 @@ struct Dispatch<KMAX + 1> {
   static void run(int, F&&) {}
 };
 
+// one wave: two resident blocks per SM (the kernels are limited to 128 registers)
+int split_grid(const VecWork& w) { return w.grid / kGridPerSM * 2; }
+
 }  // namespace
 
 dmrg_status launch_overlap_split(const VecWork& w, const double* V, int64_t ldv, int64_t n,
@@ -306,7 +314,7 @@ dmrg_status launch_overlap_split(const VecWork& w, const double* V, int64_t ldv,
   const int64_t n2 = (n + 1) / 2;
   Dispatch<2>::run(k, [&](auto kc) {
     constexpr int K = decltype(kc)::value;
-    overlap_split_kernel<K><<<w.grid, kVecThreads, 0, st>>>(V, ldv, n2, vec, w0, w.partials,
+    overlap_split_kernel<K><<<split_grid(w), kVecThreads, 0, st>>>(V, ldv, n2, vec, w0, w.partials,
                                                             w.counter, s_out, small, Bcol);
   });
   DMRG_LAUNCH_CHECK();
@@ -320,7 +328,7 @@ dmrg_status launch_residual_split(const VecWork& w, const double* V, const doubl
   const int64_t n2 = (n + 1) / 2;
   Dispatch<2>::run(k, [&](auto kc) {
     constexpr int K = decltype(kc)::value;
-    residual_split_kernel<K><<<w.grid, kVecThreads, 0, st>>>(V, W, D, ldv, n2, tcol, w.partials,
+    residual_split_kernel<K><<<split_grid(w), kVecThreads, 0, st>>>(V, W, D, ldv, n2, tcol, w.partials,
                                                              w.counter, small, mode);
   });
   DMRG_LAUNCH_CHECK();
@@ -335,10 +343,10 @@ dmrg_status launch_cgs_split(const VecWork& w, const double* V, int64_t ldv, int
   Dispatch<2>::run(k, [&](auto kc) {
     constexpr int K = decltype(kc)::value;
     if (second)
-      cgs_split_kernel<K, false><<<w.grid, kVecThreads, 0, st>>>(V, ldv, n2, tcol, w.partials,
+      cgs_split_kernel<K, false><<<split_grid(w), kVecThreads, 0, st>>>(V, ldv, n2, tcol, w.partials,
                                                                  w.counter, small, sin, sout, 1);
     else
-      cgs_split_kernel<K, true><<<w.grid, kVecThreads, 0, st>>>(V, ldv, n2, tcol, w.partials,
+      cgs_split_kernel<K, true><<<split_grid(w), kVecThreads, 0, st>>>(V, ldv, n2, tcol, w.partials,
                                                                 w.counter, small, sin, sout, 0);
   });
   DMRG_LAUNCH_CHECK();
@@ -348,7 +356,7 @@ dmrg_status launch_cgs_split(const VecWork& w, const double* V, int64_t ldv, int
 dmrg_status launch_finish_split(const VecWork& w, const double* V, double* tcol, int64_t n,
                                 int k, DevSmall* small, cudaStream_t st) {
   if (k == 1) return launch_finish(tcol, n, small, st);
-  finish_split_kernel<<<w.grid, kVecThreads, 0, st>>>(V, tcol, (n + 1) / 2, small);
+  finish_split_kernel<<<split_grid(w), kVecThreads, 0, st>>>(V, tcol, (n + 1) / 2, small);
   DMRG_LAUNCH_CHECK();
   return DMRG_OK;
 }
