@@ -147,6 +147,11 @@ typedef struct {
   int32_t vector_arith;  /* arithmetic of the Davidson vector passes (dmrg_vector_arith);
                             vectors are float64 in memory in every mode (default
                             DMRG_VEC_SPLIT)                                              */
+  int32_t autotune;      /* 1 (default): the first TF32/BF16X3 projection of a plan times
+                            the candidate tile schedules of both tensor-core GEMM stages
+                            and keeps the fastest (that call synchronizes its stream and
+                            must not be captured in a CUDA graph; dmrg_plan_autotune does
+                            it ahead of time); 0: descending-cost schedule              */
 } dmrg_options;
 
 typedef struct {
@@ -167,6 +172,12 @@ typedef struct {
                                identity factors only)                                      */
   int64_t tiles_stage1, tiles_stage2;
   int64_t device_bytes;     /* device memory owned by the plan                            */
+  int32_t tc_schedule[2];   /* tile schedule of tensor-core GEMM stages 1 and 2 (0: jobs in
+                               descending cost; 1: stage 1 grouped by vector segment, stage
+                               2 by right sector; 2: stage 1 grouped by operator block,
+                               stage 2 by left sector); -1 before a TF32/BF16X3 plan exists */
+  float tc_tune_us[2][3];   /* autotuner: median time of each schedule per stage (us), 0 if
+                               not tuned                                                   */
 } dmrg_plan_stats;
 
 typedef struct dmrg_plan dmrg_plan;
@@ -184,6 +195,14 @@ dmrg_status dmrg_plan_create(const dmrg_superblock_desc* desc, const dmrg_option
                              void* stream, dmrg_plan** out);
 void dmrg_plan_destroy(dmrg_plan* plan);
 dmrg_status dmrg_plan_get_stats(const dmrg_plan* plan, dmrg_plan_stats* stats);
+
+/* Tile-schedule autotuner of the tensor-core projection (prec DMRG_PREC_TF32 or
+ * DMRG_PREC_BF16X3): builds the operand images if needed, times every candidate schedule
+ * of each GEMM stage on this GPU (L2 flushed before each timing) and keeps the fastest;
+ * the results appear in dmrg_plan_stats.  The paper has no counterpart (its records are
+ * dispatched to streams by Algorithms 6-7).  Synchronizes the stream; allocates and frees
+ * 256 MB of scratch. */
+dmrg_status dmrg_plan_autotune(dmrg_plan* plan, dmrg_precision prec, void* stream);
 
 /* y = H_SB x (Eq. 11 summed over all records), in the given precision.  x and y are
  * device arrays of n float64 and must not overlap.  Enqueued on stream. */

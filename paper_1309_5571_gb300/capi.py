@@ -65,7 +65,7 @@ class Options(C.Structure):
     _fields_ = [("prec", C.c_int32), ("tol", C.c_double), ("max_iter", C.c_int32),
                 ("max_subspace", C.c_int32), ("fp64_refine", C.c_int32),
                 ("refine_ratio", C.c_double), ("anchor_prec", C.c_int32),
-                ("vector_arith", C.c_int32)]
+                ("vector_arith", C.c_int32), ("autotune", C.c_int32)]
 
 
 class SolveInfo(C.Structure):
@@ -81,10 +81,14 @@ class SolveInfo(C.Structure):
 class PlanStats(C.Structure):
     _fields_ = [("n", C.c_int64), ("records", C.c_int64), ("flops", C.c_int64),
                 ("tiles_stage1", C.c_int64), ("tiles_stage2", C.c_int64),
-                ("device_bytes", C.c_int64)]
+                ("device_bytes", C.c_int64), ("tc_schedule", C.c_int32 * 2),
+                ("tc_tune_us", (C.c_float * 3) * 2)]
 
     def as_dict(self):
-        return {f: getattr(self, f) for f, _ in self._fields_}
+        d = {f: getattr(self, f) for f, _ in self._fields_[:6]}
+        d["tc_schedule"] = list(self.tc_schedule)
+        d["tc_tune_us"] = [list(r) for r in self.tc_tune_us]
+        return d
 
 
 # every exported symbol and its signature (checked by the CPU test suite)
@@ -94,6 +98,7 @@ SIGNATURES = {
                                    C.POINTER(C.c_void_p)]),
     "dmrg_plan_destroy": (None, [C.c_void_p]),
     "dmrg_plan_get_stats": (C.c_int, [C.c_void_p, C.POINTER(PlanStats)]),
+    "dmrg_plan_autotune": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
     "dmrg_project": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "dmrg_project_prec": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
     "dmrg_diagonal": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
@@ -213,7 +218,7 @@ def marshal(sb) -> _Marshalled:
 
 
 def options(prec="fp64", tol=1e-10, max_iter=1000, max_subspace=20, fp64_refine=True,
-            refine_ratio=0.0, anchor_prec="fp64", vector_arith="split") -> Options:
+            refine_ratio=0.0, anchor_prec="fp64", vector_arith="split", autotune=True) -> Options:
     o = Options()
     load().dmrg_options_default(C.byref(o))
     o.prec = PREC[prec] if isinstance(prec, str) else int(prec)
@@ -224,6 +229,7 @@ def options(prec="fp64", tol=1e-10, max_iter=1000, max_subspace=20, fp64_refine=
     o.refine_ratio = refine_ratio
     o.anchor_prec = PREC[anchor_prec] if isinstance(anchor_prec, str) else int(anchor_prec)
     o.vector_arith = VEC[vector_arith] if isinstance(vector_arith, str) else int(vector_arith)
+    o.autotune = int(bool(autotune))
     return o
 
 
@@ -255,6 +261,18 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+    def get_stats(self):
+        st = PlanStats()
+        _check(self.lib.dmrg_plan_get_stats(self.handle, C.byref(st)))
+        self.stats = st.as_dict()
+        return self.stats
+
+    def autotune(self, prec="bf16x3", stream=None):
+        """dmrg_plan_autotune: time the tile schedules of the tensor-core GEMM stages."""
+        _check(self.lib.dmrg_plan_autotune(self.handle, PREC[prec] if isinstance(prec, str) else int(prec),
+                                           _stream_ptr(stream)))
+        return self.get_stats()
 
     def project(self, x, y=None, prec=None, stream=None):
         torch = _torch()

@@ -34,6 +34,7 @@ void dmrg_options_default(dmrg_options* opt) {
   opt->refine_ratio = 0.0;
   opt->anchor_prec = DMRG_PREC_FP64;
   opt->vector_arith = DMRG_VEC_SPLIT;
+  opt->autotune = 1;
 }
 
 const char* dmrg_status_string(dmrg_status s) {

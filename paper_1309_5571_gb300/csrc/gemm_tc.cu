@@ -33,6 +33,7 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <functional>
 #include <map>
 #include <tuple>
 
@@ -78,6 +79,18 @@ struct PackChunk {
 
 enum TcBuf { TB_OPS = 0, TB_XA = 1, TB_XB = 2, TB_INTER = 3 };
 
+// Tile schedules (the order in which the persistent CTAs take the output tiles; CTA b takes
+// tiles b, b + grid, ...).  Every schedule covers the same tiles, so the results are
+// identical; only the operand reuse in L2 and the load balance differ.
+//   0  jobs in descending cost (longest first), tiles row-major within a job
+//   1  stage 1: jobs grouped by the vector image they read (all records of one (i, k)
+//      segment and form together), tiles column-major; stage 2: output segments grouped
+//      by their right sector l
+//   2  stage 1: jobs grouped by the operator block image they read, tiles row-major;
+//      stage 2: output segments grouped by their left sector j
+// Groups are taken in descending total cost, jobs within a group in descending cost.
+constexpr int kSchedules = 3;
+
 struct TcPlan {
   dmrg_precision prec = DMRG_PREC_BF16X3;
   int planes = 3, kt_elems = 64;
@@ -88,9 +101,13 @@ struct TcPlan {
   int64_t n_xpack_chunks = 0;
   TcJob* d_jobs = nullptr;
   TcSeg* d_segs = nullptr;
-  TcTile* d_tiles1 = nullptr;
-  TcTile* d_tiles2 = nullptr;
+  // candidate tile schedules of each stage (kSchedules, see build_tc); the kernels run
+  // schedule sched[stage]
+  TcTile* d_tiles[2][kSchedules] = {};
   int64_t ntiles1 = 0, ntiles2 = 0;
+  int sched[2] = {0, 0};
+  bool tuned = false;
+  float tune_us[2][kSchedules] = {};
   int* d_err = nullptr;   // device view of a mapped host word: kernel error codes
   int* h_err = nullptr;
   int sms = 0;
@@ -450,8 +467,8 @@ void free_tc(TcPlan* t) {
   cudaFree(t->d_xpack_chunks);
   cudaFree(t->d_jobs);
   cudaFree(t->d_segs);
-  cudaFree(t->d_tiles1);
-  cudaFree(t->d_tiles2);
+  for (auto& st : t->d_tiles)
+    for (TcTile* d : st) cudaFree(d);
   delete t;
 }
 
@@ -582,8 +599,10 @@ dmrg_status build_tc(dmrg_plan* p, dmrg_precision prec, cudaStream_t st, TcPlan*
   }
   std::vector<std::vector<int>> by_out(npairs);
   for (size_t ri = 0; ri < p->records.size(); ++ri) by_out[p->records[ri].pout].push_back((int)ri);
+  std::vector<int> stage2_job(npairs, -1);
   for (int q = 0; q < npairs; ++q) {
     const int i = p->pair_i[q], k = p->pair_k[q];
+    stage2_job[q] = (int)jobs.size();
     TcJob job{};
     job.M = (int32_t)p->dimL[i];
     job.N = (int32_t)p->dimR[k];
@@ -626,16 +645,56 @@ dmrg_status build_tc(dmrg_plan* p, dmrg_precision prec, cudaStream_t st, TcPlan*
   };
   std::stable_sort(order1.begin(), order1.end(), by_cost);
   std::stable_sort(order2.begin(), order2.end(), by_cost);
-  for (auto& pr : order1) {
-    const TcJob& j = jobs[pr.second];
-    for (int mt = 0; mt < ceil_div(j.M, kRows); ++mt)
-      for (int nt = 0; nt < ceil_div(j.N, kRows); ++nt) tiles1.push_back(TcTile{pr.second, mt, nt, 0});
-  }
-  for (auto& pr : order2) {
-    const TcJob& j = jobs[pr.second];
-    for (int mt = 0; mt < ceil_div(j.M, kRows); ++mt)
-      for (int nt = 0; nt < ceil_div(j.N, kRows); ++nt) tiles2.push_back(TcTile{pr.second, mt, nt, 0});
-  }
+  auto add_tiles = [&](std::vector<TcTile>& out, int jb, bool col_major) {
+    const TcJob& j = jobs[jb];
+    const int nm = ceil_div(j.M, kRows), nn = ceil_div(j.N, kRows);
+    if (col_major) {
+      for (int nt = 0; nt < nn; ++nt)
+        for (int mt = 0; mt < nm; ++mt) out.push_back(TcTile{jb, mt, nt, 0});
+    } else {
+      for (int mt = 0; mt < nm; ++mt)
+        for (int nt = 0; nt < nn; ++nt) out.push_back(TcTile{jb, mt, nt, 0});
+    }
+  };
+  // jobs (already in descending cost) grouped by key; groups in descending total cost
+  auto grouped = [&](const std::vector<std::pair<int64_t, int>>& order,
+                     const std::function<int64_t(int)>& key, bool col_major) {
+    std::map<int64_t, std::pair<int64_t, std::vector<int>>> groups;
+    for (const auto& pr : order) {
+      auto& g = groups[key(pr.second)];
+      g.first += pr.first;
+      g.second.push_back(pr.second);
+    }
+    std::vector<std::pair<int64_t, int64_t>> gorder;
+    for (const auto& g : groups) gorder.push_back({g.second.first, g.first});
+    std::stable_sort(gorder.begin(), gorder.end(), [](const auto& a, const auto& b) {
+      return a.first != b.first ? a.first > b.first : a.second < b.second;
+    });
+    std::vector<TcTile> out;
+    for (const auto& g : gorder)
+      for (int jb : groups[g.second].second) add_tiles(out, jb, col_major);
+    return out;
+  };
+  std::vector<TcTile> sched1[kSchedules], sched2[kSchedules];
+  for (const auto& pr : order1) add_tiles(sched1[0], pr.second, false);
+  for (const auto& pr : order2) add_tiles(sched2[0], pr.second, false);
+  // a stage-1 job has one segment (its record), or none when its K dimension is empty
+  auto x_key = [&](int jb) -> int64_t {
+    const TcJob& j = jobs[jb];
+    return j.seg_begin == j.seg_end ? -1 : segs[j.seg_begin].q_off * 4 + segs[j.seg_begin].q_buf;
+  };
+  auto op_key = [&](int jb) -> int64_t {
+    const TcJob& j = jobs[jb];
+    return j.seg_begin == j.seg_end ? -1 : segs[j.seg_begin].p_off;
+  };
+  sched1[1] = grouped(order1, x_key, true);
+  sched1[2] = grouped(order1, op_key, false);
+  std::vector<int> job_pair(jobs.size(), -1);
+  for (int q = 0; q < npairs; ++q) job_pair[stage2_job[q]] = q;
+  sched2[1] = grouped(order2, [&](int jb) { return (int64_t)p->pair_k[job_pair[jb]]; }, false);
+  sched2[2] = grouped(order2, [&](int jb) { return (int64_t)p->pair_i[job_pair[jb]]; }, false);
+  tiles1 = sched1[0];
+  tiles2 = sched2[0];
   // stage-1 N tiles read Q image row tiles; stage-2 image K tiles must cover the segment
   // (image row tiles = ceil(rows / 128) >= tiles; image K tiles = nkt): checked here
   for (const TcSeg& s : segs) {
@@ -686,8 +745,14 @@ dmrg_status build_tc(dmrg_plan* p, dmrg_precision prec, cudaStream_t st, TcPlan*
   t->n_xpack_chunks = (int64_t)x_chunks.size();
   if ((s = upload_vec(&t->d_jobs, jobs, st)) != DMRG_OK) return fail(s);
   if ((s = upload_vec(&t->d_segs, segs, st)) != DMRG_OK) return fail(s);
-  if ((s = upload_vec(&t->d_tiles1, tiles1, st)) != DMRG_OK) return fail(s);
-  if ((s = upload_vec(&t->d_tiles2, tiles2, st)) != DMRG_OK) return fail(s);
+  for (int c = 0; c < kSchedules; ++c) {
+    if (sched1[c].size() != tiles1.size() || sched2[c].size() != tiles2.size()) {
+      set_error("internal: tile schedules of different sizes");
+      return fail(DMRG_ERR_SHAPE);
+    }
+    if ((s = upload_vec(&t->d_tiles[0][c], sched1[c], st)) != DMRG_OK) return fail(s);
+    if ((s = upload_vec(&t->d_tiles[1][c], sched2[c], st)) != DMRG_OK) return fail(s);
+  }
   t->ntiles1 = (int64_t)tiles1.size();
   t->ntiles2 = (int64_t)tiles2.size();
   if (cudaHostAlloc((void**)&t->h_err, sizeof(int), cudaHostAllocMapped) != cudaSuccess ||
@@ -703,7 +768,7 @@ dmrg_status build_tc(dmrg_plan* p, dmrg_precision prec, cudaStream_t st, TcPlan*
 }
 
 template <int PLANES, int STAGES, bool TF32>
-dmrg_status run_tc(dmrg_plan* p, TcPlan* t, const double* x, double* y, cudaStream_t st) {
+dmrg_status configure_tc() {
   constexpr size_t smem = tc::smem_bytes<PLANES, STAGES, TF32>();
   static bool configured[64] = {false};
   int dev = 0;
@@ -713,31 +778,109 @@ dmrg_status run_tc(dmrg_plan* p, TcPlan* t, const double* x, double* y, cudaStre
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     configured[dev] = true;
   }
+  return DMRG_OK;
+}
+
+// part 0: pack X into its operand images; part 1, 2: the GEMM stages with schedule c
+template <int PLANES, int STAGES, bool TF32>
+dmrg_status run_tc_part(dmrg_plan* p, TcPlan* t, const double* x, double* y, int part, int c,
+                        cudaStream_t st) {
+  constexpr size_t smem = tc::smem_bytes<PLANES, STAGES, TF32>();
+  if (part == 0) {
+    if (t->n_xpack_chunks > 0) {  // X -> A-form and B-form images
+      tc::pack_kernel<PLANES, TF32><<<(unsigned)t->n_xpack_chunks, 256, 0, st>>>(
+          t->d_xpack_chunks, t->d_xpack_jobs, p->arena, x, t->buf[TB_XA]);
+      DMRG_LAUNCH_CHECK();
+    }
+    return DMRG_OK;
+  }
+  const int64_t nt = part == 1 ? t->ntiles1 : t->ntiles2;
+  if (nt == 0) return DMRG_OK;
+  const int grid = (int)std::min<int64_t>(nt, t->sms);
+  tc::tc_gemm_kernel<PLANES, STAGES, TF32><<<grid, tc::kThreads, smem, st>>>(
+      t->d_tiles[part - 1][c], (int)nt, t->d_jobs, t->d_segs, t->buf[TB_OPS], t->buf[TB_XA],
+      t->buf[TB_XB], part == 1 ? nullptr : t->buf[TB_INTER], part == 1 ? t->buf[TB_INTER] : nullptr,
+      y, x, t->d_err);
+  DMRG_LAUNCH_CHECK();
+  return DMRG_OK;
+}
+
+template <int PLANES, int STAGES, bool TF32>
+dmrg_status run_tc(dmrg_plan* p, TcPlan* t, const double* x, double* y, cudaStream_t st) {
+  DMRG_TRY((configure_tc<PLANES, STAGES, TF32>()));
   if (*t->h_err != 0) {
     set_error("tensor-core projection kernel reported error %d (a bounded wait timed out)",
               *t->h_err);
     return DMRG_ERR_CUDA;
   }
-  if (t->n_xpack_chunks > 0) {  // X -> A-form and B-form images
-    tc::pack_kernel<PLANES, TF32><<<(unsigned)t->n_xpack_chunks, 256, 0, st>>>(
-        t->d_xpack_chunks, t->d_xpack_jobs, p->arena, x, t->buf[TB_XA]);
-    DMRG_LAUNCH_CHECK();
-  }
-  if (t->ntiles1 > 0) {
-    const int grid = (int)std::min<int64_t>(t->ntiles1, t->sms);
-    tc::tc_gemm_kernel<PLANES, STAGES, TF32><<<grid, tc::kThreads, smem, st>>>(
-        t->d_tiles1, (int)t->ntiles1, t->d_jobs, t->d_segs, t->buf[TB_OPS], t->buf[TB_XA],
-        t->buf[TB_XB], nullptr, t->buf[TB_INTER], y, x, t->d_err);
-    DMRG_LAUNCH_CHECK();
-  }
-  if (t->ntiles2 > 0) {
-    const int grid = (int)std::min<int64_t>(t->ntiles2, t->sms);
-    tc::tc_gemm_kernel<PLANES, STAGES, TF32><<<grid, tc::kThreads, smem, st>>>(
-        t->d_tiles2, (int)t->ntiles2, t->d_jobs, t->d_segs, t->buf[TB_OPS], t->buf[TB_XA],
-        t->buf[TB_XB], t->buf[TB_INTER], nullptr, y, x, t->d_err);
-    DMRG_LAUNCH_CHECK();
-  }
+  DMRG_TRY((run_tc_part<PLANES, STAGES, TF32>(p, t, x, y, 0, 0, st)));
+  DMRG_TRY((run_tc_part<PLANES, STAGES, TF32>(p, t, x, y, 1, t->sched[0], st)));
+  DMRG_TRY((run_tc_part<PLANES, STAGES, TF32>(p, t, x, y, 2, t->sched[1], st)));
   return DMRG_OK;
+}
+
+// The autotuner: times every schedule of each stage (median of 3 after one untimed run,
+// with L2 flushed by a 256 MB write before each timed run, as inside a Davidson
+// iteration whose vector passes stream far more than L2) and keeps the fastest.  Stage 2
+// reads the intermediates of stage 1, which every schedule writes identically.
+template <int PLANES, int STAGES, bool TF32>
+dmrg_status tune_tc(dmrg_plan* p, TcPlan* t, const double* x, double* y, cudaStream_t st) {
+  DMRG_TRY((configure_tc<PLANES, STAGES, TF32>()));
+  constexpr size_t kFlush = size_t(256) << 20;
+  void* flush = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  auto cleanup = [&]() {
+    if (flush) cudaFreeAsync(flush, st);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+  };
+  if (cudaMallocAsync(&flush, kFlush, st) != cudaSuccess ||
+      cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    cudaGetLastError();
+    cleanup();
+    set_error("autotune: allocation of the L2 flush buffer or events failed");
+    return DMRG_ERR_OOM;
+  }
+  dmrg_status s = run_tc_part<PLANES, STAGES, TF32>(p, t, x, y, 0, 0, st);
+  for (int part = 1; part <= 2 && s == DMRG_OK; ++part) {
+    float best = 0.0f;
+    int arg = 0;
+    for (int c = 0; c < kSchedules && s == DMRG_OK; ++c) {
+      float ms[3] = {0.0f, 0.0f, 0.0f};
+      s = run_tc_part<PLANES, STAGES, TF32>(p, t, x, y, part, c, st);
+      for (int r = 0; r < 3 && s == DMRG_OK; ++r) {
+        if (cudaMemsetAsync(flush, r + 1, kFlush, st) != cudaSuccess ||
+            cudaEventRecord(e0, st) != cudaSuccess) {
+          set_error("autotune: %s", cudaGetErrorString(cudaGetLastError()));
+          s = DMRG_ERR_CUDA;
+          break;
+        }
+        s = run_tc_part<PLANES, STAGES, TF32>(p, t, x, y, part, c, st);
+        if (s != DMRG_OK) break;
+        if (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+            cudaEventElapsedTime(&ms[r], e0, e1) != cudaSuccess) {
+          set_error("autotune: %s", cudaGetErrorString(cudaGetLastError()));
+          s = DMRG_ERR_CUDA;
+        }
+      }
+      if (s != DMRG_OK) break;
+      std::sort(ms, ms + 3);
+      t->tune_us[part - 1][c] = ms[1] * 1000.0f;
+      if (c == 0 || ms[1] < best) {
+        best = ms[1];
+        arg = c;
+      }
+    }
+    t->sched[part - 1] = arg;
+  }
+  cleanup();
+  if (s == DMRG_OK && *t->h_err != 0) {
+    set_error("tensor-core projection kernel reported error %d (a bounded wait timed out)",
+              *t->h_err);
+    s = DMRG_ERR_CUDA;
+  }
+  if (s == DMRG_OK) t->tuned = true;
+  return s;
 }
 
 }  // namespace
@@ -775,8 +918,41 @@ dmrg_status launch_project_tc(dmrg_plan* p, dmrg_precision prec, const double* x
     p->tc[slot] = t;
   }
   TcPlan* t = p->tc[slot];
+  if (p->opt.autotune && !t->tuned) {
+    if (prec == DMRG_PREC_TF32) DMRG_TRY((tune_tc<1, 6, true>(p, t, x, y, st)));
+    else DMRG_TRY((tune_tc<3, 2, false>(p, t, x, y, st)));
+  }
   if (prec == DMRG_PREC_TF32) return run_tc<1, 6, true>(p, t, x, y, st);
   return run_tc<3, 2, false>(p, t, x, y, st);
+}
+
+dmrg_status tune_project_tc(dmrg_plan* p, dmrg_precision prec, cudaStream_t st) {
+  const int slot = prec == DMRG_PREC_TF32 ? 0 : 1;
+  if (!p->tc[slot]) {
+    TcPlan* t = nullptr;
+    DMRG_TRY(build_tc(p, prec, st, &t));
+    p->tc[slot] = t;
+  }
+  TcPlan* t = p->tc[slot];
+  // input: diag(H_SB) (any vector of the right size times the same); output: scratch
+  double* y = nullptr;
+  if (cudaMallocAsync((void**)&y, sizeof(double) * (size_t)std::max<int64_t>(p->n, 1), st) != cudaSuccess) {
+    cudaGetLastError();
+    set_error("autotune: scratch allocation failed");
+    return DMRG_ERR_OOM;
+  }
+  dmrg_status s = prec == DMRG_PREC_TF32 ? tune_tc<1, 6, true>(p, t, p->D, y, st)
+                                         : tune_tc<3, 2, false>(p, t, p->D, y, st);
+  cudaFreeAsync(y, st);
+  return s;
+}
+
+void tc_schedule_stats(const dmrg_plan* p, int32_t sched[2], float us[2][3]) {
+  const TcPlan* t = p->tc[1] ? p->tc[1] : p->tc[0];
+  for (int g = 0; g < 2; ++g) {
+    sched[g] = t ? t->sched[g] : -1;
+    for (int c = 0; c < 3; ++c) us[g][c] = t ? t->tune_us[g][c] : 0.0f;
+  }
 }
 
 }  // namespace dmrg

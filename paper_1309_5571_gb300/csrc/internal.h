@@ -144,6 +144,10 @@ dmrg_status launch_project_fp64(dmrg_plan* plan, const double* x, double* y,
 // gemm_tc.cu
 dmrg_status launch_project_tc(dmrg_plan* plan, dmrg_precision prec, const double* x,
                               double* y, cudaStream_t stream);
+// builds the tensor-core plan of prec if needed and times its tile schedules
+dmrg_status tune_project_tc(dmrg_plan* plan, dmrg_precision prec, cudaStream_t stream);
+// chosen schedule per GEMM stage (-1: no tensor-core plan) and the tuning times (us)
+void tc_schedule_stats(const dmrg_plan* plan, int32_t sched[2], float us[2][3]);
 void destroy_tc(dmrg_plan* plan);
 bool tc_available(dmrg_precision prec);
 dmrg_status tc_error_status(dmrg_plan* plan);

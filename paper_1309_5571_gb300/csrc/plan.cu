@@ -427,7 +427,8 @@ dmrg_status dmrg_plan_create(const dmrg_superblock_desc* desc, const dmrg_option
       p->opt.max_iter < 1 || !(p->opt.tol >= 0.0) ||
       (int)p->opt.prec < 0 || (int)p->opt.prec > 3 ||
       (p->opt.anchor_prec != DMRG_PREC_FP64 && p->opt.anchor_prec != DMRG_PREC_FP64_TC) ||
-      p->opt.vector_arith < DMRG_VEC_FP64 || p->opt.vector_arith > DMRG_VEC_SPLIT) {
+      p->opt.vector_arith < DMRG_VEC_FP64 || p->opt.vector_arith > DMRG_VEC_SPLIT ||
+      (p->opt.autotune != 0 && p->opt.autotune != 1)) {
     set_error("options out of range (max_subspace must be in [2, %d])", DMRG_MAX_SUBSPACE);
     delete p;
     return DMRG_ERR_INVALID_ARG;
@@ -507,6 +508,23 @@ dmrg_status dmrg_plan_get_stats(const dmrg_plan* p, dmrg_plan_stats* s) {
   s->tiles_stage1 = p->ntiles1;
   s->tiles_stage2 = p->ntiles2;
   s->device_bytes = (int64_t)p->device_bytes;
+  tc_schedule_stats(p, s->tc_schedule, s->tc_tune_us);
+  return DMRG_OK;
+}
+
+dmrg_status dmrg_plan_autotune(dmrg_plan* p, dmrg_precision prec, void* stream) {
+  if (!p) {
+    set_error("NULL plan");
+    return DMRG_ERR_INVALID_ARG;
+  }
+  if (prec != DMRG_PREC_TF32 && prec != DMRG_PREC_BF16X3) {
+    set_error("autotune: precision must be DMRG_PREC_TF32 or DMRG_PREC_BF16X3");
+    return DMRG_ERR_INVALID_ARG;
+  }
+  if (p->n == 0) return DMRG_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  DMRG_TRY(tune_project_tc(p, prec, st));
+  DMRG_CUDA_TRY(cudaStreamSynchronize(st));
   return DMRG_OK;
 }
 

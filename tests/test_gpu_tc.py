@@ -70,6 +70,25 @@ def test_mixed_davidson_matches_oracle(name, prec):
     assert info["fp64_projections"] >= 1 and info["projections"] >= 1
 
 
+@pytest.mark.parametrize("prec", ["bf16x3", "tf32"])
+def test_autotuned_schedule_gives_identical_projection(prec):
+    # every tile schedule computes each output tile in the same CTA arithmetic, so the
+    # tuned plan and the untuned (descending-cost) plan agree bit for bit
+    sb = problem("ragged")
+    x = cuda(np.random.default_rng(11).standard_normal(sb.n))
+    fixed = Plan(sb, prec=prec, autotune=False)
+    y0 = fixed.project(x).cpu().numpy()
+    assert fixed.get_stats()["tc_schedule"] == [0, 0]
+    tuned = Plan(sb, prec=prec)
+    st = tuned.autotune(prec)
+    assert all(0 <= c <= 2 for c in st["tc_schedule"])
+    assert all(t > 0 for row in st["tc_tune_us"] for t in row)
+    y1 = tuned.project(x).cpu().numpy()
+    np.testing.assert_array_equal(y0, y1)
+    # tuning on first use, inside the projection call, gives the same values
+    np.testing.assert_array_equal(y0, Plan(sb, prec=prec).project(x).cpu().numpy())
+
+
 @pytest.mark.parametrize("name", ["heis_L16_m64", "hub_quarter_L12_m48", "ragged"])
 def test_mixed_davidson_vector_arithmetic(name):
     # split arithmetic (FP64 anchor column, FP32 low-precision columns) reaches the same
