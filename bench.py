@@ -34,6 +34,17 @@ WORKLOAD_DESC = "Hubbard chain t=1 U=4 half filling L=64 m=2048, mid-chain LR su
 METRIC = "H*psi TFLOP/s over a full Davidson solve (tol 1e-10), Hubbard L=64 m=2048"
 
 
+def workload_desc(name):
+    from dmrg_inputs import warmup
+    w = warmup.WORKLOADS[name]
+    if w["model"] == "hubbard":
+        fill = w.get("filling", 1.0)
+        return (f"Hubbard chain t={w.get('t', 1.0):g} U={w.get('U', 4.0):g} "
+                f"{'half' if fill == 1.0 else 'quarter' if fill == 0.5 else fill} filling "
+                f"L={w['L']} m={w['m']}, mid-chain LR superblock")
+    return f"Heisenberg chain J=1 L={w['L']} m={w['m']}, mid-chain LR superblock"
+
+
 def peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -47,6 +58,10 @@ def peaks():
 # profiles/peaks_fp64_tf32_probe.txt
 FP64_DGEMM_TFLOPS = 1.10
 TF32_TFLOPS = 1006.0
+# DRAM bytes (read + write) of one BF16x3 projection of the default workload (pack + the two
+# tcgen05 GEMM launches), from an ncu capture of the current kernels; None when no capture
+# of the current kernels exists
+TC_TRAFFIC = None
 
 
 class ClockSampler:
@@ -220,19 +235,24 @@ def run_project(args):
     x = torch.from_numpy(warmup.start_vector(sb.n, 0)).cuda()
     y = torch.empty_like(x)
     plan = Plan(sb, prec=prec)
+    if prec in ("bf16x3", "tf32"):
+        plan.autotune(prec)
     for _ in range(args.warmup):
         plan.project(x, y, prec=prec)
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.profiler.start()   # profiler range = the timed projections only
     e0.record()
     for _ in range(args.steps):
         plan.project(x, y, prec=prec)
     e1.record()
     torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
     t = e0.elapsed_time(e1) / 1e3 / args.steps
     print(json.dumps({"mode": "project", "workload": args.workload, "prec": prec, "n": sb.n,
-                      "ms": t * 1e3, "tflops": plan.stats["flops"] / t / 1e12}), flush=True)
+                      "ms": t * 1e3, "tflops": plan.stats["flops"] / t / 1e12,
+                      "tc_schedule": plan.get_stats()["tc_schedule"]}), flush=True)
 
 
 def run_batched(args):
@@ -247,7 +267,8 @@ def run_batched(args):
     from paper_1309_5571_gb300 import Plan, solve_batched
     prec = "bf16x3" if args.prec == "auto" else args.prec
     sbs, ms, x0s = warmup.batched_workload(count=args.batch)
-    plist = [Plan(sb, prec=prec) for sb in sbs]   # one plan (and scratch) per problem
+    # one plan (and scratch) per problem
+    plist = [Plan(sb, prec=prec, anchor_prec=args.anchor) for sb in sbs]
     xs = [torch.from_numpy(x).cuda() for x in x0s]
     flops = sum(p.stats["flops"] for p in plist)
     solve_batched(plist, xs, raise_on_nonconvergence=False)  # warm-up (operand images)
@@ -264,7 +285,7 @@ def run_batched(args):
     proj = sum(i["projections"] + i["fp64_projections"] for i in infos)
     print(json.dumps({"mode": "batched", "problems": len(plist), "m": sorted(set(ms)),
                       "m_counts": {int(m): ms.count(m) for m in sorted(set(ms))},
-                      "prec": prec, "batched_s": t_b, "sequential_s": t_s,
+                      "prec": prec, "anchor": args.anchor, "batched_s": t_b, "sequential_s": t_s,
                       "speedup": t_s / t_b, "all_converged": all(i["converged"] for i in infos),
                       "projections": proj,
                       "hpsi_tflops_batched": sum(i["projections"] + i["fp64_projections"]
@@ -342,12 +363,16 @@ def main():
         ev0 = torch.cuda.Event(enable_timing=True)
         ev1 = torch.cuda.Event(enable_timing=True)
         barrier()
+        # profiler range = the timed solves only (ncu --profile-from-start off); no effect
+        # without a profiler
+        torch.cuda.profiler.start()
         ev0.record(stream)
         for _ in range(args.steps):
             x, info = plan.solve(x0_t)
             infos.append(info)
         ev1.record(stream)
         barrier()
+        torch.cuda.profiler.stop()
     launches = capi.kernel_launches() - launches0
     t_step = max_over_ranks(ev0.elapsed_time(ev1) / 1e3 / args.steps, device="cuda")
     proj_per_step = statistics.mean(i["projections"] + i["fp64_projections"] for i in infos)
@@ -381,15 +406,18 @@ def main():
 
     # FP64 path solve time (the comparison arm of the metric), once
     fp64_solve_ms = None
+    e_fp64 = None
     if prec != "fp64":
         plan64 = Plan(sb, prec="fp64", tol=1e-10)
         torch.cuda.synchronize()
         a = time.perf_counter()
         _, info64 = plan64.solve(x0_t)
         fp64_solve_ms = (time.perf_counter() - a) * 1e3
+        e_fp64 = info64["energy"]
         plan64.close()
     else:
         fp64_solve_ms = t_step * 1e3
+        e_fp64 = infos[-1]["energy"]
 
     pk, pk_kind = peaks()
     if prec == "fp64":
@@ -404,7 +432,7 @@ def main():
     achieved = flops / proj[prec] / 1e12
     # DRAM bytes of one BF16x3 projection (pack + two tcgen05 launches) from the ncu capture
     # in profiles/tc_gemm_bf16x3_hub_L64_m2048.md (same kernels as timed here)
-    traffic = 517.6e6 if (prec == "bf16x3" and args.workload == WORKLOAD) else None
+    traffic = TC_TRAFFIC if (prec == "bf16x3" and args.workload == WORKLOAD) else None
     roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
                 "frac": achieved / peak, "traffic": traffic, "kernel": f"projection ({prec})",
                 "peak_source": peak_note}
@@ -425,17 +453,21 @@ def main():
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64" if prec == "fp64" else f"{prec}+f64",
             "data": "synthetic (seeded warm-up generator; operators shaped like the paper's runs)",
-            "config": {"workload": WORKLOAD, "desc": WORKLOAD_DESC, "n": sb.n, "prec": prec,
+            "config": {"workload": args.workload, "desc": workload_desc(args.workload), "n": sb.n,
+                       "prec": prec,
                        "records": plan.stats["records"], "flops_per_projection": flops,
                        "tol": 1e-10, "parallelism": f"replicas x{ws}",
-                       "l2": "solve working set (V, W: 2 x 20 x 29 MB) > L2; L2 flushed "
-                             "between projection timings"},
+                       "l2": f"solve working set (V, W: 2 x 20 x {8 * sb.n / 1e6:.0f} MB) > L2; "
+                             "L2 flushed between projection timings",
+                       "tc_schedule": plan.get_stats()["tc_schedule"],
+                       "device_gb": (plan.get_stats()["device_bytes"] + 8 * 44 * sb.n) / 1e9},
             "solve": {"ms": t_step * 1e3, "iters": infos[-1]["iters"],
                       "projections": infos[-1]["projections"],
                       "fp64_projections": infos[-1]["fp64_projections"],
                       "restarts": infos[-1]["restarts"], "energy": e_ref,
                       "resnorm": infos[-1]["resnorm"], "plan_ms": plan_ms,
-                      "fp64_path_solve_ms": fp64_solve_ms,
+                      "fp64_path_solve_ms": fp64_solve_ms, "fp64_path_energy": e_fp64,
+                      "dE_vs_fp64_path": abs(e_ref - e_fp64),
                       "speedup_vs_fp64_path": (fp64_solve_ms / (t_step * 1e3)) if fp64_solve_ms else None},
             "projection_ms": {p: v * 1e3 for p, v in proj.items()},
             "roofline": roofline,

@@ -66,6 +66,7 @@ struct dmrg_davidson_state {
   bool cur_anchor = false;  // this iteration projects an FP64 anchor
   int knew = 1;             // basis size after a restart decided in phase_b
   bool did_restart = false;
+  bool proj_fp64 = false;   // this iteration's projection is FP64-accurate
 };
 
 namespace {
@@ -231,16 +232,27 @@ namespace {
 //   phase_b  (after a sync) read lambda, ||r||; decide convergence / anchor / restart;
 //            enqueue Gram-Schmidt and normalisation; copy the small state back
 //   phase_c  (after a sync) check for a basis breakdown, append the new column
-dmrg_status phase_a(dmrg_davidson_state* s, cudaStream_t st) {
-  const int64_t ldv = s->ldv, n = s->n;
-  const int k = s->k, col = k - 1;
+// phase_a in three parts, so that a batch can group the low-precision projections:
+// begin decides the projection arithmetic (true: a low-precision one), project runs it,
+// end enqueues the rest of the phase
+bool phase_a_begin(dmrg_davidson_state* s) {
   const bool anchor = s->mixed && s->anchor_pending;
   if (anchor) s->anchored = true;
   s->cur_anchor = anchor;
   const bool fp64 = !s->mixed && (s->plan->opt.prec == DMRG_PREC_FP64 ||
                                    s->plan->opt.prec == DMRG_PREC_FP64_TC);
-  DMRG_TRY(project_col(s, col, fp64 || anchor, st));
+  s->proj_fp64 = fp64 || anchor;
   s->anchor_pending = false;
+  return !s->proj_fp64;
+}
+
+dmrg_status phase_a_project(dmrg_davidson_state* s, cudaStream_t st) {
+  return project_col(s, s->k - 1, s->proj_fp64, st);
+}
+
+dmrg_status phase_a_end(dmrg_davidson_state* s, cudaStream_t st) {
+  const int64_t ldv = s->ldv;
+  const int k = s->k, col = k - 1;
   // after an FP64 anchor, the anchor row of B comes from the exact column W(:,0)
   const double* w0 = (s->mixed && s->anchored) ? s->W : nullptr;
   DMRG_TRY(ov(s, k, s->W + col * ldv, nullptr, col, st, w0));
@@ -248,6 +260,12 @@ dmrg_status phase_a(dmrg_davidson_state* s, cudaStream_t st) {
   DMRG_TRY(res(s, k, s->V + (int64_t)k * ldv, 0, st));
   DMRG_CUDA_TRY(cudaMemcpyAsync(s->hsmall, s->small, sizeof(DevSmall), cudaMemcpyDeviceToHost, st));
   return DMRG_OK;
+}
+
+dmrg_status phase_a(dmrg_davidson_state* s, cudaStream_t st) {
+  phase_a_begin(s);
+  DMRG_TRY(phase_a_project(s, st));
+  return phase_a_end(s, st);
 }
 
 dmrg_status phase_b(dmrg_davidson_state* s, cudaStream_t st, bool* need_c) {
@@ -564,18 +582,83 @@ dmrg_status dmrg_davidson_solve_batched(dmrg_plan* const* plans, int32_t nb,
     sts[i] = owned[found];
     err = dmrg_state_create(plans[i], x0[i], sts[i], &states[i]);
   }
+  // Grouped projections: when every problem has its own plan and all plans project in the
+  // same tensor-core precision, the low-precision projections of one lockstep phase run as
+  // one pack launch and one launch per GEMM stage on a batch stream (TcBatch); FP64 and
+  // FP64-accurate anchor projections stay on the problems' streams.
+  TcBatch* batch = nullptr;
+  cudaStream_t bst = nullptr;
+  cudaEvent_t bdone = nullptr;
+  std::vector<cudaEvent_t> ready(nb, nullptr);
+  const dmrg_precision p0 = nb > 0 ? plans[0]->opt.prec : DMRG_PREC_FP64;
+  bool group = err == DMRG_OK && nb >= 2 && (int)owned.size() == nb &&
+               (p0 == DMRG_PREC_TF32 || p0 == DMRG_PREC_BF16X3);
+  for (int i = 0; i < nb && group; ++i) group = plans[i]->opt.prec == p0;
+  if (group) {
+    if (cudaStreamCreateWithFlags(&bst, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamWaitEvent(bst, start_ev, 0) != cudaSuccess ||
+        cudaEventCreateWithFlags(&bdone, cudaEventDisableTiming) != cudaSuccess) {
+      set_error("dmrg_davidson_solve_batched: stream creation failed");
+      err = DMRG_ERR_CUDA;
+    }
+    for (int i = 0; i < nb && err == DMRG_OK; ++i)
+      if (cudaEventCreateWithFlags(&ready[i], cudaEventDisableTiming) != cudaSuccess) {
+        set_error("dmrg_davidson_solve_batched: event creation failed");
+        err = DMRG_ERR_CUDA;
+      }
+    if (err == DMRG_OK) err = tc_batch_create(plans, nb, p0, bst, &batch);
+  }
+  std::vector<const double*> bx(nb, nullptr);
+  std::vector<double*> by(nb, nullptr);
+  std::vector<char> lp(nb, 0);
   // lockstep: every phase is enqueued for all active problems before one wait for all
   for (int it = 0; err == DMRG_OK; ++it) {
-    bool any = false;
+    bool any = false, any_lp = false;
     for (int i = 0; i < nb; ++i) {
+      lp[i] = 0;
       if (!active[i]) continue;
       if (states[i]->converged || states[i]->iters >= plans[i]->opt.max_iter) {
         active[i] = 0;
         continue;
       }
       any = true;
-      status[i] = phase_a(states[i], sts[i]);
+      dmrg_davidson_state* s = states[i];
+      const bool is_lp = phase_a_begin(s);
+      if (batch && is_lp) {
+        lp[i] = 1;
+        any_lp = true;
+        bx[i] = s->V + (int64_t)(s->k - 1) * s->ldv;
+        by[i] = s->W + (int64_t)(s->k - 1) * s->ldv;
+        if (cudaEventRecord(ready[i], sts[i]) != cudaSuccess ||
+            cudaStreamWaitEvent(bst, ready[i], 0) != cudaSuccess) {
+          set_error("dmrg_davidson_solve_batched: event record failed");
+          err = DMRG_ERR_CUDA;
+        }
+        continue;
+      }
+      status[i] = phase_a_project(s, sts[i]);
+      if (status[i] == DMRG_OK) status[i] = phase_a_end(s, sts[i]);
       if (status[i] != DMRG_OK) active[i] = 0;
+    }
+    if (err != DMRG_OK) break;
+    if (any_lp) {
+      err = tc_batch_project(batch, bx.data(), by.data(), lp.data(), bst);
+      if (err == DMRG_OK && cudaEventRecord(bdone, bst) != cudaSuccess) {
+        set_error("dmrg_davidson_solve_batched: event record failed");
+        err = DMRG_ERR_CUDA;
+      }
+      for (int i = 0; i < nb && err == DMRG_OK; ++i) {
+        if (!lp[i]) continue;
+        states[i]->projections++;
+        if (cudaStreamWaitEvent(sts[i], bdone, 0) != cudaSuccess) {
+          set_error("dmrg_davidson_solve_batched: stream wait failed");
+          err = DMRG_ERR_CUDA;
+          break;
+        }
+        status[i] = phase_a_end(states[i], sts[i]);
+        if (status[i] != DMRG_OK) active[i] = 0;
+      }
+      if (err != DMRG_OK) break;
     }
     if (!any) break;
     std::vector<char> need_c(nb, 0);
@@ -587,6 +670,10 @@ dmrg_status dmrg_davidson_solve_batched(dmrg_plan* const* plans, int32_t nb,
         break;
       }
       bool c = false;
+      if (batch && tc_batch_error(batch) != DMRG_OK) {
+        err = DMRG_ERR_CUDA;
+        break;
+      }
       status[i] = phase_b(states[i], sts[i], &c);
       need_c[i] = c;
       if (status[i] != DMRG_OK) active[i] = 0;
@@ -627,6 +714,12 @@ dmrg_status dmrg_davidson_solve_batched(dmrg_plan* const* plans, int32_t nb,
     }
     cudaStreamSynchronize(os);
   }
+  if (bst) cudaStreamSynchronize(bst);
+  tc_batch_destroy(batch);
+  for (cudaEvent_t e : ready)
+    if (e) cudaEventDestroy(e);
+  if (bdone) cudaEventDestroy(bdone);
+  if (bst) cudaStreamDestroy(bst);
   for (int i = 0; i < nb; ++i) dmrg_state_destroy(states[i]);
   for (cudaStream_t os : owned) cudaStreamDestroy(os);
   cudaEventDestroy(start_ev);

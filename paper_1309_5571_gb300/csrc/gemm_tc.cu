@@ -31,9 +31,11 @@
 // error code, stops issuing work, waits (bounded) for its own copies and MMAs, frees TMEM
 // and returns.
 #include <cuda_bf16.h>
+#include <stdio.h>
 
 #include <algorithm>
 #include <functional>
+#include <vector>
 #include <map>
 #include <tuple>
 
@@ -79,6 +81,18 @@ struct PackChunk {
 
 enum TcBuf { TB_OPS = 0, TB_XA = 1, TB_XB = 2, TB_INTER = 3 };
 
+// Per-problem pointers of a grouped launch over several plans (TcBatch): tiles and pack
+// chunks carry the problem index; problems with active == 0 are skipped.
+struct TcPtrs {
+  const double* arena;
+  const double* x;
+  double* y;
+  const uint8_t* ops;
+  uint8_t* xa;          // A-form and B-form vector images (one buffer)
+  uint8_t* inter;
+  int32_t active, pad_;
+};
+
 // Tile schedules (the order in which the persistent CTAs take the output tiles; CTA b takes
 // tiles b, b + grid, ...).  Every schedule covers the same tiles, so the results are
 // identical; only the operand reuse in L2 and the load balance differ.
@@ -111,6 +125,12 @@ struct TcPlan {
   int* d_err = nullptr;   // device view of a mapped host word: kernel error codes
   int* h_err = nullptr;
   int sms = 0;
+  // host copies for grouped launches over several plans (TcBatch)
+  std::vector<TcJob> h_jobs;
+  std::vector<TcSeg> h_segs;
+  std::vector<std::pair<int64_t, int>> h_order[2];  // (cost per tile, job), descending
+  std::vector<PackJob> h_xjobs;
+  std::vector<PackChunk> h_xchunks;
 };
 
 namespace tc {
@@ -126,10 +146,17 @@ template <int PLANES, bool TF32>
 __global__ void __launch_bounds__(256)
 pack_kernel(const PackChunk* __restrict__ chunks, const PackJob* __restrict__ jobs,
             const double* __restrict__ arena, const double* __restrict__ x,
-            uint8_t* __restrict__ dst) {
+            uint8_t* __restrict__ dst, const TcPtrs* __restrict__ ptrs) {
   constexpr int EPG = TF32 ? 4 : 8;  // elements per 16-byte group
   constexpr int KT = TF32 ? 32 : 64;
   const PackChunk ch = chunks[blockIdx.x];
+  if (ptrs) {  // grouped launch: the chunk's problem
+    const TcPtrs& pt = ptrs[ch.pad_];
+    if (!pt.active) return;
+    arena = pt.arena;
+    x = pt.x;
+    dst = pt.xa;
+  }
   const PackJob jb = jobs[ch.job];
   const double* src = (jb.src_space ? x : arena) + jb.src_off;
   uint8_t* base = dst + jb.dst_off + ((int64_t)ch.rt * jb.nkt + ch.kt) * PLANES * kChunk;
@@ -193,7 +220,8 @@ tc_gemm_kernel(const TcTile* __restrict__ tiles, int ntiles, const TcJob* __rest
                const TcSeg* __restrict__ segs, const uint8_t* __restrict__ b0,
                const uint8_t* __restrict__ b1, const uint8_t* __restrict__ b2,
                const uint8_t* __restrict__ b3, uint8_t* __restrict__ out_img,
-               double* __restrict__ y, const double* __restrict__ x, int* __restrict__ gerr) {
+               double* __restrict__ y, const double* __restrict__ x, int* __restrict__ gerr,
+               const TcPtrs* __restrict__ ptrs, int gemm_stage) {
   constexpr uint32_t kStageA = PLANES * kChunk;
   constexpr uint32_t kStage = 2 * kStageA;
   constexpr int KT = TF32 ? 32 : 64;
@@ -230,7 +258,9 @@ tc_gemm_kernel(const TcTile* __restrict__ tiles, int ntiles, const TcJob* __rest
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem_base = tmem_slot;
-  const uint8_t* bufs[4] = {b0, b1, b2, b3};
+  // grouped launch (ptrs != NULL): the operand buffers and outputs of each tile are those
+  // of its problem (tile.pad_), and tiles of inactive problems are skipped by all roles
+  auto active = [&](const TcTile& tile) { return !ptrs || ptrs[tile.pad_].active != 0; };
 
   if (warp == 0) {
     // ------------------------------------------------ producer
@@ -240,6 +270,14 @@ tc_gemm_kernel(const TcTile* __restrict__ tiles, int ntiles, const TcJob* __rest
       int64_t issued = 0;
       for (int t = blockIdx.x; t < ntiles && !abort_flag; t += gridDim.x) {
         const TcTile tile = tiles[t];
+        if (!active(tile)) continue;
+        const uint8_t* bufs[4] = {b0, b1, b2, b3};
+        if (ptrs) {
+          const TcPtrs& pt = ptrs[tile.pad_];
+          bufs[0] = pt.ops;
+          bufs[1] = bufs[2] = pt.xa;
+          bufs[3] = gemm_stage == 2 ? pt.inter : nullptr;
+        }
         const TcJob job = jobs[tile.job];
         for (int si = job.seg_begin; si < job.seg_end && !abort_flag; ++si) {
           const TcSeg sg = segs[si];
@@ -278,6 +316,7 @@ tc_gemm_kernel(const TcTile* __restrict__ tiles, int ntiles, const TcJob* __rest
       bool any = false;
       constexpr uint32_t idesc = instr_desc<TF32>();
       for (int t = blockIdx.x; t < ntiles && !abort_flag; t += gridDim.x) {
+        if (!active(tiles[t])) continue;
         const TcJob job = jobs[tiles[t].job];
         if (job.seg_begin == job.seg_end) continue;
         if (!mbar_wait(smem_u32(&tempty_bar[acc]), acc_phase ^ 1, &abort_flag, gerr, 2)) break;
@@ -328,6 +367,16 @@ tc_gemm_kernel(const TcTile* __restrict__ tiles, int ntiles, const TcJob* __rest
     uint32_t acc_phase = 0;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
       const TcTile tile = tiles[t];
+      if (!active(tile)) continue;
+      uint8_t* o_img = out_img;
+      double* o_y = y;
+      const double* i_x = x;
+      if (ptrs) {
+        const TcPtrs& pt = ptrs[tile.pad_];
+        o_img = gemm_stage == 1 ? pt.inter : nullptr;
+        o_y = pt.y;
+        i_x = pt.x;
+      }
       const TcJob job = jobs[tile.job];
       const bool has = job.seg_begin < job.seg_end;
       if (has) {
@@ -346,8 +395,8 @@ tc_gemm_kernel(const TcTile* __restrict__ tiles, int ntiles, const TcJob* __rest
         const int n0 = tile.nt * kRows + c0;
         if (job.out_fp64) {
           if (m < job.M) {
-            double* yr = y + job.out_off + m * job.N;
-            const double* xr = x + job.x_off + m * job.N;
+            double* yr = o_y + job.out_off + m * job.N;
+            const double* xr = i_x + job.x_off + m * job.N;
 #pragma unroll
             for (int j = 0; j < 32; ++j) {
               const int n = n0 + j;
@@ -361,7 +410,7 @@ tc_gemm_kernel(const TcTile* __restrict__ tiles, int ntiles, const TcJob* __rest
         } else {
           const int kt = n0 / KT;
           if (kt < job.out_nkt) {
-            uint8_t* tb = out_img + job.out_off + ((int64_t)tile.mt * job.out_nkt + kt) * PLANES * kChunk;
+            uint8_t* tb = o_img + job.out_off + ((int64_t)tile.mt * job.out_nkt + kt) * PLANES * kChunk;
             if constexpr (TF32) {
 #pragma unroll
               for (int g = 0; g < 8; ++g) {
@@ -477,9 +526,45 @@ dmrg_status launch_pack(const std::vector<PackChunk>& chunks, const PackChunk* d
                         const PackJob* d_jobs, const double* arena, const double* x,
                         uint8_t* dst, cudaStream_t st) {
   if (chunks.empty()) return DMRG_OK;
-  tc::pack_kernel<PLANES, TF32><<<(unsigned)chunks.size(), 256, 0, st>>>(d_chunks, d_jobs, arena, x, dst);
+  tc::pack_kernel<PLANES, TF32><<<(unsigned)chunks.size(), 256, 0, st>>>(d_chunks, d_jobs, arena, x, dst,
+                                                                          nullptr);
   DMRG_LAUNCH_CHECK();
   return DMRG_OK;
+}
+
+// Checks that every operand tile a GEMM tile reads and every output it writes lie inside
+// the plan's buffers (byte sizes buf_bytes, TB_XB aliasing TB_XA; y has n elements).
+bool tc_tiles_in_range(const TcPlan* t, int64_t n, const std::vector<TcJob>& jobs,
+                       const std::vector<TcSeg>& segs, const std::vector<TcTile>& tiles,
+                       int job_base, int seg_base, char* why, size_t why_len) {
+  const int64_t stageA = (int64_t)t->planes * kChunk;
+  auto bytes = [&](int b) { return (int64_t)t->buf_bytes[b == TB_XB ? TB_XA : b]; };
+  for (const TcTile& tl : tiles) {
+    const TcJob& j = jobs[tl.job - job_base];
+    for (int si = j.seg_begin; si < j.seg_end; ++si) {
+      const TcSeg& sg = segs[si - seg_base];
+      const int64_t pe = sg.p_off + ((int64_t)tl.mt * sg.p_nkt + sg.nkt) * stageA;
+      const int64_t qe = sg.q_off + ((int64_t)tl.nt * sg.q_nkt + sg.nkt) * stageA;
+      if (sg.p_off < 0 || pe > bytes(sg.p_buf) || sg.q_off < 0 || qe > bytes(sg.q_buf)) {
+        snprintf(why, why_len, "tile (job %d, %d, %d) segment %d reads outside its operand images",
+                 tl.job, tl.mt, tl.nt, si);
+        return false;
+      }
+    }
+    if (j.out_fp64) {
+      if (j.out_off < 0 || j.out_off + (int64_t)j.M * j.N > n || j.x_off < 0 ||
+          j.x_off + (int64_t)j.M * j.N > n) {
+        snprintf(why, why_len, "tile (job %d) writes outside y or reads outside x", tl.job);
+        return false;
+      }
+    } else if (j.out_off < 0 ||
+               j.out_off + ((int64_t)tl.mt * j.out_nkt + j.out_nkt) * stageA > bytes(TB_INTER)) {
+      snprintf(why, why_len, "tile (job %d, %d, %d) writes outside the intermediate images",
+               tl.job, tl.mt, tl.nt);
+      return false;
+    }
+  }
+  return true;
 }
 
 dmrg_status build_tc(dmrg_plan* p, dmrg_precision prec, cudaStream_t st, TcPlan** out) {
@@ -645,15 +730,15 @@ dmrg_status build_tc(dmrg_plan* p, dmrg_precision prec, cudaStream_t st, TcPlan*
   };
   std::stable_sort(order1.begin(), order1.end(), by_cost);
   std::stable_sort(order2.begin(), order2.end(), by_cost);
-  auto add_tiles = [&](std::vector<TcTile>& out, int jb, bool col_major) {
+  auto add_tiles = [&](std::vector<TcTile>& dst, int jb, bool col_major) {
     const TcJob& j = jobs[jb];
     const int nm = ceil_div(j.M, kRows), nn = ceil_div(j.N, kRows);
     if (col_major) {
       for (int nt = 0; nt < nn; ++nt)
-        for (int mt = 0; mt < nm; ++mt) out.push_back(TcTile{jb, mt, nt, 0});
+        for (int mt = 0; mt < nm; ++mt) dst.push_back(TcTile{jb, mt, nt, 0});
     } else {
       for (int mt = 0; mt < nm; ++mt)
-        for (int nt = 0; nt < nn; ++nt) out.push_back(TcTile{jb, mt, nt, 0});
+        for (int nt = 0; nt < nn; ++nt) dst.push_back(TcTile{jb, mt, nt, 0});
     }
   };
   // jobs (already in descending cost) grouped by key; groups in descending total cost
@@ -670,10 +755,10 @@ dmrg_status build_tc(dmrg_plan* p, dmrg_precision prec, cudaStream_t st, TcPlan*
     std::stable_sort(gorder.begin(), gorder.end(), [](const auto& a, const auto& b) {
       return a.first != b.first ? a.first > b.first : a.second < b.second;
     });
-    std::vector<TcTile> out;
+    std::vector<TcTile> res;
     for (const auto& g : gorder)
-      for (int jb : groups[g.second].second) add_tiles(out, jb, col_major);
-    return out;
+      for (int jb : groups[g.second].second) add_tiles(res, jb, col_major);
+    return res;
   };
   std::vector<TcTile> sched1[kSchedules], sched2[kSchedules];
   for (const auto& pr : order1) add_tiles(sched1[0], pr.second, false);
@@ -718,6 +803,14 @@ dmrg_status build_tc(dmrg_plan* p, dmrg_precision prec, cudaStream_t st, TcPlan*
     p->device_bytes += t->buf_bytes[b];
   }
   t->buf[TB_XB] = t->buf[TB_XA];  // alias: B-form offsets follow the A-form tiles
+  {
+    char why[160];
+    if (!tc_tiles_in_range(t, p->n, jobs, segs, tiles1, 0, 0, why, sizeof(why)) ||
+        !tc_tiles_in_range(t, p->n, jobs, segs, tiles2, 0, 0, why, sizeof(why))) {
+      set_error("internal: %s", why);
+      return fail(DMRG_ERR_SHAPE);
+    }
+  }
   if (t->buf[TB_INTER]) {
     // intermediate tiles beyond the written rows stay zero
     DMRG_CUDA_TRY(cudaMemsetAsync(t->buf[TB_INTER], 0, t->buf_bytes[TB_INTER], st));
@@ -755,6 +848,12 @@ dmrg_status build_tc(dmrg_plan* p, dmrg_precision prec, cudaStream_t st, TcPlan*
   }
   t->ntiles1 = (int64_t)tiles1.size();
   t->ntiles2 = (int64_t)tiles2.size();
+  t->h_jobs = jobs;
+  t->h_segs = segs;
+  t->h_order[0] = order1;
+  t->h_order[1] = order2;
+  t->h_xjobs = x_jobs;
+  t->h_xchunks = x_chunks;
   if (cudaHostAlloc((void**)&t->h_err, sizeof(int), cudaHostAllocMapped) != cudaSuccess ||
       cudaHostGetDevicePointer((void**)&t->d_err, t->h_err, 0) != cudaSuccess) {
     cudaGetLastError();
@@ -789,7 +888,7 @@ dmrg_status run_tc_part(dmrg_plan* p, TcPlan* t, const double* x, double* y, int
   if (part == 0) {
     if (t->n_xpack_chunks > 0) {  // X -> A-form and B-form images
       tc::pack_kernel<PLANES, TF32><<<(unsigned)t->n_xpack_chunks, 256, 0, st>>>(
-          t->d_xpack_chunks, t->d_xpack_jobs, p->arena, x, t->buf[TB_XA]);
+          t->d_xpack_chunks, t->d_xpack_jobs, p->arena, x, t->buf[TB_XA], nullptr);
       DMRG_LAUNCH_CHECK();
     }
     return DMRG_OK;
@@ -800,7 +899,7 @@ dmrg_status run_tc_part(dmrg_plan* p, TcPlan* t, const double* x, double* y, int
   tc::tc_gemm_kernel<PLANES, STAGES, TF32><<<grid, tc::kThreads, smem, st>>>(
       t->d_tiles[part - 1][c], (int)nt, t->d_jobs, t->d_segs, t->buf[TB_OPS], t->buf[TB_XA],
       t->buf[TB_XB], part == 1 ? nullptr : t->buf[TB_INTER], part == 1 ? t->buf[TB_INTER] : nullptr,
-      y, x, t->d_err);
+      y, x, t->d_err, nullptr, part);
   DMRG_LAUNCH_CHECK();
   return DMRG_OK;
 }
@@ -884,6 +983,228 @@ dmrg_status tune_tc(dmrg_plan* p, TcPlan* t, const double* x, double* y, cudaStr
 }
 
 }  // namespace
+
+// ======================================================================== grouped launch
+// One pack launch and one launch per GEMM stage for the low-precision projections of many
+// independent plans (batched Davidson solves): the jobs, segments, tiles and pack chunks of
+// all plans are concatenated once; every tile and chunk carries its problem index, and a
+// small per-call table gives each problem's vector pointers and whether it takes part.
+// Tiles of all problems are taken in one descending-cost order (longest first).
+struct TcBatch {
+  dmrg_precision prec = DMRG_PREC_BF16X3;
+  std::vector<dmrg_plan*> plans;
+  TcJob* d_jobs = nullptr;
+  TcSeg* d_segs = nullptr;
+  TcTile* d_tiles[2] = {nullptr, nullptr};
+  int64_t ntiles[2] = {0, 0};
+  PackJob* d_pjobs = nullptr;
+  PackChunk* d_pchunks = nullptr;
+  int64_t nchunks = 0;
+  TcPtrs* d_ptrs = nullptr;
+  TcPtrs* h_ptrs[2] = {nullptr, nullptr};   // pinned ring: slot r reused after ev[r]
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  int slot = 0;
+  int* d_err = nullptr;
+  int* h_err = nullptr;
+  int sms = 0;
+};
+
+void tc_batch_destroy(TcBatch* b) {
+  if (!b) return;
+  cudaFree(b->d_jobs);
+  cudaFree(b->d_segs);
+  cudaFree(b->d_tiles[0]);
+  cudaFree(b->d_tiles[1]);
+  cudaFree(b->d_pjobs);
+  cudaFree(b->d_pchunks);
+  cudaFree(b->d_ptrs);
+  for (int r = 0; r < 2; ++r) {
+    if (b->ev[r]) {
+      cudaEventSynchronize(b->ev[r]);
+      cudaEventDestroy(b->ev[r]);
+    }
+    if (b->h_ptrs[r]) cudaFreeHost(b->h_ptrs[r]);
+  }
+  if (b->h_err) cudaFreeHost(b->h_err);
+  delete b;
+}
+
+dmrg_status tc_batch_create(dmrg_plan* const* plans, int nb, dmrg_precision prec,
+                            cudaStream_t st, TcBatch** out) {
+  *out = nullptr;
+  if (prec != DMRG_PREC_TF32 && prec != DMRG_PREC_BF16X3) {
+    set_error("internal: grouped launch needs a TF32 or BF16X3 plan");
+    return DMRG_ERR_INVALID_ARG;
+  }
+  const int slot = prec == DMRG_PREC_TF32 ? 0 : 1;
+  TcBatch* b = new TcBatch();
+  b->prec = prec;
+  auto fail = [&](dmrg_status e) { tc_batch_destroy(b); return e; };
+  std::vector<TcJob> jobs;
+  std::vector<TcSeg> segs;
+  std::vector<PackJob> pjobs;
+  std::vector<PackChunk> pchunks;
+  struct Item { int64_t cost; int prob, job; };
+  std::vector<Item> items[2];
+  for (int i = 0; i < nb; ++i) {
+    dmrg_plan* p = plans[i];
+    if (!p->tc[slot]) {
+      TcPlan* t = nullptr;
+      dmrg_status e = build_tc(p, prec, st, &t);
+      if (e != DMRG_OK) return fail(e);
+      p->tc[slot] = t;
+    }
+    const TcPlan* t = p->tc[slot];
+    b->plans.push_back(p);
+    b->sms = t->sms;
+    const int job0 = (int)jobs.size(), seg0 = (int)segs.size(), pjob0 = (int)pjobs.size();
+    for (TcJob j : t->h_jobs) {
+      j.seg_begin += seg0;
+      j.seg_end += seg0;
+      jobs.push_back(j);
+    }
+    segs.insert(segs.end(), t->h_segs.begin(), t->h_segs.end());
+    for (int g = 0; g < 2; ++g)
+      for (const auto& pr : t->h_order[g]) items[g].push_back(Item{pr.first, i, job0 + pr.second});
+    pjobs.insert(pjobs.end(), t->h_xjobs.begin(), t->h_xjobs.end());
+    for (PackChunk c : t->h_xchunks) {
+      c.job += pjob0;
+      c.pad_ = i;
+      pchunks.push_back(c);
+    }
+  }
+  std::vector<TcTile> tiles[2];
+  for (int g = 0; g < 2; ++g) {
+    std::stable_sort(items[g].begin(), items[g].end(), [](const Item& a, const Item& c) {
+      return a.cost > c.cost;
+    });
+    for (const Item& it : items[g]) {
+      const TcJob& j = jobs[it.job];
+      for (int mt = 0; mt < ceil_div(j.M, kRows); ++mt)
+        for (int nt = 0; nt < ceil_div(j.N, kRows); ++nt) tiles[g].push_back(TcTile{it.job, mt, nt, it.prob});
+    }
+    b->ntiles[g] = (int64_t)tiles[g].size();
+  }
+  {
+    // every tile of problem i against problem i's own buffers
+    std::vector<int> job_base(nb + 1, 0), seg_base(nb + 1, 0);
+    for (int i = 0; i < nb; ++i) {
+      job_base[i + 1] = job_base[i] + (int)plans[i]->tc[slot]->h_jobs.size();
+      seg_base[i + 1] = seg_base[i] + (int)plans[i]->tc[slot]->h_segs.size();
+    }
+    char why[160];
+    for (int g = 0; g < 2; ++g) {
+      for (const TcTile& tl : tiles[g]) {
+        const int i = tl.pad_;
+        if (i < 0 || i >= nb || tl.job < job_base[i] || tl.job >= job_base[i + 1]) {
+          set_error("internal: grouped tile with a bad problem or job index");
+          return fail(DMRG_ERR_SHAPE);
+        }
+        const TcPlan* t = plans[i]->tc[slot];
+        TcJob j = jobs[tl.job];
+        j.seg_begin -= seg_base[i];
+        j.seg_end -= seg_base[i];
+        std::vector<TcJob> one(1, j);
+        std::vector<TcTile> onet(1, TcTile{0, tl.mt, tl.nt, 0});
+        if (j.seg_begin < 0 || j.seg_end > (int)t->h_segs.size() ||
+            !tc_tiles_in_range(t, plans[i]->n, one, t->h_segs, onet, 0, 0, why, sizeof(why))) {
+          set_error("internal: grouped launch, problem %d: %s", i, why);
+          return fail(DMRG_ERR_SHAPE);
+        }
+      }
+    }
+    for (const PackChunk& c : pchunks) {
+      if (c.pad_ < 0 || c.pad_ >= nb || c.job < 0 || c.job >= (int)pjobs.size()) {
+        set_error("internal: grouped pack chunk with a bad index");
+        return fail(DMRG_ERR_SHAPE);
+      }
+    }
+  }
+  dmrg_status e;
+  if ((e = upload_vec(&b->d_jobs, jobs, st)) != DMRG_OK) return fail(e);
+  if ((e = upload_vec(&b->d_segs, segs, st)) != DMRG_OK) return fail(e);
+  if ((e = upload_vec(&b->d_tiles[0], tiles[0], st)) != DMRG_OK) return fail(e);
+  if ((e = upload_vec(&b->d_tiles[1], tiles[1], st)) != DMRG_OK) return fail(e);
+  if ((e = upload_vec(&b->d_pjobs, pjobs, st)) != DMRG_OK) return fail(e);
+  if ((e = upload_vec(&b->d_pchunks, pchunks, st)) != DMRG_OK) return fail(e);
+  b->nchunks = (int64_t)pchunks.size();
+  if (cudaMalloc((void**)&b->d_ptrs, sizeof(TcPtrs) * std::max(nb, 1)) != cudaSuccess ||
+      cudaHostAlloc((void**)&b->h_ptrs[0], sizeof(TcPtrs) * std::max(nb, 1), cudaHostAllocDefault) != cudaSuccess ||
+      cudaHostAlloc((void**)&b->h_ptrs[1], sizeof(TcPtrs) * std::max(nb, 1), cudaHostAllocDefault) != cudaSuccess ||
+      cudaEventCreateWithFlags(&b->ev[0], cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&b->ev[1], cudaEventDisableTiming) != cudaSuccess ||
+      cudaHostAlloc((void**)&b->h_err, sizeof(int), cudaHostAllocMapped) != cudaSuccess ||
+      cudaHostGetDevicePointer((void**)&b->d_err, b->h_err, 0) != cudaSuccess) {
+    cudaGetLastError();
+    set_error("grouped launch: allocation failed");
+    return fail(DMRG_ERR_OOM);
+  }
+  *b->h_err = 0;
+  DMRG_CUDA_TRY(cudaStreamSynchronize(st));
+  *out = b;
+  return DMRG_OK;
+}
+
+dmrg_status tc_batch_error(const TcBatch* b) {
+  if (b && b->h_err && *b->h_err != 0) {
+    set_error("grouped tensor-core projection reported error %d (a bounded wait timed out)", *b->h_err);
+    return DMRG_ERR_CUDA;
+  }
+  return DMRG_OK;
+}
+
+namespace {
+template <int PLANES, int STAGES, bool TF32>
+dmrg_status run_batch(TcBatch* b, cudaStream_t st) {
+  constexpr size_t smem = tc::smem_bytes<PLANES, STAGES, TF32>();
+  DMRG_TRY((configure_tc<PLANES, STAGES, TF32>()));
+  if (b->nchunks > 0) {
+    tc::pack_kernel<PLANES, TF32><<<(unsigned)b->nchunks, 256, 0, st>>>(
+        b->d_pchunks, b->d_pjobs, nullptr, nullptr, nullptr, b->d_ptrs);
+    DMRG_LAUNCH_CHECK();
+  }
+  for (int part = 1; part <= 2; ++part) {
+    const int64_t nt = b->ntiles[part - 1];
+    if (nt == 0) continue;
+    const int grid = (int)std::min<int64_t>(nt, b->sms);
+    tc::tc_gemm_kernel<PLANES, STAGES, TF32><<<grid, tc::kThreads, smem, st>>>(
+        b->d_tiles[part - 1], (int)nt, b->d_jobs, b->d_segs, nullptr, nullptr, nullptr, nullptr,
+        nullptr, nullptr, nullptr, b->d_err, b->d_ptrs, part);
+    DMRG_LAUNCH_CHECK();
+  }
+  return DMRG_OK;
+}
+}  // namespace
+
+dmrg_status tc_batch_project(TcBatch* b, const double* const* x, double* const* y,
+                             const char* active, cudaStream_t st) {
+  DMRG_TRY(tc_batch_error(b));
+  const int slot = b->prec == DMRG_PREC_TF32 ? 0 : 1;
+  const int r = b->slot;
+  b->slot ^= 1;
+  // the pinned slot is rewritten only after its previous copy has completed
+  DMRG_CUDA_TRY(cudaEventSynchronize(b->ev[r]));
+  TcPtrs* h = b->h_ptrs[r];
+  bool any = false;
+  for (size_t i = 0; i < b->plans.size(); ++i) {
+    const dmrg_plan* p = b->plans[i];
+    const TcPlan* t = p->tc[slot];
+    h[i] = TcPtrs{p->arena, x[i], y[i], t->buf[TB_OPS], t->buf[TB_XA], t->buf[TB_INTER],
+                  active[i] ? 1 : 0, 0};
+    if (active[i] && (!x[i] || !y[i] || !t->buf[TB_OPS] || !t->buf[TB_XA] ||
+                      (t->ntiles1 > 0 && !t->buf[TB_INTER]))) {
+      set_error("internal: grouped projection of problem %zu without its buffers", i);
+      return DMRG_ERR_INVALID_ARG;
+    }
+    any = any || active[i];
+  }
+  if (!any) return DMRG_OK;
+  DMRG_CUDA_TRY(cudaMemcpyAsync(b->d_ptrs, h, sizeof(TcPtrs) * b->plans.size(),
+                                cudaMemcpyHostToDevice, st));
+  DMRG_CUDA_TRY(cudaEventRecord(b->ev[r], st));
+  if (b->prec == DMRG_PREC_TF32) return run_batch<1, 6, true>(b, st);
+  return run_batch<3, 2, false>(b, st);
+}
 
 bool tc_available(dmrg_precision prec) {
   return prec == DMRG_PREC_TF32 || prec == DMRG_PREC_BF16X3 || prec == DMRG_PREC_FP64_TC;

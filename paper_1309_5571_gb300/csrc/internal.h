@@ -148,6 +148,15 @@ dmrg_status launch_project_tc(dmrg_plan* plan, dmrg_precision prec, const double
 dmrg_status tune_project_tc(dmrg_plan* plan, dmrg_precision prec, cudaStream_t stream);
 // chosen schedule per GEMM stage (-1: no tensor-core plan) and the tuning times (us)
 void tc_schedule_stats(const dmrg_plan* plan, int32_t sched[2], float us[2][3]);
+// grouped launch of the low-precision projections of several distinct plans
+struct TcBatch;
+dmrg_status tc_batch_create(dmrg_plan* const* plans, int nb, dmrg_precision prec,
+                            cudaStream_t stream, TcBatch** out);
+// y[i] = H_i x[i] for every i with active[i]; x[i], y[i] are device vectors of plan i
+dmrg_status tc_batch_project(TcBatch* b, const double* const* x, double* const* y,
+                             const char* active, cudaStream_t stream);
+dmrg_status tc_batch_error(const TcBatch* b);
+void tc_batch_destroy(TcBatch* b);
 void destroy_tc(dmrg_plan* plan);
 bool tc_available(dmrg_precision prec);
 dmrg_status tc_error_status(dmrg_plan* plan);
