@@ -59,9 +59,9 @@ def peaks():
 FP64_DGEMM_TFLOPS = 1.10
 TF32_TFLOPS = 1006.0
 # DRAM bytes (read + write) of one BF16x3 projection of the default workload (pack + the two
-# tcgen05 GEMM launches), from an ncu capture of the current kernels; None when no capture
-# of the current kernels exists
-TC_TRAFFIC = None
+# tcgen05 GEMM launches: 31.5 + 162.7 + 316.2 MB), from the ncu capture of the current
+# kernels in profiles/tc_gemm_bf16x3_hub_L64_m2048.md
+TC_TRAFFIC = 510.4e6
 
 
 class ClockSampler:

@@ -319,9 +319,11 @@ dmrg_status phase_b(dmrg_davidson_state* s, cudaStream_t st, bool* need_c) {
         (k > 1 && ratio > 0.0 && s->rnorm <= ratio * s->anchor_rnorm))
       do_anchor = true;
     if (trace_on())
-      fprintf(stderr, "dmrg it %4d k %2d %s lambda % .15f r %.3e floor %.3e ytail %.2e sweeps %d fallbacks %d%s\n",
+      fprintf(stderr, "dmrg it %4d k %2d %s lambda % .15f r %.3e floor %.3e ytail %.2e sweeps %d "
+              "eig cycles %lld/%lld/%lld fallbacks %d%s\n",
               s->iters, k, anchor ? "FP64" : "lp  ", s->lambda, s->rnorm, floor_est, ytail,
-              h.jacobi_sweeps, h.eig_fallbacks, do_anchor ? "  -> anchor" : "");
+              h.jacobi_sweeps, (long long)h.eig_cycles[0], (long long)h.eig_cycles[1],
+              (long long)h.eig_cycles[2], h.eig_fallbacks, do_anchor ? "  -> anchor" : "");
   } else if (trace_on()) {
     fprintf(stderr, "dmrg it %4d k %2d lambda % .15f r %.3e sweeps %d fallbacks %d\n", s->iters, k,
             s->lambda, s->rnorm, s->hsmall->jacobi_sweeps, s->hsmall->eig_fallbacks);

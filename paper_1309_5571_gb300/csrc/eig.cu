@@ -27,7 +27,7 @@
 namespace dmrg {
 namespace {
 
-constexpr int kEigThreads = 128;
+constexpr int kEigThreads = 256;  // >= KMAX^2 / 2: two Q items per thread suffice
 constexpr double kEps = 1.1102230246251565e-16;  // 2^-53
 
 // player at position j of step `step` of the round-robin tournament over kk (even)
@@ -62,23 +62,51 @@ __device__ __forceinline__ void rotation(T app, T aqq, T apq, T& c, T& s) {
   }
 }
 
+// Round-robin schedule of one sweep, computed once per call: pair i of step t is
+// (sp[t][i], sq[t][i]) with sp < sq; players >= k are dummies (no rotation).
+struct Schedule {
+  uint8_t sp[KMAX][KMAX / 2], sq[KMAX][KMAX / 2];
+  __device__ void build(int kk) {
+    const int half = kk / 2;
+    for (int e = threadIdx.x; e < (kk - 1) * half; e += blockDim.x) {
+      const int t = e / half, i = e - t * half;
+      int p = rr_player(i, t, kk), q = rr_player(kk - 1 - i, t, kk);
+      if (p > q) { const int w = p; p = q; q = w; }
+      sp[t][i] = (uint8_t)p;
+      sq[t][i] = (uint8_t)q;
+    }
+  }
+};
+
 // Cyclic Jacobi on A (k x k in shared memory, rows and columns k..kk-1 zero), accumulating
 // Q <- Q J.  A rotation is skipped when a_pq^2 <= rel2 |a_pp a_qq| + abs2; sweeps stop
-// after one without rotations.  Returns the number of sweeps.  All threads call it.
+// after one without rotations.  Returns the number of sweeps.  All threads call it.  Each
+// thread owns fixed work items for the whole solve (no index arithmetic per step): at
+// most one 2 x 2 block (I, J) of J^T A J and two (row, pair) items of Q J.
 template <typename T>
 __device__ int jacobi_sweeps(T (*A)[KMAX + 1], T (*Q)[KMAX + 1], int k, T rel2, T abs2,
-                             int max_sweeps, T* cs, T* sn, int* pp, int* qq, int* rotated) {
+                             int max_sweeps, const Schedule& sch, T* cs, T* sn, int* rotated) {
   const int tid = threadIdx.x;
   const int kk = (k + 1) & ~1;
   const int half = kk / 2;
+  const bool has_blk = tid < half * half;
+  const int bI = has_blk ? tid / half : 0, bJ = has_blk ? tid - (tid / half) * half : 0;
+  int qr[2], qj[2];
+  bool has_q[2];
+#pragma unroll
+  for (int u = 0; u < 2; ++u) {
+    const int e = tid + u * (int)blockDim.x;
+    has_q[u] = e < k * half;
+    qr[u] = has_q[u] ? e / half : 0;
+    qj[u] = has_q[u] ? e - (e / half) * half : 0;
+  }
   int sweep = 0;
   for (; sweep < max_sweeps && k > 1; ++sweep) {
     if (tid == 0) *rotated = 0;
     __syncthreads();
     for (int step = 0; step < kk - 1; ++step) {
       if (tid < half) {
-        int p = rr_player(tid, step, kk), q = rr_player(kk - 1 - tid, step, kk);
-        if (p > q) { const int t = p; p = q; q = t; }
+        const int p = sch.sp[step][tid], q = sch.sq[step][tid];
         T c = (T)1, s = (T)0;
         if (q < k) {
           const T apq = A[p][q], app = A[p][p], aqq = A[q][q];
@@ -87,40 +115,40 @@ __device__ int jacobi_sweeps(T (*A)[KMAX + 1], T (*Q)[KMAX + 1], int k, T rel2, 
             *rotated = 1;
           }
         }
-        pp[tid] = p;
-        qq[tid] = q;
         cs[tid] = c;
         sn[tid] = s;
       }
       __syncthreads();
       // A <- J^T A J: the 2 x 2 block (rows of pair I, columns of pair J) depends only on
-      // itself, so each thread updates its blocks in place
-      for (int e = tid; e < half * half; e += blockDim.x) {
-        const int I = e / half, J = e - (e / half) * half;
-        const T sI = sn[I], sJ = sn[J];
-        if (sI == (T)0 && sJ == (T)0) continue;
-        const int a0 = pp[I], a1 = qq[I], b0 = pp[J], b1 = qq[J];
-        const T cI = cs[I], cJ = cs[J];
-        const T x00 = A[a0][b0], x01 = A[a0][b1], x10 = A[a1][b0], x11 = A[a1][b1];
-        const T y00 = cI * x00 - sI * x10, y01 = cI * x01 - sI * x11;
-        const T y10 = sI * x00 + cI * x10, y11 = sI * x01 + cI * x11;
-        T z01 = sJ * y00 + cJ * y01, z10 = cJ * y10 - sJ * y11;
-        if (sizeof(T) == 4 && I == J) z01 = z10 = (T)0;  // the FP32 rotation annihilates a_pq
-        A[a0][b0] = cJ * y00 - sJ * y01;
-        A[a0][b1] = z01;
-        A[a1][b0] = z10;
-        A[a1][b1] = sJ * y10 + cJ * y11;
+      // itself, so each thread updates its block in place
+      if (has_blk) {
+        const T sI = sn[bI], sJ = sn[bJ];
+        if (sI != (T)0 || sJ != (T)0) {
+          const int a0 = sch.sp[step][bI], a1 = sch.sq[step][bI];
+          const int b0 = sch.sp[step][bJ], b1 = sch.sq[step][bJ];
+          const T cI = cs[bI], cJ = cs[bJ];
+          const T x00 = A[a0][b0], x01 = A[a0][b1], x10 = A[a1][b0], x11 = A[a1][b1];
+          const T y00 = cI * x00 - sI * x10, y01 = cI * x01 - sI * x11;
+          const T y10 = sI * x00 + cI * x10, y11 = sI * x01 + cI * x11;
+          T z01 = sJ * y00 + cJ * y01, z10 = cJ * y10 - sJ * y11;
+          if (sizeof(T) == 4 && bI == bJ) z01 = z10 = (T)0;  // the FP32 rotation annihilates a_pq
+          A[a0][b0] = cJ * y00 - sJ * y01;
+          A[a0][b1] = z01;
+          A[a1][b0] = z10;
+          A[a1][b1] = sJ * y10 + cJ * y11;
+        }
       }
       // Q <- Q J
-      for (int e = tid; e < k * half; e += blockDim.x) {
-        const int r = e / half, J = e - (e / half) * half;
-        const T sJ = sn[J];
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        if (!has_q[u]) continue;
+        const T sJ = sn[qj[u]];
         if (sJ == (T)0) continue;
-        const int b0 = pp[J], b1 = qq[J];
-        const T cJ = cs[J];
-        const T q0 = Q[r][b0], q1 = Q[r][b1];
-        Q[r][b0] = cJ * q0 - sJ * q1;
-        Q[r][b1] = sJ * q0 + cJ * q1;
+        const int b0 = sch.sp[step][qj[u]], b1 = sch.sq[step][qj[u]];
+        const T cJ = cs[qj[u]];
+        const T q0 = Q[qr[u]][b0], q1 = Q[qr[u]][b1];
+        Q[qr[u]][b0] = cJ * q0 - sJ * q1;
+        Q[qr[u]][b1] = sJ * q0 + cJ * q1;
       }
       __syncthreads();
     }
@@ -148,13 +176,15 @@ __global__ void __launch_bounds__(kEigThreads) small_eig_kernel(DevSmall* small,
   __shared__ double A64[KMAX][KMAX + 1];
   __shared__ double Q64[KMAX][KMAX + 1];
   __shared__ double cs64[KMAX / 2], sn64[KMAX / 2];
-  __shared__ int pp[KMAX / 2], qq[KMAX / 2];
+  __shared__ Schedule sch;
   __shared__ int rotated, best, refined_ok;
   __shared__ double yref[KMAX];
   __shared__ double lam_ref;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const long long c0 = clock64();
   const bool warm = k > 1 && small->qk == k - 1;
 
+  sch.build((k + 1) & ~1);
   // ---- B, and the FP32 start: the arrowhead in the previous eigenbasis, or B itself
   for (int e = tid; e < KMAX * KMAX; e += blockDim.x) {
     const int r = e / KMAX, c = e - (e / KMAX) * KMAX;
@@ -197,7 +227,7 @@ __global__ void __launch_bounds__(kEigThreads) small_eig_kernel(DevSmall* small,
   }
   __syncthreads();
   const float tol32 = 2e-7f * scale32;
-  int sweeps = jacobi_sweeps<float>(A32, Q32, k, 0.0f, tol32 * tol32, 30, cs32, sn32, pp, qq, &rotated);
+  int sweeps = jacobi_sweeps<float>(A32, Q32, k, 0.0f, tol32 * tol32, 30, sch, cs32, sn32, &rotated);
   if (tid == 0) {
     int b = 0;
     for (int i = 1; i < k; ++i)
@@ -206,48 +236,79 @@ __global__ void __launch_bounds__(kEigThreads) small_eig_kernel(DevSmall* small,
     refined_ok = 0;
   }
   __syncthreads();
+  const long long c1 = clock64();
 
-  // ---- 2. FP64 refinement of the lowest pair (warp 0, lane i owns row i).  B y, the
-  // Rayleigh quotient and rho are FP64; the correction U D^-1 U^T rho only has to be
-  // accurate relative to the (small) error it removes, so it runs in FP32 (no FP64
-  // conversions or FMAs in its inner loops).  y is normalised once, at the end.
+  // ---- 2. FP64 refinement of the lowest pair.  B y is split over the 8 warps (warp w adds
+  // the columns j = w, w + 8, w + 16 for row = lane; the FP64 pipe of each SM sub-partition
+  // works in parallel), the rest runs in warp 0 (lane i owns row i).  B y, the Rayleigh
+  // quotient and rho are FP64; the correction U D^-1 U^T rho only has to be accurate
+  // relative to the (small) error it removes, so it runs in FP32.  y is normalised at the end.
+  __shared__ double ysh[KMAX], wpart[kEigThreads / 32][KMAX];
+  __shared__ int ref_stop;
+  constexpr int kWarps = kEigThreads / 32;
+  static_assert(kWarps == 8, "the partial sums below combine 8 warps");
+  const int b = best;
+  const bool act = lane < k;
+  double scale = 0.0;
+  for (int i = 0; i < k; ++i) scale = fmax(scale, fabs((double)A32[i][i]));
+  scale = fmax(scale, 1e-300);
+  const double tol = 8.0 * kEps * scale * sqrt((double)k);
+  const double accept = 64.0 * kEps * scale * sqrt((double)k);
+  double y = 0.0, lam = 0.0, rel2 = INFINITY, yy = 1.0;
   if (warp == 0) {
-    const int b = best;
-    const bool act = lane < k;
-    double scale = 0.0;
-    for (int i = 0; i < k; ++i) scale = fmax(scale, fabs((double)A32[i][i]));
-    scale = fmax(scale, 1e-300);
-    const double tol = 8.0 * kEps * scale * sqrt((double)k);
-    const double accept = 64.0 * kEps * scale * sqrt((double)k);
-    const double theta = act ? (double)A32[lane][lane] : 0.0;
-    double y = act ? (double)Q32[lane][b] : 0.0;
-    double lam = 0.0, rel2 = INFINITY, yy = 1.0;
-    for (int it = 0; it < 6; ++it) {
+    y = act ? (double)Q32[lane][b] : 0.0;
+    if (act) ysh[lane] = y;
+    if (lane == 0) ref_stop = 0;
+  }
+  const double theta = act ? (double)A32[lane][lane] : 0.0;
+  for (int it = 0; it < 6; ++it) {
+    __syncthreads();  // ysh, ref_stop
+    if (ref_stop) break;
+    if (act) {
+      double part = 0.0;
+      for (int j = warp; j < k; j += kWarps) part = fma(Bs[lane][j], ysh[j], part);
+      wpart[warp][lane] = part;
+    }
+    __syncthreads();
+    if (warp == 0) {
       double w = 0.0;
-      for (int j = 0; j < k; ++j) {
-        const double yj = __shfl_sync(0xffffffffu, y, j);
-        if (act) w = fma(Bs[lane][j], yj, w);
+      if (act) {
+        double w0 = wpart[0][lane] + wpart[1][lane], w1 = wpart[2][lane] + wpart[3][lane];
+        double w2 = wpart[4][lane] + wpart[5][lane], w3 = wpart[6][lane] + wpart[7][lane];
+        w = (w0 + w1) + (w2 + w3);
       }
-      yy = warp_sum(y * y);
-      lam = warp_sum(y * w) / yy;
+      double s_yy = y * y, s_yw = y * w;  // two reductions in one shuffle tree
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        s_yy += __shfl_xor_sync(0xffffffffu, s_yy, o);
+        s_yw += __shfl_xor_sync(0xffffffffu, s_yw, o);
+      }
+      yy = s_yy;
+      lam = s_yw / yy;
       const double rho = act ? fma(-lam, y, w) : 0.0;
       rel2 = warp_sum(rho * rho) / yy;  // ||rho||^2 / ||y||^2
-      if (rel2 <= tol * tol || it == 5) break;
-      const float rf = (float)rho;
-      float c = 0.0f;
-      for (int j = 0; j < k; ++j) {
-        const float rj = __shfl_sync(0xffffffffu, rf, j);
-        if (act) c = fmaf(Q32[j][lane], rj, c);
+      if (rel2 <= tol * tol || it == 5) {
+        if (lane == 0) ref_stop = 1;
+      } else {
+        const float rf = (float)rho;
+        float c = 0.0f;
+        for (int j = 0; j < k; ++j) {
+          const float rj = __shfl_sync(0xffffffffu, rf, j);
+          if (act) c = fmaf(Q32[j][lane], rj, c);
+        }
+        const double d = theta - lam;
+        c = (!act || lane == b || fabs(d) < 1e-6 * scale) ? 0.0f : c / (float)d;
+        float dy = 0.0f;
+        for (int i = 0; i < k; ++i) {
+          const float ci = __shfl_sync(0xffffffffu, c, i);
+          if (act) dy = fmaf(Q32[lane][i], ci, dy);
+        }
+        y -= (double)dy;
+        if (act) ysh[lane] = y;
       }
-      const double d = theta - lam;
-      c = (!act || lane == b || fabs(d) < 1e-6 * scale) ? 0.0f : c / (float)d;
-      float dy = 0.0f;
-      for (int i = 0; i < k; ++i) {
-        const float ci = __shfl_sync(0xffffffffu, c, i);
-        if (act) dy = fmaf(Q32[lane][i], ci, dy);
-      }
-      y -= (double)dy;
     }
+  }
+  if (warp == 0) {
     if (act) yref[lane] = y / sqrt(yy);
     if (lane == 0) {
       lam_ref = lam;
@@ -256,11 +317,15 @@ __global__ void __launch_bounds__(kEigThreads) small_eig_kernel(DevSmall* small,
   }
   __syncthreads();
 
+  const long long c2 = clock64();
   if (refined_ok) {
     if (tid == 0) {
       small->lambda = lam_ref;
       small->jacobi_sweeps = sweeps;
       small->qk = k;
+      small->eig_cycles[0] = c1 - c0;
+      small->eig_cycles[1] = c2 - c1;
+      small->eig_cycles[2] = clock64() - c0;
     }
     for (int e = tid; e < k * k; e += blockDim.x) {
       const int r = e / k, c = e - (e / k) * k;
@@ -286,13 +351,16 @@ __global__ void __launch_bounds__(kEigThreads) small_eig_kernel(DevSmall* small,
   }
   __syncthreads();
   const double abs64 = 1e-17 * scale64;
-  sweeps += jacobi_sweeps<double>(A64, Q64, k, 1e-30, abs64 * abs64, 40, cs64, sn64, pp, qq, &rotated);
+  sweeps += jacobi_sweeps<double>(A64, Q64, k, 1e-30, abs64 * abs64, 40, sch, cs64, sn64, &rotated);
   if (tid == 0) {
     int b = 0;
     for (int i = 1; i < k; ++i)
       if (A64[i][i] < A64[b][b]) b = i;
     best = b;
     small->eig_fallbacks += 1;
+    small->eig_cycles[0] = c1 - c0;
+    small->eig_cycles[1] = c2 - c1;
+    small->eig_cycles[2] = clock64() - c0;
     small->lambda = A64[b][b];
     small->jacobi_sweeps = sweeps;
     small->qk = k;

@@ -139,6 +139,7 @@ constexpr int kThreads = 192;
 constexpr int kTmemCols = 256;             // two 128-column FP32 accumulators
 
 #include "tc_ptx.cuh"
+#include "cvt.cuh"
 
 // ---------------------------------------------------------------- packing kernel
 // One CTA packs one image tile (128 rows x 128 bytes x planes) of one pack job from FP64.
@@ -168,7 +169,8 @@ pack_kernel(const PackChunk* __restrict__ chunks, const PackJob* __restrict__ jo
     const int64_t grow = (int64_t)ch.rt * kRows + r;
     const int k0 = ch.kt * KT + g * EPG;
     // operands are rounded to FP32 first (one conversion, no further FP64 arithmetic:
-    // FP64 throughput is low on this part); the three BF16 terms of an FP32 value
+    // FP64 throughput is low on this part, and so is the hardware conversion, so the
+    // rounding is done with integer operations); the three BF16 terms of an FP32 value
     // represent it exactly
     const bool scaled = jb.scale != 1.0;
     float v[EPG];
@@ -177,7 +179,7 @@ pack_kernel(const PackChunk* __restrict__ chunks, const PackJob* __restrict__ jo
       const int k = k0 + e;
       double a = 0.0;
       if (grow < jb.R && k < jb.K) a = src[grow * jb.rs + (int64_t)k * jb.cs];
-      v[e] = (float)(scaled ? jb.scale * a : a);
+      v[e] = scaled ? (float)(jb.scale * a) : f64_to_f32_rn(a);
     }
     const uint32_t off = swz(r, g);
     if constexpr (TF32) {
@@ -401,7 +403,7 @@ tc_gemm_kernel(const TcTile* __restrict__ tiles, int ntiles, const TcJob* __rest
             for (int j = 0; j < 32; ++j) {
               const int n = n0 + j;
               if (n < job.N) {
-                double val = (double)__uint_as_float(v[j]);
+                double val = f32_to_f64(__uint_as_float(v[j]));  // exact, integer ops
                 if (job.axpy != 0.0) val = fma(job.axpy, xr[n], val);
                 yr[n] = val;
               }

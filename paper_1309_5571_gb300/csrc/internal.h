@@ -185,6 +185,8 @@ struct DevSmall {
   double theta[KMAX];     // its eigenvalues
   int32_t qk;             // order of the stored decomposition (0: none)
   int32_t eig_fallbacks;  // small eigenproblems that needed the FP64 Jacobi fallback
+  int64_t eig_cycles[3];  // last small eigenproblem: SM clock cycles of setup + FP32
+                          // Jacobi, of the FP64 refinement, and in total (diagnostics)
 };
 
 struct VecWork {
