@@ -138,6 +138,9 @@ typedef struct {
   double tol;            /* stop when ||H x - lambda x||_2 <= tol, ||x|| = 1 (1e-10)      */
   int32_t max_iter;      /* Davidson iterations before DMRG_ERR_NOT_CONVERGED (1000)      */
   int32_t max_subspace;  /* basis size that triggers a restart, <= 24 (20, Sec. 6.1)     */
+  int32_t restart_keep;  /* vectors kept at a subspace-limit restart: 1 (the Ritz vector)
+                            or 2 (also the previous iteration's Ritz vector, orthonormalised
+                            against it; default); FP64 anchors of the mixed modes keep 1  */
   int32_t fp64_refine;   /* low-precision modes: re-anchor with FP64 projections (1)      */
   double refine_ratio;   /* if > 0, also re-anchor when the low-precision residual has
                             fallen by this factor below the last FP64 residual (0: only

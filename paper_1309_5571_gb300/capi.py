@@ -63,7 +63,7 @@ class SuperblockDesc(C.Structure):
 
 class Options(C.Structure):
     _fields_ = [("prec", C.c_int32), ("tol", C.c_double), ("max_iter", C.c_int32),
-                ("max_subspace", C.c_int32), ("fp64_refine", C.c_int32),
+                ("max_subspace", C.c_int32), ("restart_keep", C.c_int32), ("fp64_refine", C.c_int32),
                 ("refine_ratio", C.c_double), ("anchor_prec", C.c_int32),
                 ("vector_arith", C.c_int32), ("autotune", C.c_int32)]
 
@@ -217,7 +217,7 @@ def marshal(sb) -> _Marshalled:
     return _Marshalled(desc, keep)
 
 
-def options(prec="fp64", tol=1e-10, max_iter=1000, max_subspace=20, fp64_refine=True,
+def options(prec="fp64", tol=1e-10, max_iter=1000, max_subspace=20, restart_keep=2, fp64_refine=True,
             refine_ratio=0.0, anchor_prec="fp64", vector_arith="split", autotune=True) -> Options:
     o = Options()
     load().dmrg_options_default(C.byref(o))
@@ -225,6 +225,7 @@ def options(prec="fp64", tol=1e-10, max_iter=1000, max_subspace=20, fp64_refine=
     o.tol = tol
     o.max_iter = max_iter
     o.max_subspace = max_subspace
+    o.restart_keep = restart_keep
     o.fp64_refine = int(bool(fp64_refine))
     o.refine_ratio = refine_ratio
     o.anchor_prec = PREC[anchor_prec] if isinstance(anchor_prec, str) else int(anchor_prec)

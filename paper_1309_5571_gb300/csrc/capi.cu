@@ -30,6 +30,7 @@ void dmrg_options_default(dmrg_options* opt) {
   opt->tol = 1e-10;
   opt->max_iter = 1000;
   opt->max_subspace = 20;
+  opt->restart_keep = 2;
   opt->fp64_refine = 1;
   opt->refine_ratio = 0.0;
   opt->anchor_prec = DMRG_PREC_FP64;

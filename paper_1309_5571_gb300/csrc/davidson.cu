@@ -45,6 +45,8 @@ struct dmrg_davidson_state {
   double* D = nullptr;     // padded diag(H_SB)
   double* xbuf = nullptr;  // Ritz vector at a restart
   double* wbuf = nullptr;  // W y at a restart
+  double* pbuf = nullptr;  // second kept vector of a two-vector restart
+  double* wpbuf = nullptr; // its W combination
   DevSmall* small = nullptr;
   DevSmall* hsmall = nullptr;  // pinned mirror
   VecWork vw;
@@ -178,11 +180,13 @@ dmrg_status dmrg_state_create(dmrg_plan* plan, const double* x0, void* stream,
       cudaMalloc((void**)&s->D, col) != cudaSuccess ||
       cudaMalloc((void**)&s->xbuf, col) != cudaSuccess ||
       cudaMalloc((void**)&s->wbuf, col) != cudaSuccess ||
+      (plan->opt.restart_keep == 2 && (cudaMalloc((void**)&s->pbuf, col) != cudaSuccess ||
+                                       cudaMalloc((void**)&s->wpbuf, col) != cudaSuccess)) ||
       cudaMalloc((void**)&s->small, sizeof(DevSmall)) != cudaSuccess ||
       cudaMallocHost((void**)&s->hsmall, sizeof(DevSmall)) != cudaSuccess) {
     cudaGetLastError();
     set_error("allocation of the Davidson workspace (%zu bytes) failed",
-              col * (2 * s->kmax + 4));
+              col * (2 * s->kmax + 6));
     return fail(DMRG_ERR_OOM);
   }
   dmrg_status e = vec_work_create(&s->vw);
@@ -216,6 +220,8 @@ void dmrg_state_destroy(dmrg_davidson_state* s) {
   cudaFree(s->D);
   cudaFree(s->xbuf);
   cudaFree(s->wbuf);
+  cudaFree(s->pbuf);
+  cudaFree(s->wpbuf);
   cudaFree(s->small);
   cudaFreeHost(s->hsmall);
   vec_work_destroy(&s->vw);
@@ -353,7 +359,56 @@ dmrg_status phase_b(dmrg_davidson_state* s, cudaStream_t st, bool* need_c) {
     return DMRG_OK;
   }
   int knew = k;
-  if (do_restart) {
+  // two-vector restart (restart_keep = 2): keep x and the previous iteration's Ritz vector,
+  // orthogonalised against x in coefficient space (c2 = y_prev - y (y . y_prev), twice)
+  double c2[KMAX] = {0.0};
+  bool keep2 = false;
+  if (do_restart && s->plan->opt.restart_keep == 2 && k >= 2) {
+    const DevSmall& h = *s->hsmall;
+    for (int j = 0; j < k - 1; ++j) c2[j] = h.y_prev[j];
+    for (int pass = 0; pass < 2; ++pass) {
+      double a = 0.0;
+      for (int j = 0; j < k; ++j) a += h.y[j] * c2[j];
+      for (int j = 0; j < k; ++j) c2[j] -= a * h.y[j];
+    }
+    double nrm = 0.0;
+    for (int j = 0; j < k; ++j) nrm += c2[j] * c2[j];
+    nrm = std::sqrt(nrm);
+    if (nrm > 1e-8) {
+      keep2 = true;
+      for (int j = 0; j < k; ++j) c2[j] /= nrm;
+    }
+  }
+  if (keep2) {
+    // V = [x, p], W = [W y, W c2]; B(0,0) = lambda here, B(:,1) from an overlap after p is
+    // re-orthonormalised against x in FP64 (the low-precision columns of the old basis are
+    // orthonormal only to FP32 in the split arithmetic); the correction t is kept
+    DevSmall& h = *s->hsmall;
+    for (int j = 0; j < KMAX; ++j) {
+      h.C[0][j] = j < k ? h.y[j] : 0.0;
+      h.C[1][j] = j < k ? c2[j] : 0.0;
+    }
+    for (int j = 0; j < KMAX * KMAX; ++j) h.B[j] = 0.0;
+    h.B[0] = s->lambda;
+    for (int j = 0; j < KMAX; ++j) h.y[j] = j == 0 ? 1.0 : 0.0;
+    h.qk = 0;  // the next small eigenproblem starts cold
+    DMRG_CUDA_TRY(cudaMemcpyAsync(s->small, s->hsmall, sizeof(DevSmall), cudaMemcpyHostToDevice, st));
+    DMRG_TRY(launch_ritz2(s->V, s->W, ldv, n, k, s->small, s->xbuf, s->pbuf, s->wbuf, s->wpbuf, st));
+    const size_t bytes = sizeof(double) * n;
+    DMRG_CUDA_TRY(cudaMemcpyAsync(s->V, s->xbuf, bytes, cudaMemcpyDeviceToDevice, st));
+    DMRG_CUDA_TRY(cudaMemcpyAsync(s->V + ldv, s->pbuf, bytes, cudaMemcpyDeviceToDevice, st));
+    DMRG_CUDA_TRY(cudaMemcpyAsync(s->W, s->wbuf, bytes, cudaMemcpyDeviceToDevice, st));
+    DMRG_CUDA_TRY(cudaMemcpyAsync(s->W + ldv, s->wpbuf, bytes, cudaMemcpyDeviceToDevice, st));
+    DMRG_TRY(launch_orth_pair(s->vw, s->V + ldv, s->W + ldv, s->V, s->W, n, s->small, st));
+    const double* w0 = (s->mixed && s->anchored) ? s->W : nullptr;
+    DMRG_TRY(ov(s, 2, s->W + ldv, nullptr, 1, st, w0));
+    knew = 2;
+    s->restarts++;
+    s->plain_restarts++;
+    s->baked_err += s->cur_err;
+    s->ritz_k = 0;
+    DMRG_TRY(ov(s, knew, tcol, s->small->s[0], -1, st));
+  } else if (do_restart) {
     // V = [x], W = [W y], B = [lambda]; the correction t (column k) is kept
     DMRG_TRY(launch_ritz(s->V, s->W, ldv, n, k, s->small, s->xbuf, s->wbuf, st));
     DMRG_CUDA_TRY(cudaMemcpyAsync(s->V, s->xbuf, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
@@ -367,7 +422,7 @@ dmrg_status phase_b(dmrg_davidson_state* s, cudaStream_t st, bool* need_c) {
     DMRG_TRY(ov(s, knew, tcol, s->small->s[0], -1, st));
   }
   s->knew = knew;
-  s->did_restart = do_restart;
+  s->did_restart = do_restart;  // (after a restart y = e_1 in the new basis)
   // classical Gram-Schmidt (second pass only when needed), then normalise
   DMRG_CUDA_TRY(cudaMemsetAsync(&s->small->flags, 0, sizeof(int32_t), st));
   DMRG_TRY(cgs(s, knew, tcol, 0, 1, 0, st));

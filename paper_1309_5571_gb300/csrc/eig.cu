@@ -184,6 +184,9 @@ __global__ void __launch_bounds__(kEigThreads) small_eig_kernel(DevSmall* small,
   const long long c0 = clock64();
   const bool warm = k > 1 && small->qk == k - 1;
 
+  // the previous call's eigenvector (restarts keep the previous Ritz vector); thread tid
+  // also writes y[tid] at the end, after this read
+  if (tid < KMAX) small->y_prev[tid] = small->y[tid];
   sch.build((k + 1) & ~1);
   // ---- B, and the FP32 start: the arrowhead in the previous eigenbasis, or B itself
   for (int e = tid; e < KMAX * KMAX; e += blockDim.x) {

@@ -187,6 +187,8 @@ struct DevSmall {
   int32_t eig_fallbacks;  // small eigenproblems that needed the FP64 Jacobi fallback
   int64_t eig_cycles[3];  // last small eigenproblem: SM clock cycles of setup + FP32
                           // Jacobi, of the FP64 refinement, and in total (diagnostics)
+  double y_prev[KMAX];    // lowest eigenvector of the previous small eigenproblem
+  double C[2][KMAX];      // restart coefficients: new basis = [V C0, V C1]
 };
 
 struct VecWork {
@@ -223,6 +225,13 @@ dmrg_status launch_ritz(const double* V, const double* W, int64_t ldv, int64_t n
 dmrg_status launch_normalize(const VecWork& w, const double* src, double* dst, int64_t n,
                              DevSmall* small, cudaStream_t st);
 dmrg_status launch_set_B00(DevSmall* small, cudaStream_t st);
+// two-vector restart: x = V C0, p = V C1, wx = W C0, wp = W C1 (n elements each)
+dmrg_status launch_ritz2(const double* V, const double* W, int64_t ldv, int64_t n, int k,
+                         const DevSmall* small, double* x, double* p, double* wx, double* wp,
+                         cudaStream_t st);
+// p -= a x and wp -= a wx with a = small->s[2][0], then p and wp scaled by 1 / ||p||
+dmrg_status launch_orth_pair(const VecWork& w, double* p, double* wp, const double* x,
+                             const double* wx, int64_t n, DevSmall* small, cudaStream_t st);
 // vec_df.cu -- the same passes in double-float (FP32 pair) arithmetic
 dmrg_status launch_overlap_df(const VecWork& w, const double* V, int64_t ldv, int64_t n, int k,
                               const double* vec, double* s_out, DevSmall* small, int Bcol,

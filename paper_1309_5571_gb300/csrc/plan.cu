@@ -428,7 +428,8 @@ dmrg_status dmrg_plan_create(const dmrg_superblock_desc* desc, const dmrg_option
       (int)p->opt.prec < 0 || (int)p->opt.prec > 3 ||
       (p->opt.anchor_prec != DMRG_PREC_FP64 && p->opt.anchor_prec != DMRG_PREC_FP64_TC) ||
       p->opt.vector_arith < DMRG_VEC_FP64 || p->opt.vector_arith > DMRG_VEC_SPLIT ||
-      (p->opt.autotune != 0 && p->opt.autotune != 1)) {
+      (p->opt.autotune != 0 && p->opt.autotune != 1) ||
+      (p->opt.restart_keep != 1 && p->opt.restart_keep != 2)) {
     set_error("options out of range (max_subspace must be in [2, %d])", DMRG_MAX_SUBSPACE);
     delete p;
     return DMRG_ERR_INVALID_ARG;

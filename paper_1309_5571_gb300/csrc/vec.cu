@@ -302,6 +302,55 @@ __global__ void ritz_kernel(const double* __restrict__ V, const double* __restri
   }
 }
 
+// ---------------------------------------------------------------- two-vector restart
+__global__ void ritz2_kernel(const double* __restrict__ V, const double* __restrict__ W,
+                             int64_t ldv, int64_t n, int k, const DevSmall* small,
+                             double* __restrict__ x, double* __restrict__ p,
+                             double* __restrict__ wx, double* __restrict__ wp) {
+  __shared__ double c0[KMAX], c1[KMAX];
+  if (threadIdx.x < KMAX) {
+    c0[threadIdx.x] = threadIdx.x < k ? small->C[0][threadIdx.x] : 0.0;
+    c1[threadIdx.x] = threadIdx.x < k ? small->C[1][threadIdx.x] : 0.0;
+  }
+  __syncthreads();
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    double a = 0.0, b = 0.0, c = 0.0, d = 0.0;
+    for (int j = 0; j < k; ++j) {
+      const double v = V[j * ldv + e], w = W[j * ldv + e];
+      a = fma(c0[j], v, a);
+      b = fma(c1[j], v, b);
+      c = fma(c0[j], w, c);
+      d = fma(c1[j], w, d);
+    }
+    x[e] = a;
+    p[e] = b;
+    wx[e] = c;
+    wp[e] = d;
+  }
+}
+
+__global__ void axpy_pair_kernel(double* __restrict__ p, double* __restrict__ wp,
+                                 const double* __restrict__ x, const double* __restrict__ wx,
+                                 int64_t n, const DevSmall* small) {
+  const double a = small->s[2][0];
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    p[e] = fma(-a, x[e], p[e]);
+    wp[e] = fma(-a, wx[e], wp[e]);
+  }
+}
+
+__global__ void scale_pair_kernel(double* __restrict__ p, double* __restrict__ wp, int64_t n,
+                                  const DevSmall* small) {
+  const double inv = 1.0 / sqrt(small->nrm2);
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    p[e] *= inv;
+    wp[e] *= inv;
+  }
+}
+
 // ---------------------------------------------------------------- normalise a vector
 __global__ void __launch_bounds__(kVecThreads)
 sumsq_kernel(const double* __restrict__ src, int64_t n, double* __restrict__ partials,
@@ -414,6 +463,27 @@ dmrg_status launch_normalize(const VecWork& w, const double* src, double* dst, i
   sumsq_kernel<<<w.grid, kVecThreads, 0, st>>>(src, n, w.partials, w.counter, small);
   DMRG_LAUNCH_CHECK();
   scale_copy_kernel<<<w.grid, kVecThreads, 0, st>>>(src, dst, n, small);
+  DMRG_LAUNCH_CHECK();
+  return DMRG_OK;
+}
+
+dmrg_status launch_ritz2(const double* V, const double* W, int64_t ldv, int64_t n, int k,
+                         const DevSmall* small, double* x, double* p, double* wx, double* wp,
+                         cudaStream_t st) {
+  ritz2_kernel<<<vec_grid(), kVecThreads, 0, st>>>(V, W, ldv, n, k, small, x, p, wx, wp);
+  DMRG_LAUNCH_CHECK();
+  return DMRG_OK;
+}
+
+dmrg_status launch_orth_pair(const VecWork& w, double* p, double* wp, const double* x,
+                             const double* wx, int64_t n, DevSmall* small, cudaStream_t st) {
+  // a = x . p (one-column overlap, FP64), p -= a x, ||p||, scale
+  DMRG_TRY(launch_overlap(w, x, n, n, 1, p, small->s[2], small, -1, st));
+  axpy_pair_kernel<<<vec_grid(), kVecThreads, 0, st>>>(p, wp, x, wx, n, small);
+  DMRG_LAUNCH_CHECK();
+  sumsq_kernel<<<w.grid, kVecThreads, 0, st>>>(p, n, w.partials, w.counter, small);
+  DMRG_LAUNCH_CHECK();
+  scale_pair_kernel<<<vec_grid(), kVecThreads, 0, st>>>(p, wp, n, small);
   DMRG_LAUNCH_CHECK();
   return DMRG_OK;
 }

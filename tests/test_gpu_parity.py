@@ -112,18 +112,20 @@ def test_gemv_trans_matches_numpy(n, k):
     np.testing.assert_allclose(s, ref, rtol=1e-12, atol=1e-12 * max(1.0, np.abs(V).max() * n))
 
 
-@pytest.mark.parametrize("name,max_subspace", [("heis_L16_m64", 20), ("hub_L8_m40", 20),
-                                               ("hub_quarter_L12_m48", 20),
-                                               ("heis_L16_m64", 4), ("ragged", 20),
-                                               ("heis_L6_exact", 20)])
-def test_davidson_fp64_matches_oracle(name, max_subspace):
+@pytest.mark.parametrize("name,max_subspace,keep", [("heis_L16_m64", 20, 2), ("hub_L8_m40", 20, 2),
+                                                    ("hub_quarter_L12_m48", 20, 2),
+                                                    ("heis_L16_m64", 4, 2), ("heis_L16_m64", 4, 1),
+                                                    ("hub_L8_m40", 8, 1), ("hub_L8_m40", 8, 2),
+                                                    ("ragged", 20, 2), ("heis_L6_exact", 20, 2)])
+def test_davidson_fp64_matches_oracle(name, max_subspace, keep):
+    # keep: vectors kept at a subspace-limit restart (the Ritz vector; or also the previous one)
     sb = problem(name)
     x0 = warmup.start_vector(sb.n, seed=0)
-    plan = Plan(sb, prec="fp64", max_subspace=max_subspace)
+    plan = Plan(sb, prec="fp64", max_subspace=max_subspace, restart_keep=keep)
     x, info = plan.solve(cuda(x0))
     x = x.cpu().numpy()
     lam, xo, oinfo = odav.davidson(lambda v: oproj.project_blocks(sb, v), oproj.diagonal(sb),
-                                   x0, max_subspace=max_subspace)
+                                   x0, max_subspace=max_subspace, restart_keep=keep)
     assert oinfo["converged"] and info["converged"]
     assert abs(info["energy"] - lam) <= E_TOL
     assert abs(x @ xo) / (np.linalg.norm(x) * np.linalg.norm(xo)) >= 1 - 1e-8
