@@ -82,6 +82,7 @@ typedef enum {
 enum { DMRG_HOST_DATA = 0, DMRG_DEVICE_DATA = 1 };
 enum { DMRG_IDENTITY_OP = -1 };
 enum { DMRG_MAX_SUBSPACE = 24 };
+enum { DMRG_TILE_SCHEDULES = 9 };  /* candidate tile schedules per tensor-core GEMM stage */
 
 /* One dense block A_{q_in -> q_out} of an operator (Sec. 4.1, around Eq. 11). */
 typedef struct {
@@ -175,12 +176,15 @@ typedef struct {
                                identity factors only)                                      */
   int64_t tiles_stage1, tiles_stage2;
   int64_t device_bytes;     /* device memory owned by the plan                            */
-  int32_t tc_schedule[2];   /* tile schedule of tensor-core GEMM stages 1 and 2 (0: jobs in
-                               descending cost; 1: stage 1 grouped by vector segment, stage
-                               2 by right sector; 2: stage 1 grouped by operator block,
-                               stage 2 by left sector); -1 before a TF32/BF16X3 plan exists */
-  float tc_tune_us[2][3];   /* autotuner: median time of each schedule per stage (us), 0 if
-                               not tuned                                                   */
+  int32_t tc_schedule[2];   /* tile schedule of tensor-core GEMM stages 1 and 2, 3 w + o:
+                               order o (0: jobs in descending cost; 1: stage 1 grouped by
+                               vector segment, stage 2 by right sector; 2: stage 1 grouped
+                               by operator block, stage 2 by left sector) and BF16x3 tile
+                               width w (0: 128 columns; 1: 256 columns for tiles below half
+                               the mean work per SM; 2: 256 wherever possible); -1 before a
+                               TF32/BF16X3 plan exists                                      */
+  float tc_tune_us[2][DMRG_TILE_SCHEDULES]; /* autotuner: median time of each schedule per
+                               stage (us), 0 if not tuned or not a candidate               */
 } dmrg_plan_stats;
 
 typedef struct dmrg_plan dmrg_plan;

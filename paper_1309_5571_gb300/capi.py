@@ -82,7 +82,7 @@ class PlanStats(C.Structure):
     _fields_ = [("n", C.c_int64), ("records", C.c_int64), ("flops", C.c_int64),
                 ("tiles_stage1", C.c_int64), ("tiles_stage2", C.c_int64),
                 ("device_bytes", C.c_int64), ("tc_schedule", C.c_int32 * 2),
-                ("tc_tune_us", (C.c_float * 3) * 2)]
+                ("tc_tune_us", (C.c_float * 9) * 2)]
 
     def as_dict(self):
         d = {f: getattr(self, f) for f, _ in self._fields_[:6]}

@@ -62,7 +62,8 @@ struct TcJob {
 };
 
 struct TcTile {
-  int32_t job, mt, nt, pad_;
+  int32_t job, mt, nt, pad_;  // pad_: problem index in a grouped launch
+  int32_t wide;               // 1: 256 output columns (row tiles nt and nt + 1 of B)
 };
 
 struct PackJob {
@@ -93,21 +94,31 @@ struct TcPtrs {
   int32_t active, pad_;
 };
 
-// Tile schedules (the order in which the persistent CTAs take the output tiles; CTA b takes
-// tiles b, b + grid, ...).  Every schedule covers the same tiles, so the results are
-// identical; only the operand reuse in L2 and the load balance differ.
+// Tile schedules: the tile shapes and the order in which the persistent CTAs take the
+// output tiles (CTA b takes tiles b, b + grid, ...).  Schedule c = 3 w + o combines
+// order o:
 //   0  jobs in descending cost (longest first), tiles row-major within a job
 //   1  stage 1: jobs grouped by the vector image they read (all records of one (i, k)
 //      segment and form together), tiles column-major; stage 2: output segments grouped
 //      by their right sector l
 //   2  stage 1: jobs grouped by the operator block image they read, tiles row-major;
 //      stage 2: output segments grouped by their left sector j
-// Groups are taken in descending total cost, jobs within a group in descending cost.
-constexpr int kSchedules = 3;
+// (groups in descending total cost, jobs within a group in descending cost) with tile
+// width policy w (BF16x3 only; TF32 tiles are always 128 x 128):
+//   0  all tiles 128 columns
+//   1  256 columns where the job has two B row tiles left and the tile's work stays below
+//      half of the mean work per SM (wide tiles halve the B-operand traffic per FLOP, but
+//      a long wide tile can become the critical path of the stage)
+//   2  256 columns wherever possible
+// Every schedule computes each output element with the same arithmetic, so the results
+// are identical; operand reuse, load balance and time differ.
+constexpr int kOrders = 3, kWidths = 3;
+constexpr int kSchedules = kOrders * kWidths;
 
 struct TcPlan {
   dmrg_precision prec = DMRG_PREC_BF16X3;
-  int planes = 3, kt_elems = 64;
+  int planes = 3, kt_elems = 32;
+  int64_t chunk = 0;  // bytes of one plane of one image tile
   uint8_t* buf[4] = {nullptr, nullptr, nullptr, nullptr};
   size_t buf_bytes[4] = {0, 0, 0, 0};
   PackJob* d_xpack_jobs = nullptr;
@@ -118,7 +129,9 @@ struct TcPlan {
   // candidate tile schedules of each stage (kSchedules, see build_tc); the kernels run
   // schedule sched[stage]
   TcTile* d_tiles[2][kSchedules] = {};
-  int64_t ntiles1 = 0, ntiles2 = 0;
+  int64_t ntiles[2][kSchedules] = {};
+  int nsched = kSchedules;  // TF32: the narrow schedules only
+  int64_t ntiles1 = 0, ntiles2 = 0;  // tiles of schedule 0 (all narrow)
   int sched[2] = {0, 0};
   bool tuned = false;
   float tune_us[2][kSchedules] = {};
@@ -136,10 +149,42 @@ struct TcPlan {
 namespace tc {
 
 constexpr int kThreads = 192;
-constexpr int kTmemCols = 256;             // two 128-column FP32 accumulators
 
 #include "tc_ptx.cuh"
 #include "cvt.cuh"
+
+// Operand image layout.  An image tile is 128 rows x one K-tile of 32 elements, K-major:
+//   BF16x3 planes: 64-byte rows, 64-byte swizzle (8-row atoms of 512 bytes; the 16-byte
+//                  group g of row r sits at group g ^ ((r >> 1) & 3) of its row), 8 KB
+//   TF32:          128-byte rows, 128-byte swizzle (1024-byte atoms, g ^ (r & 7)), 16 KB
+// so that a pipeline stage of BF16x3 (three planes of A and of B) is 48 KB and four stages
+// fit in shared memory.
+template <bool TF32>
+struct Layout {
+  static constexpr int ROWB = TF32 ? 128 : 64;  // bytes per image row
+  static constexpr int GROUPS = ROWB / 16;      // 16-byte groups per row
+  static constexpr int KT = 32;                 // elements per K-tile
+  static constexpr int CHUNK = kRows * ROWB;    // bytes of one plane of one image tile
+  __host__ __device__ static uint32_t off(int r, int g) {
+    if constexpr (TF32) return swz(r, g);
+    else return (uint32_t)((r >> 3) * 512 + (r & 7) * 64 + ((g ^ ((r >> 1) & 3)) << 4));
+  }
+  // shared-memory matrix descriptor of a K-major operand in this layout (descriptor
+  // version 1; stride byte offset = distance between 8-row atoms)
+  __device__ static uint64_t desc(uint32_t addr) {
+    if constexpr (TF32) {
+      return smem_desc(addr);
+    } else {
+      uint64_t d = 0;
+      d |= (uint64_t)((addr & 0x3FFFFu) >> 4);
+      d |= (uint64_t)(16u >> 4) << 16;
+      d |= (uint64_t)(512u >> 4) << 32;
+      d |= (uint64_t)1 << 46;
+      d |= (uint64_t)4 << 61;  // 64-byte swizzle
+      return d;
+    }
+  }
+};
 
 // ---------------------------------------------------------------- packing kernel
 // One CTA packs one image tile (128 rows x 128 bytes x planes) of one pack job from FP64.
@@ -148,8 +193,9 @@ __global__ void __launch_bounds__(256)
 pack_kernel(const PackChunk* __restrict__ chunks, const PackJob* __restrict__ jobs,
             const double* __restrict__ arena, const double* __restrict__ x,
             uint8_t* __restrict__ dst, const TcPtrs* __restrict__ ptrs) {
+  using L = Layout<TF32>;
   constexpr int EPG = TF32 ? 4 : 8;  // elements per 16-byte group
-  constexpr int KT = TF32 ? 32 : 64;
+  constexpr int KT = L::KT;
   const PackChunk ch = chunks[blockIdx.x];
   if (ptrs) {  // grouped launch: the chunk's problem
     const TcPtrs& pt = ptrs[ch.pad_];
@@ -160,11 +206,11 @@ pack_kernel(const PackChunk* __restrict__ chunks, const PackJob* __restrict__ jo
   }
   const PackJob jb = jobs[ch.job];
   const double* src = (jb.src_space ? x : arena) + jb.src_off;
-  uint8_t* base = dst + jb.dst_off + ((int64_t)ch.rt * jb.nkt + ch.kt) * PLANES * kChunk;
+  uint8_t* base = dst + jb.dst_off + ((int64_t)ch.rt * jb.nkt + ch.kt) * PLANES * L::CHUNK;
   const bool kfast = jb.cs == 1;
-  for (int idx = threadIdx.x; idx < kRows * 8; idx += blockDim.x) {
+  for (int idx = threadIdx.x; idx < kRows * L::GROUPS; idx += blockDim.x) {
     int r, g;
-    if (kfast) { g = idx & 7; r = idx >> 3; }
+    if (kfast) { g = idx % L::GROUPS; r = idx / L::GROUPS; }
     else { r = idx & (kRows - 1); g = idx >> 7; }
     const int64_t grow = (int64_t)ch.rt * kRows + r;
     const int k0 = ch.kt * KT + g * EPG;
@@ -181,7 +227,7 @@ pack_kernel(const PackChunk* __restrict__ chunks, const PackJob* __restrict__ jo
       if (grow < jb.R && k < jb.K) a = src[grow * jb.rs + (int64_t)k * jb.cs];
       v[e] = scaled ? (float)(jb.scale * a) : f64_to_f32_rn(a);
     }
-    const uint32_t off = swz(r, g);
+    const uint32_t off = L::off(r, g);
     if constexpr (TF32) {
       uint4 q;
       q.x = __float_as_uint(to_tf32(v[0]));
@@ -209,14 +255,17 @@ pack_kernel(const PackChunk* __restrict__ chunks, const PackJob* __restrict__ jo
         q.y = pack2_bf16(h[p][2], h[p][3]);
         q.z = pack2_bf16(h[p][4], h[p][5]);
         q.w = pack2_bf16(h[p][6], h[p][7]);
-        *reinterpret_cast<uint4*>(base + p * kChunk + off) = q;
+        *reinterpret_cast<uint4*>(base + p * L::CHUNK + off) = q;
       }
     }
   }
 }
 
 // ---------------------------------------------------------------- grouped GEMM kernel
-template <int PLANES, int STAGES, bool TF32>
+// WIDE: tiles may be 256 columns wide (N = 256 MMA, B operand = two 128-row image tiles,
+// each plane of B in a 2 x CHUNK slot so that its 256 rows are contiguous; TMEM holds two
+// 256-column accumulators).  Otherwise every tile is 128 x 128.
+template <int PLANES, int STAGES, bool TF32, bool WIDE>
 __global__ void __launch_bounds__(kThreads, 1)
 tc_gemm_kernel(const TcTile* __restrict__ tiles, int ntiles, const TcJob* __restrict__ jobs,
                const TcSeg* __restrict__ segs, const uint8_t* __restrict__ b0,
@@ -224,9 +273,13 @@ tc_gemm_kernel(const TcTile* __restrict__ tiles, int ntiles, const TcJob* __rest
                const uint8_t* __restrict__ b3, uint8_t* __restrict__ out_img,
                double* __restrict__ y, const double* __restrict__ x, int* __restrict__ gerr,
                const TcPtrs* __restrict__ ptrs, int gemm_stage) {
-  constexpr uint32_t kStageA = PLANES * kChunk;
-  constexpr uint32_t kStage = 2 * kStageA;
-  constexpr int KT = TF32 ? 32 : 64;
+  using L = Layout<TF32>;
+  constexpr uint32_t kStageA = PLANES * L::CHUNK;             // A operand of one stage
+  constexpr uint32_t kSlotB = (WIDE ? 2 : 1) * L::CHUNK;      // one plane of B
+  constexpr uint32_t kStage = kStageA + PLANES * kSlotB;
+  constexpr int kAccCols = WIDE ? 256 : 128;                  // columns of one accumulator
+  constexpr uint32_t kTmemCols = 2 * kAccCols;
+  constexpr int KT = L::KT;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
@@ -285,13 +338,26 @@ tc_gemm_kernel(const TcTile* __restrict__ tiles, int ntiles, const TcJob* __rest
           const TcSeg sg = segs[si];
           const uint8_t* P = bufs[sg.p_buf] + sg.p_off + (int64_t)tile.mt * sg.p_nkt * kStageA;
           const uint8_t* Q = bufs[sg.q_buf] + sg.q_off + (int64_t)tile.nt * sg.q_nkt * kStageA;
+          const bool wide = WIDE && tile.wide;
           for (int kt = 0; kt < sg.nkt; ++kt) {
             if (!mbar_wait(smem_u32(&empty_bar[stage]), phase ^ 1, &abort_flag, gerr, 1)) break;
             const uint32_t sa = smem_u32(smem + stage * kStage);
             const uint32_t fb = smem_u32(&full_bar[stage]);
-            mbar_expect_tx(fb, kStage);
+            const uint8_t* q0 = Q + (int64_t)kt * kStageA;
+            mbar_expect_tx(fb, kStageA + (wide ? 2u : 1u) * PLANES * L::CHUNK);
             bulk_g2s(sa, P + (int64_t)kt * kStageA, kStageA, fb);
-            bulk_g2s(sa + kStageA, Q + (int64_t)kt * kStageA, kStageA, fb);
+            if constexpr (WIDE) {
+              // plane p of B rows 0-127 (and 128-255) into the slot of plane p
+#pragma unroll
+              for (int pl = 0; pl < PLANES; ++pl) {
+                bulk_g2s(sa + kStageA + pl * kSlotB, q0 + pl * L::CHUNK, L::CHUNK, fb);
+                if (wide)
+                  bulk_g2s(sa + kStageA + pl * kSlotB + L::CHUNK,
+                           q0 + (int64_t)sg.q_nkt * kStageA + pl * L::CHUNK, L::CHUNK, fb);
+              }
+            } else {
+              bulk_g2s(sa + kStageA, q0, kStageA, fb);
+            }
             ++issued;
             if (++stage == STAGES) { stage = 0; phase ^= 1; }
           }
@@ -316,14 +382,16 @@ tc_gemm_kernel(const TcTile* __restrict__ tiles, int ntiles, const TcJob* __rest
       int acc = 0;
       uint32_t acc_phase = 0;
       bool any = false;
-      constexpr uint32_t idesc = instr_desc<TF32>();
+      constexpr uint32_t idesc128 = instr_desc<TF32, 128>();
+      constexpr uint32_t idesc256 = instr_desc<TF32, 256>();
       for (int t = blockIdx.x; t < ntiles && !abort_flag; t += gridDim.x) {
         if (!active(tiles[t])) continue;
         const TcJob job = jobs[tiles[t].job];
         if (job.seg_begin == job.seg_end) continue;
+        const uint32_t idesc = (WIDE && tiles[t].wide) ? idesc256 : idesc128;
         if (!mbar_wait(smem_u32(&tempty_bar[acc]), acc_phase ^ 1, &abort_flag, gerr, 2)) break;
         tc_fence_after();
-        const uint32_t d_tmem = tmem_base + (uint32_t)(acc * kRows);
+        const uint32_t d_tmem = tmem_base + (uint32_t)(acc * kAccCols);
         uint32_t accumulate = 0;
         for (int si = job.seg_begin; si < job.seg_end && !abort_flag; ++si) {
           const int nkt = segs[si].nkt;
@@ -338,9 +406,9 @@ tc_gemm_kernel(const TcTile* __restrict__ tiles, int ntiles, const TcJob* __rest
               const int pa = PLANES == 3 ? (pr == 0 ? 0 : pr == 1 ? 0 : pr == 2 ? 1 : pr == 3 ? 0 : pr == 4 ? 1 : 2) : 0;
               const int pb = PLANES == 3 ? (pr == 0 ? 0 : pr == 1 ? 1 : pr == 2 ? 0 : pr == 3 ? 2 : pr == 4 ? 1 : 0) : 0;
 #pragma unroll
-              for (int kk = 0; kk < 4; ++kk) {
-                const uint64_t ad = smem_desc(sa + pa * kChunk + kk * 32);
-                const uint64_t bd = smem_desc(sb + pb * kChunk + kk * 32);
+              for (int kk = 0; kk < L::ROWB / 32; ++kk) {  // one MMA per 32 bytes of K
+                const uint64_t ad = L::desc(sa + pa * L::CHUNK + kk * 32);
+                const uint64_t bd = L::desc(sb + pb * kSlotB + kk * 32);
                 mma<TF32>(d_tmem, ad, bd, idesc, accumulate);
                 accumulate = 1;
               }
@@ -386,10 +454,11 @@ tc_gemm_kernel(const TcTile* __restrict__ tiles, int ntiles, const TcJob* __rest
         tc_fence_after();
       }
       const int64_t m = (int64_t)tile.mt * kRows + row;
-      for (int c0 = 0; c0 < kRows; c0 += 32) {
+      const int ncols = (WIDE && tile.wide) ? 256 : 128;
+      for (int c0 = 0; c0 < ncols; c0 += 32) {
         uint32_t v[32];
         if (has) {
-          tmem_ld32(tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(acc * kRows + c0), v);
+          tmem_ld32(tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(acc * kAccCols + c0), v);
         } else {
 #pragma unroll
           for (int j = 0; j < 32; ++j) v[j] = 0u;
@@ -412,7 +481,7 @@ tc_gemm_kernel(const TcTile* __restrict__ tiles, int ntiles, const TcJob* __rest
         } else {
           const int kt = n0 / KT;
           if (kt < job.out_nkt) {
-            uint8_t* tb = o_img + job.out_off + ((int64_t)tile.mt * job.out_nkt + kt) * PLANES * kChunk;
+            uint8_t* tb = o_img + job.out_off + ((int64_t)tile.mt * job.out_nkt + kt) * PLANES * L::CHUNK;
             if constexpr (TF32) {
 #pragma unroll
               for (int g = 0; g < 8; ++g) {
@@ -421,7 +490,7 @@ tc_gemm_kernel(const TcTile* __restrict__ tiles, int ntiles, const TcJob* __rest
                 q.y = __float_as_uint(to_tf32(__uint_as_float(v[4 * g + 1])));
                 q.z = __float_as_uint(to_tf32(__uint_as_float(v[4 * g + 2])));
                 q.w = __float_as_uint(to_tf32(__uint_as_float(v[4 * g + 3])));
-                *reinterpret_cast<uint4*>(tb + swz(row, g)) = q;
+                *reinterpret_cast<uint4*>(tb + L::off(row, g)) = q;
               }
             } else {
               const int gbase = (n0 % KT) / 8;
@@ -446,10 +515,10 @@ tc_gemm_kernel(const TcTile* __restrict__ tiles, int ntiles, const TcJob* __rest
                   w1[e] = pack2_bf16(h[0][1], h[1][1]);
                   w2[e] = pack2_bf16(h[0][2], h[1][2]);
                 }
-                const uint32_t off = swz(row, gbase + g);
+                const uint32_t off = L::off(row, gbase + g);
                 *reinterpret_cast<uint4*>(tb + off) = make_uint4(w0[0], w0[1], w0[2], w0[3]);
-                *reinterpret_cast<uint4*>(tb + kChunk + off) = make_uint4(w1[0], w1[1], w1[2], w1[3]);
-                *reinterpret_cast<uint4*>(tb + 2 * kChunk + off) = make_uint4(w2[0], w2[1], w2[2], w2[3]);
+                *reinterpret_cast<uint4*>(tb + L::CHUNK + off) = make_uint4(w1[0], w1[1], w1[2], w1[3]);
+                *reinterpret_cast<uint4*>(tb + 2 * L::CHUNK + off) = make_uint4(w2[0], w2[1], w2[2], w2[3]);
               }
             }
           }
@@ -474,9 +543,9 @@ tc_gemm_kernel(const TcTile* __restrict__ tiles, int ntiles, const TcJob* __rest
   }
 }
 
-template <int PLANES, int STAGES, bool TF32>
+template <int PLANES, int STAGES, bool TF32, bool WIDE>
 constexpr size_t smem_bytes() {
-  return (size_t)STAGES * 2 * PLANES * kChunk + 1024;
+  return (size_t)STAGES * (PLANES * Layout<TF32>::CHUNK * (WIDE ? 3 : 2)) + 1024;
 }
 
 }  // namespace tc
@@ -484,18 +553,18 @@ constexpr size_t smem_bytes() {
 // ======================================================================== host side
 namespace {
 
-using tc::kChunk;
 using tc::kRows;
 
 int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 
 struct ImageAlloc {
   int64_t bytes = 0;
+  int64_t chunk = 0;  // bytes of one plane of one image tile
   int64_t add(int64_t rows, int64_t K, int planes, int kt_elems, int* nkt_out) {
     const int nrt = ceil_div(rows, kRows), nkt = ceil_div(K, kt_elems);
     *nkt_out = nkt;
     const int64_t off = bytes;
-    bytes += (int64_t)nrt * nkt * planes * kChunk;
+    bytes += (int64_t)nrt * nkt * planes * chunk;
     return off;
   }
 };
@@ -539,14 +608,14 @@ dmrg_status launch_pack(const std::vector<PackChunk>& chunks, const PackChunk* d
 bool tc_tiles_in_range(const TcPlan* t, int64_t n, const std::vector<TcJob>& jobs,
                        const std::vector<TcSeg>& segs, const std::vector<TcTile>& tiles,
                        int job_base, int seg_base, char* why, size_t why_len) {
-  const int64_t stageA = (int64_t)t->planes * kChunk;
+  const int64_t stageA = (int64_t)t->planes * t->chunk;
   auto bytes = [&](int b) { return (int64_t)t->buf_bytes[b == TB_XB ? TB_XA : b]; };
   for (const TcTile& tl : tiles) {
     const TcJob& j = jobs[tl.job - job_base];
     for (int si = j.seg_begin; si < j.seg_end; ++si) {
       const TcSeg& sg = segs[si - seg_base];
       const int64_t pe = sg.p_off + ((int64_t)tl.mt * sg.p_nkt + sg.nkt) * stageA;
-      const int64_t qe = sg.q_off + ((int64_t)tl.nt * sg.q_nkt + sg.nkt) * stageA;
+      const int64_t qe = sg.q_off + ((int64_t)(tl.nt + (tl.wide ? 1 : 0)) * sg.q_nkt + sg.nkt) * stageA;
       if (sg.p_off < 0 || pe > bytes(sg.p_buf) || sg.q_off < 0 || qe > bytes(sg.q_buf)) {
         snprintf(why, why_len, "tile (job %d, %d, %d) segment %d reads outside its operand images",
                  tl.job, tl.mt, tl.nt, si);
@@ -574,7 +643,8 @@ dmrg_status build_tc(dmrg_plan* p, dmrg_precision prec, cudaStream_t st, TcPlan*
   t->prec = prec;
   const bool tf32 = prec == DMRG_PREC_TF32;
   t->planes = tf32 ? 1 : 3;
-  t->kt_elems = tf32 ? 32 : 64;
+  t->kt_elems = tf32 ? tc::Layout<true>::KT : tc::Layout<false>::KT;
+  t->chunk = tf32 ? tc::Layout<true>::CHUNK : tc::Layout<false>::CHUNK;
   const int planes = t->planes, KT = t->kt_elems;
   int dev = 0;
   cudaGetDevice(&dev);
@@ -583,6 +653,7 @@ dmrg_status build_tc(dmrg_plan* p, dmrg_precision prec, cudaStream_t st, TcPlan*
 
   // ---- operator images, keyed by (side, op, block, scale)
   ImageAlloc ops_alloc;
+  ops_alloc.chunk = t->chunk;
   std::vector<PackJob> op_jobs;
   std::map<std::tuple<int, int, int, double>, std::pair<int64_t, int>> op_img;  // -> (off, nkt)
   auto op_image = [&](int side, int op, int blk, double scale) -> std::pair<int64_t, int> {
@@ -610,6 +681,7 @@ dmrg_status build_tc(dmrg_plan* p, dmrg_precision prec, cudaStream_t st, TcPlan*
   // ---- vector images (A-form rows = left index, B-form rows = right index)
   const int npairs = (int)p->pair_i.size();
   ImageAlloc xa_alloc;  // both forms share one buffer: A-form tiles, then B-form tiles
+  xa_alloc.chunk = t->chunk;
   std::vector<PackJob> x_jobs;
   std::vector<std::pair<int64_t, int>> xa(npairs), xb(npairs);
   for (int q = 0; q < npairs; ++q) {
@@ -632,6 +704,7 @@ dmrg_status build_tc(dmrg_plan* p, dmrg_precision prec, cudaStream_t st, TcPlan*
 
   // ---- jobs
   ImageAlloc inter_alloc;
+  inter_alloc.chunk = t->chunk;
   std::vector<TcJob> jobs;
   std::vector<TcSeg> segs;
   std::vector<TcTile> tiles1, tiles2;
@@ -732,15 +805,29 @@ dmrg_status build_tc(dmrg_plan* p, dmrg_precision prec, cudaStream_t st, TcPlan*
   };
   std::stable_sort(order1.begin(), order1.end(), by_cost);
   std::stable_sort(order2.begin(), order2.end(), by_cost);
+  // work of a 128 x 128 tile of each job (K tiles) and the mean narrow work per SM
+  std::vector<int64_t> job_cost(jobs.size(), 0);
+  int64_t mean_work[2] = {0, 0};
+  for (int g = 0; g < 2; ++g) {
+    for (const auto& pr : g == 0 ? order1 : order2) {
+      job_cost[pr.second] = pr.first;
+      const TcJob& j = jobs[pr.second];
+      mean_work[g] += pr.first * ceil_div(j.M, kRows) * ceil_div(j.N, kRows);
+    }
+    mean_work[g] /= std::max(1, t->sms);
+  }
+  int wpol = 0, cur_stage = 0;  // width policy and stage of the schedule being built
   auto add_tiles = [&](std::vector<TcTile>& dst, int jb, bool col_major) {
     const TcJob& j = jobs[jb];
     const int nm = ceil_div(j.M, kRows), nn = ceil_div(j.N, kRows);
+    const bool may_wide = !tf32 && (wpol == 2 || (wpol == 1 && 4 * job_cost[jb] <= mean_work[cur_stage]));
+    auto width = [&](int nt) { return (may_wide && nt + 1 < nn) ? 2 : 1; };
     if (col_major) {
-      for (int nt = 0; nt < nn; ++nt)
-        for (int mt = 0; mt < nm; ++mt) dst.push_back(TcTile{jb, mt, nt, 0});
+      for (int nt = 0; nt < nn; nt += width(nt))
+        for (int mt = 0; mt < nm; ++mt) dst.push_back(TcTile{jb, mt, nt, 0, width(nt) - 1});
     } else {
       for (int mt = 0; mt < nm; ++mt)
-        for (int nt = 0; nt < nn; ++nt) dst.push_back(TcTile{jb, mt, nt, 0});
+        for (int nt = 0; nt < nn; nt += width(nt)) dst.push_back(TcTile{jb, mt, nt, 0, width(nt) - 1});
     }
   };
   // jobs (already in descending cost) grouped by key; groups in descending total cost
@@ -763,8 +850,6 @@ dmrg_status build_tc(dmrg_plan* p, dmrg_precision prec, cudaStream_t st, TcPlan*
     return res;
   };
   std::vector<TcTile> sched1[kSchedules], sched2[kSchedules];
-  for (const auto& pr : order1) add_tiles(sched1[0], pr.second, false);
-  for (const auto& pr : order2) add_tiles(sched2[0], pr.second, false);
   // a stage-1 job has one segment (its record), or none when its K dimension is empty
   auto x_key = [&](int jb) -> int64_t {
     const TcJob& j = jobs[jb];
@@ -774,12 +859,21 @@ dmrg_status build_tc(dmrg_plan* p, dmrg_precision prec, cudaStream_t st, TcPlan*
     const TcJob& j = jobs[jb];
     return j.seg_begin == j.seg_end ? -1 : segs[j.seg_begin].p_off;
   };
-  sched1[1] = grouped(order1, x_key, true);
-  sched1[2] = grouped(order1, op_key, false);
   std::vector<int> job_pair(jobs.size(), -1);
   for (int q = 0; q < npairs; ++q) job_pair[stage2_job[q]] = q;
-  sched2[1] = grouped(order2, [&](int jb) { return (int64_t)p->pair_k[job_pair[jb]]; }, false);
-  sched2[2] = grouped(order2, [&](int jb) { return (int64_t)p->pair_i[job_pair[jb]]; }, false);
+  t->nsched = tf32 ? kOrders : kSchedules;
+  for (int c = 0; c < t->nsched; ++c) {
+    wpol = c / kOrders;
+    const int o = c % kOrders;
+    cur_stage = 0;
+    if (o == 0) for (const auto& pr : order1) add_tiles(sched1[c], pr.second, false);
+    if (o == 1) sched1[c] = grouped(order1, x_key, true);
+    if (o == 2) sched1[c] = grouped(order1, op_key, false);
+    cur_stage = 1;
+    if (o == 0) for (const auto& pr : order2) add_tiles(sched2[c], pr.second, false);
+    if (o == 1) sched2[c] = grouped(order2, [&](int jb) { return (int64_t)p->pair_k[job_pair[jb]]; }, false);
+    if (o == 2) sched2[c] = grouped(order2, [&](int jb) { return (int64_t)p->pair_i[job_pair[jb]]; }, false);
+  }
   tiles1 = sched1[0];
   tiles2 = sched2[0];
   // stage-1 N tiles read Q image row tiles; stage-2 image K tiles must cover the segment
@@ -807,10 +901,12 @@ dmrg_status build_tc(dmrg_plan* p, dmrg_precision prec, cudaStream_t st, TcPlan*
   t->buf[TB_XB] = t->buf[TB_XA];  // alias: B-form offsets follow the A-form tiles
   {
     char why[160];
-    if (!tc_tiles_in_range(t, p->n, jobs, segs, tiles1, 0, 0, why, sizeof(why)) ||
-        !tc_tiles_in_range(t, p->n, jobs, segs, tiles2, 0, 0, why, sizeof(why))) {
-      set_error("internal: %s", why);
-      return fail(DMRG_ERR_SHAPE);
+    for (int c = 0; c < t->nsched; ++c) {
+      if (!tc_tiles_in_range(t, p->n, jobs, segs, sched1[c], 0, 0, why, sizeof(why)) ||
+          !tc_tiles_in_range(t, p->n, jobs, segs, sched2[c], 0, 0, why, sizeof(why))) {
+        set_error("internal: %s", why);
+        return fail(DMRG_ERR_SHAPE);
+      }
     }
   }
   if (t->buf[TB_INTER]) {
@@ -840,13 +936,11 @@ dmrg_status build_tc(dmrg_plan* p, dmrg_precision prec, cudaStream_t st, TcPlan*
   t->n_xpack_chunks = (int64_t)x_chunks.size();
   if ((s = upload_vec(&t->d_jobs, jobs, st)) != DMRG_OK) return fail(s);
   if ((s = upload_vec(&t->d_segs, segs, st)) != DMRG_OK) return fail(s);
-  for (int c = 0; c < kSchedules; ++c) {
-    if (sched1[c].size() != tiles1.size() || sched2[c].size() != tiles2.size()) {
-      set_error("internal: tile schedules of different sizes");
-      return fail(DMRG_ERR_SHAPE);
-    }
+  for (int c = 0; c < t->nsched; ++c) {
     if ((s = upload_vec(&t->d_tiles[0][c], sched1[c], st)) != DMRG_OK) return fail(s);
     if ((s = upload_vec(&t->d_tiles[1][c], sched2[c], st)) != DMRG_OK) return fail(s);
+    t->ntiles[0][c] = (int64_t)sched1[c].size();
+    t->ntiles[1][c] = (int64_t)sched2[c].size();
   }
   t->ntiles1 = (int64_t)tiles1.size();
   t->ntiles2 = (int64_t)tiles2.size();
@@ -870,12 +964,13 @@ dmrg_status build_tc(dmrg_plan* p, dmrg_precision prec, cudaStream_t st, TcPlan*
 
 template <int PLANES, int STAGES, bool TF32>
 dmrg_status configure_tc() {
-  constexpr size_t smem = tc::smem_bytes<PLANES, STAGES, TF32>();
+  constexpr bool WIDE = !TF32;
+  constexpr size_t smem = tc::smem_bytes<PLANES, STAGES, TF32, WIDE>();
   static bool configured[64] = {false};
   int dev = 0;
   DMRG_CUDA_TRY(cudaGetDevice(&dev));
   if (dev >= 0 && dev < 64 && !configured[dev]) {
-    DMRG_CUDA_TRY(cudaFuncSetAttribute(tc::tc_gemm_kernel<PLANES, STAGES, TF32>,
+    DMRG_CUDA_TRY(cudaFuncSetAttribute(tc::tc_gemm_kernel<PLANES, STAGES, TF32, !TF32>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     configured[dev] = true;
   }
@@ -886,7 +981,8 @@ dmrg_status configure_tc() {
 template <int PLANES, int STAGES, bool TF32>
 dmrg_status run_tc_part(dmrg_plan* p, TcPlan* t, const double* x, double* y, int part, int c,
                         cudaStream_t st) {
-  constexpr size_t smem = tc::smem_bytes<PLANES, STAGES, TF32>();
+  constexpr bool WIDE = !TF32;
+  constexpr size_t smem = tc::smem_bytes<PLANES, STAGES, TF32, WIDE>();
   if (part == 0) {
     if (t->n_xpack_chunks > 0) {  // X -> A-form and B-form images
       tc::pack_kernel<PLANES, TF32><<<(unsigned)t->n_xpack_chunks, 256, 0, st>>>(
@@ -895,10 +991,10 @@ dmrg_status run_tc_part(dmrg_plan* p, TcPlan* t, const double* x, double* y, int
     }
     return DMRG_OK;
   }
-  const int64_t nt = part == 1 ? t->ntiles1 : t->ntiles2;
+  const int64_t nt = t->ntiles[part - 1][c];
   if (nt == 0) return DMRG_OK;
   const int grid = (int)std::min<int64_t>(nt, t->sms);
-  tc::tc_gemm_kernel<PLANES, STAGES, TF32><<<grid, tc::kThreads, smem, st>>>(
+  tc::tc_gemm_kernel<PLANES, STAGES, TF32, WIDE><<<grid, tc::kThreads, smem, st>>>(
       t->d_tiles[part - 1][c], (int)nt, t->d_jobs, t->d_segs, t->buf[TB_OPS], t->buf[TB_XA],
       t->buf[TB_XB], part == 1 ? nullptr : t->buf[TB_INTER], part == 1 ? t->buf[TB_INTER] : nullptr,
       y, x, t->d_err, nullptr, part);
@@ -946,7 +1042,7 @@ dmrg_status tune_tc(dmrg_plan* p, TcPlan* t, const double* x, double* y, cudaStr
   for (int part = 1; part <= 2 && s == DMRG_OK; ++part) {
     float best = 0.0f;
     int arg = 0;
-    for (int c = 0; c < kSchedules && s == DMRG_OK; ++c) {
+    for (int c = 0; c < t->nsched && s == DMRG_OK; ++c) {
       float ms[3] = {0.0f, 0.0f, 0.0f};
       s = run_tc_part<PLANES, STAGES, TF32>(p, t, x, y, part, c, st);
       for (int r = 0; r < 3 && s == DMRG_OK; ++r) {
@@ -1080,10 +1176,24 @@ dmrg_status tc_batch_create(dmrg_plan* const* plans, int nb, dmrg_precision prec
     std::stable_sort(items[g].begin(), items[g].end(), [](const Item& a, const Item& c) {
       return a.cost > c.cost;
     });
+    // width policy 1 of the single-plan schedules over the whole batch: 256-column tiles
+    // for jobs whose wide tile stays below half of the mean work per SM
+    int64_t mean = 0;
     for (const Item& it : items[g]) {
       const TcJob& j = jobs[it.job];
+      mean += it.cost * ceil_div(j.M, kRows) * ceil_div(j.N, kRows);
+    }
+    mean /= std::max(1, b->sms);
+    for (const Item& it : items[g]) {
+      const TcJob& j = jobs[it.job];
+      const int nn = ceil_div(j.N, kRows);
+      const bool wide_tiles = prec == DMRG_PREC_BF16X3 && 4 * it.cost <= mean;
       for (int mt = 0; mt < ceil_div(j.M, kRows); ++mt)
-        for (int nt = 0; nt < ceil_div(j.N, kRows); ++nt) tiles[g].push_back(TcTile{it.job, mt, nt, it.prob});
+        for (int nt = 0; nt < nn;) {
+          const int w = (wide_tiles && nt + 1 < nn) ? 2 : 1;
+          tiles[g].push_back(TcTile{it.job, mt, nt, it.prob, w - 1});
+          nt += w;
+        }
     }
     b->ntiles[g] = (int64_t)tiles[g].size();
   }
@@ -1107,7 +1217,7 @@ dmrg_status tc_batch_create(dmrg_plan* const* plans, int nb, dmrg_precision prec
         j.seg_begin -= seg_base[i];
         j.seg_end -= seg_base[i];
         std::vector<TcJob> one(1, j);
-        std::vector<TcTile> onet(1, TcTile{0, tl.mt, tl.nt, 0});
+        std::vector<TcTile> onet(1, TcTile{0, tl.mt, tl.nt, 0, tl.wide});
         if (j.seg_begin < 0 || j.seg_end > (int)t->h_segs.size() ||
             !tc_tiles_in_range(t, plans[i]->n, one, t->h_segs, onet, 0, 0, why, sizeof(why))) {
           set_error("internal: grouped launch, problem %d: %s", i, why);
@@ -1158,7 +1268,8 @@ dmrg_status tc_batch_error(const TcBatch* b) {
 namespace {
 template <int PLANES, int STAGES, bool TF32>
 dmrg_status run_batch(TcBatch* b, cudaStream_t st) {
-  constexpr size_t smem = tc::smem_bytes<PLANES, STAGES, TF32>();
+  constexpr bool WIDE = !TF32;
+  constexpr size_t smem = tc::smem_bytes<PLANES, STAGES, TF32, WIDE>();
   DMRG_TRY((configure_tc<PLANES, STAGES, TF32>()));
   if (b->nchunks > 0) {
     tc::pack_kernel<PLANES, TF32><<<(unsigned)b->nchunks, 256, 0, st>>>(
@@ -1169,7 +1280,7 @@ dmrg_status run_batch(TcBatch* b, cudaStream_t st) {
     const int64_t nt = b->ntiles[part - 1];
     if (nt == 0) continue;
     const int grid = (int)std::min<int64_t>(nt, b->sms);
-    tc::tc_gemm_kernel<PLANES, STAGES, TF32><<<grid, tc::kThreads, smem, st>>>(
+    tc::tc_gemm_kernel<PLANES, STAGES, TF32, WIDE><<<grid, tc::kThreads, smem, st>>>(
         b->d_tiles[part - 1], (int)nt, b->d_jobs, b->d_segs, nullptr, nullptr, nullptr, nullptr,
         nullptr, nullptr, nullptr, b->d_err, b->d_ptrs, part);
     DMRG_LAUNCH_CHECK();
@@ -1205,7 +1316,7 @@ dmrg_status tc_batch_project(TcBatch* b, const double* const* x, double* const* 
                                 cudaMemcpyHostToDevice, st));
   DMRG_CUDA_TRY(cudaEventRecord(b->ev[r], st));
   if (b->prec == DMRG_PREC_TF32) return run_batch<1, 6, true>(b, st);
-  return run_batch<3, 2, false>(b, st);
+  return run_batch<3, 3, false>(b, st);
 }
 
 bool tc_available(dmrg_precision prec) {
@@ -1243,10 +1354,10 @@ dmrg_status launch_project_tc(dmrg_plan* p, dmrg_precision prec, const double* x
   TcPlan* t = p->tc[slot];
   if (p->opt.autotune && !t->tuned) {
     if (prec == DMRG_PREC_TF32) DMRG_TRY((tune_tc<1, 6, true>(p, t, x, y, st)));
-    else DMRG_TRY((tune_tc<3, 2, false>(p, t, x, y, st)));
+    else DMRG_TRY((tune_tc<3, 3, false>(p, t, x, y, st)));
   }
   if (prec == DMRG_PREC_TF32) return run_tc<1, 6, true>(p, t, x, y, st);
-  return run_tc<3, 2, false>(p, t, x, y, st);
+  return run_tc<3, 3, false>(p, t, x, y, st);
 }
 
 dmrg_status tune_project_tc(dmrg_plan* p, dmrg_precision prec, cudaStream_t st) {
@@ -1265,16 +1376,17 @@ dmrg_status tune_project_tc(dmrg_plan* p, dmrg_precision prec, cudaStream_t st) 
     return DMRG_ERR_OOM;
   }
   dmrg_status s = prec == DMRG_PREC_TF32 ? tune_tc<1, 6, true>(p, t, p->D, y, st)
-                                         : tune_tc<3, 2, false>(p, t, p->D, y, st);
+                                         : tune_tc<3, 3, false>(p, t, p->D, y, st);
   cudaFreeAsync(y, st);
   return s;
 }
 
-void tc_schedule_stats(const dmrg_plan* p, int32_t sched[2], float us[2][3]) {
+void tc_schedule_stats(const dmrg_plan* p, int32_t sched[2], float us[2][DMRG_TILE_SCHEDULES]) {
+  static_assert(DMRG_TILE_SCHEDULES == kSchedules, "schedule count of the public stats");
   const TcPlan* t = p->tc[1] ? p->tc[1] : p->tc[0];
   for (int g = 0; g < 2; ++g) {
     sched[g] = t ? t->sched[g] : -1;
-    for (int c = 0; c < 3; ++c) us[g][c] = t ? t->tune_us[g][c] : 0.0f;
+    for (int c = 0; c < kSchedules; ++c) us[g][c] = t ? t->tune_us[g][c] : 0.0f;
   }
 }
 
