@@ -135,3 +135,35 @@ __host__ __device__ __forceinline__ uint32_t swz(int r, int g) {
   return (uint32_t)((r >> 3) * 1024 + (r & 7) * 128 + ((g ^ (r & 7)) << 4));
 }
 
+// Operand image layout.  An image tile is 128 rows x one K-tile of 32 elements, K-major:
+//   BF16x3 planes: 64-byte rows, 64-byte swizzle (8-row atoms of 512 bytes; the 16-byte
+//                  group g of row r sits at group g ^ ((r >> 1) & 3) of its row), 8 KB
+//   TF32:          128-byte rows, 128-byte swizzle (1024-byte atoms, g ^ (r & 7)), 16 KB
+// so that a pipeline stage of BF16x3 (three planes of A and of B) is 48 KB and four stages
+// fit in shared memory.
+template <bool TF32>
+struct Layout {
+  static constexpr int ROWB = TF32 ? 128 : 64;  // bytes per image row
+  static constexpr int GROUPS = ROWB / 16;      // 16-byte groups per row
+  static constexpr int KT = 32;                 // elements per K-tile
+  static constexpr int CHUNK = kRows * ROWB;    // bytes of one plane of one image tile
+  __host__ __device__ static uint32_t off(int r, int g) {
+    if constexpr (TF32) return swz(r, g);
+    else return (uint32_t)((r >> 3) * 512 + (r & 7) * 64 + ((g ^ ((r >> 1) & 3)) << 4));
+  }
+  // shared-memory matrix descriptor of a K-major operand in this layout (descriptor
+  // version 1; stride byte offset = distance between 8-row atoms)
+  __device__ static uint64_t desc(uint32_t addr) {
+    if constexpr (TF32) {
+      return smem_desc(addr);
+    } else {
+      uint64_t d = 0;
+      d |= (uint64_t)((addr & 0x3FFFFu) >> 4);
+      d |= (uint64_t)(16u >> 4) << 16;
+      d |= (uint64_t)(512u >> 4) << 32;
+      d |= (uint64_t)1 << 46;
+      d |= (uint64_t)4 << 61;  // 64-byte swizzle
+      return d;
+    }
+  }
+};
