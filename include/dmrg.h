@@ -82,7 +82,7 @@ typedef enum {
 enum { DMRG_HOST_DATA = 0, DMRG_DEVICE_DATA = 1 };
 enum { DMRG_IDENTITY_OP = -1 };
 enum { DMRG_MAX_SUBSPACE = 24 };
-enum { DMRG_TILE_SCHEDULES = 9 };  /* candidate tile schedules per tensor-core GEMM stage */
+enum { DMRG_TILE_SCHEDULES = 27 };  /* candidate tile schedules per tensor-core GEMM stage */
 
 /* One dense block A_{q_in -> q_out} of an operator (Sec. 4.1, around Eq. 11). */
 typedef struct {
@@ -176,13 +176,16 @@ typedef struct {
                                identity factors only)                                      */
   int64_t tiles_stage1, tiles_stage2;
   int64_t device_bytes;     /* device memory owned by the plan                            */
-  int32_t tc_schedule[2];   /* tile schedule of tensor-core GEMM stages 1 and 2, 3 w + o:
-                               order o (0: jobs in descending cost; 1: stage 1 grouped by
-                               vector segment, stage 2 by right sector; 2: stage 1 grouped
-                               by operator block, stage 2 by left sector) and BF16x3 tile
-                               width w (0: 128 columns; 1: 256 columns for tiles below half
-                               the mean work per SM; 2: 256 wherever possible); -1 before a
-                               TF32/BF16X3 plan exists                                      */
+  int32_t tc_schedule[2];   /* tile schedule of tensor-core GEMM stages 1 and 2,
+                               (3 s + w) 3 + o: order o of the tile list that the CTAs take
+                               tiles from (0: descending estimated time; 1: stage 1 grouped
+                               by vector segment, stage 2 by right sector; 2: stage 1
+                               grouped by operator block, stage 2 by left sector), BF16x3
+                               tile width w (0: 128 columns; 1: 256 columns for tiles below
+                               half the mean work per SM; 2: 256 wherever possible) and
+                               stage-2 K split s (0: none; 1, 2: tiles above 2/3, 2/5 of the
+                               mean time per SM split into parts); -1 before a TF32/BF16X3
+                               plan exists                                                 */
   float tc_tune_us[2][DMRG_TILE_SCHEDULES]; /* autotuner: median time of each schedule per
                                stage (us), 0 if not tuned or not a candidate               */
 } dmrg_plan_stats;
@@ -210,6 +213,14 @@ dmrg_status dmrg_plan_get_stats(const dmrg_plan* plan, dmrg_plan_stats* stats);
  * dispatched to streams by Algorithms 6-7).  Synchronizes the stream; allocates and frees
  * 256 MB of scratch. */
 dmrg_status dmrg_plan_autotune(dmrg_plan* plan, dmrg_precision prec, void* stream);
+
+/* Fixes the tile schedules of the tensor-core projection in precision prec (DMRG_PREC_TF32
+ * or DMRG_PREC_BF16X3) to stage1 and stage2 (indices as in dmrg_plan_stats.tc_schedule;
+ * stage 1 takes no K split, TF32 only 128-column tiles) and keeps the first projection
+ * from autotuning; builds the operand images if needed and synchronizes the stream.
+ * DMRG_ERR_INVALID_ARG for an index that is not a candidate of its stage. */
+dmrg_status dmrg_plan_set_tile_schedule(dmrg_plan* plan, dmrg_precision prec, int32_t stage1,
+                                        int32_t stage2, void* stream);
 
 /* y = H_SB x (Eq. 11 summed over all records), in the given precision.  x and y are
  * device arrays of n float64 and must not overlap.  Enqueued on stream. */

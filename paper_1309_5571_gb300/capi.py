@@ -19,6 +19,7 @@ LIB_PATH = os.path.join(HERE, "_build", "libdmrg_gb300.so")
 
 PREC = {"fp64": 0, "tf32": 1, "bf16x3": 2, "fp64tc": 3}
 VEC = {"fp64": 0, "df": 1, "split": 2}
+TILE_SCHEDULES = 27  # DMRG_TILE_SCHEDULES: candidate tile schedules per GEMM stage
 IDENTITY = -1
 MAX_SUBSPACE = 24
 
@@ -82,7 +83,7 @@ class PlanStats(C.Structure):
     _fields_ = [("n", C.c_int64), ("records", C.c_int64), ("flops", C.c_int64),
                 ("tiles_stage1", C.c_int64), ("tiles_stage2", C.c_int64),
                 ("device_bytes", C.c_int64), ("tc_schedule", C.c_int32 * 2),
-                ("tc_tune_us", (C.c_float * 9) * 2)]
+                ("tc_tune_us", (C.c_float * TILE_SCHEDULES) * 2)]
 
     def as_dict(self):
         d = {f: getattr(self, f) for f, _ in self._fields_[:6]}
@@ -99,6 +100,7 @@ SIGNATURES = {
     "dmrg_plan_destroy": (None, [C.c_void_p]),
     "dmrg_plan_get_stats": (C.c_int, [C.c_void_p, C.POINTER(PlanStats)]),
     "dmrg_plan_autotune": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
+    "dmrg_plan_set_tile_schedule": (C.c_int, [C.c_void_p, C.c_int, C.c_int32, C.c_int32, C.c_void_p]),
     "dmrg_project": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "dmrg_project_prec": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
     "dmrg_diagonal": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
@@ -273,6 +275,13 @@ class Plan:
         """dmrg_plan_autotune: time the tile schedules of the tensor-core GEMM stages."""
         _check(self.lib.dmrg_plan_autotune(self.handle, PREC[prec] if isinstance(prec, str) else int(prec),
                                            _stream_ptr(stream)))
+        return self.get_stats()
+
+    def set_tile_schedule(self, stage1, stage2, prec="bf16x3", stream=None):
+        """dmrg_plan_set_tile_schedule: fix the tile schedules of the two GEMM stages."""
+        _check(self.lib.dmrg_plan_set_tile_schedule(
+            self.handle, PREC[prec] if isinstance(prec, str) else int(prec), int(stage1), int(stage2),
+            _stream_ptr(stream)))
         return self.get_stats()
 
     def project(self, x, y=None, prec=None, stream=None):

@@ -434,7 +434,7 @@ dmrg_status phase_b(dmrg_davidson_state* s, cudaStream_t st, bool* need_c) {
 }
 
 dmrg_status phase_c(dmrg_davidson_state* s, cudaStream_t st) {
-  const int64_t ldv = s->ldv, n = s->n;
+  const int64_t ldv = s->ldv;
   const int k = s->k, knew = s->knew;
   double* tcol = s->V + (int64_t)k * ldv;
   if (s->hsmall->flags & 1) {

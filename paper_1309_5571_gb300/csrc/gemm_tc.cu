@@ -9,24 +9,32 @@
 //   BF16x3 : every operand stored as three BF16 planes x = x0 + x1 + x2 (24 significant
 //            bits); the six products x_i y_j with i + j <= 2 are accumulated in FP32.
 //
-// Operand tiles are "images": the exact shared-memory byte image of a 128-row x 128-byte
-// K-major tile in the 128-byte swizzled canonical layout (8-row atoms of 1024 bytes, the
-// 16-byte chunk c of row r stored at chunk c ^ (r % 8)), zero-padded to whole tiles, with
-// the planes of one (row tile, K tile) contiguous.  A tile therefore arrives in shared
-// memory with ONE bulk asynchronous copy (cp.async.bulk, the TMA engine) and no bounds
-// logic.  Operator blocks are packed once per plan (they are fixed during Davidson, Sec. 7);
-// the Davidson vector is packed per projection in two forms (A-form: rows = left index;
-// B-form: rows = right index); stage-1 epilogues write their results directly as images
-// for stage 2.  The record order "X B^T first" is computed transposed, U^T = B X^T, so that
-// every epilogue writes its accumulator rows as image rows.
+// Operand tiles are "images": the exact shared-memory byte image of a 128-row x 32-element
+// K-major tile in a swizzled canonical layout (BF16x3: 64-byte rows, 512-byte atoms; TF32:
+// 128-byte rows, 1024-byte atoms; see Layout), zero-padded to whole tiles, with the planes
+// of one (row tile, K tile) contiguous.  A tile therefore arrives in shared memory with ONE
+// bulk asynchronous copy (cp.async.bulk, the TMA engine) and no bounds logic.  Operator
+// blocks are packed once per plan (they are fixed during Davidson, Sec. 7); the Davidson
+// vector is packed per projection in two forms (A-form: rows = left index; B-form: rows =
+// right index); stage-1 epilogues write their results directly as images for stage 2.  The
+// record order "X B^T first" is computed transposed, U^T = B X^T, so that every epilogue
+// writes its accumulator rows as image rows.
 //
 // Kernel structure (persistent, one CTA per SM, 192 threads):
-//   warp 0     producer: bulk copies of A and B tiles into a ring of shared-memory stages
-//   warp 1     allocates 256 TMEM columns (two 128-column FP32 accumulators) and one lane
-//              issues tcgen05.mma; tcgen05.commit releases stages and publishes accumulators
+//   warp 0     producer: takes output tiles from the launch's tile list (the first one
+//              blockIdx.x, the following ones from a global atomic counter, i.e. greedy
+//              list scheduling in list order), publishes each tile index in a small
+//              shared-memory ring for the other roles, and issues the bulk copies of its A
+//              and B tiles into a ring of shared-memory stages
+//   warp 1     allocates the TMEM accumulators (two of 128 or 256 FP32 columns) and one
+//              lane issues tcgen05.mma; tcgen05.commit releases stages and publishes
+//              accumulators
 //   warps 2-5  epilogue: tcgen05.ld of the accumulator (warp w reads TMEM lanes
 //              32 (w % 4) .. + 31), then either an image of the result (stage 1) or FP64 Y
-//              plus the identity-identity term (stage 2)
+//              plus the identity-identity term (stage 2).  A stage-2 tile whose K range is
+//              split into parts writes its FP32 partial sums to a scratch slot of its own;
+//              a small kernel after the stage adds the slots in part order and writes Y,
+//              so the result does not depend on which CTA ran which part.
 // Every mbarrier wait is bounded (2 s of %globaltimer); on a timeout the kernel records an
 // error code, stops issuing work, waits (bounded) for its own copies and MMAs, frees TMEM
 // and returns.
@@ -64,7 +72,15 @@ struct TcJob {
 struct TcTile {
   int32_t job, mt, nt, pad_;  // pad_: problem index in a grouped launch
   int32_t wide;               // 1: 256 output columns (row tiles nt and nt + 1 of B)
+  int32_t kb, ke;             // K tiles [kb, ke) of the job's segments taken in order
+  int32_t part, nparts;       // split K (FP64-output tiles only): part of nparts > 1
+  int32_t red;                // split K: partial-sum slots red .. red + nparts - 1; -1 if
+                              // not split
 };
+
+inline TcTile make_tile(int job, int mt, int nt, int prob, int wide, int kb, int ke) {
+  return TcTile{job, mt, nt, prob, wide, kb, ke, 0, 1, -1};
+}
 
 struct PackJob {
   int64_t src_off;        // element offset in the FP64 source
@@ -94,26 +110,34 @@ struct TcPtrs {
   int32_t active, pad_;
 };
 
-// Tile schedules: the tile shapes and the order in which the persistent CTAs take the
-// output tiles (CTA b takes tiles b, b + grid, ...).  Schedule c = 3 w + o combines
-// order o:
-//   0  jobs in descending cost (longest first), tiles row-major within a job
+// Tile schedules: the tile shapes, the K split and the order of the tile list.  The CTAs
+// of a launch take tiles from the list greedily (CTA b starts with tile b; each CTA that
+// finishes a tile takes the next untaken one), so the list order is a priority order.
+// Schedule c = (3 s + w) 3 + o combines order o:
+//   0  tiles in descending estimated time (longest first: list scheduling in LPT order)
 //   1  stage 1: jobs grouped by the vector image they read (all records of one (i, k)
 //      segment and form together), tiles column-major; stage 2: output segments grouped
 //      by their right sector l
 //   2  stage 1: jobs grouped by the operator block image they read, tiles row-major;
 //      stage 2: output segments grouped by their left sector j
-// (groups in descending total cost, jobs within a group in descending cost) with tile
-// width policy w (BF16x3 only; TF32 tiles are always 128 x 128):
+// (groups in descending total cost, jobs within a group in descending cost), tile width
+// policy w (BF16x3 only; TF32 tiles are always 128 x 128):
 //   0  all tiles 128 columns
 //   1  256 columns where the job has two B row tiles left and the tile's work stays below
 //      half of the mean work per SM (wide tiles halve the B-operand traffic per FLOP, but
 //      a long wide tile can become the critical path of the stage)
 //   2  256 columns wherever possible
-// Every schedule computes each output element with the same arithmetic, so the results
-// are identical; operand reuse, load balance and time differ.
-constexpr int kOrders = 3, kWidths = 3;
-constexpr int kSchedules = kOrders * kWidths;
+// and K split policy s (stage 2 only):
+//   0  none
+//   1  tiles estimated above 2/3 (s = 2: 2/5) of the mean time per SM are cut into parts
+//      of whole K tiles below that bound; the parts are list entries of their own, and
+//      a reduction launch after the stage adds their partial sums
+// Schedules without a K split compute each output element with the same arithmetic, so
+// their results are identical; a split changes the FP32 summation order of the split tiles
+// (partial sums added in part order), which is deterministic for a given schedule.
+constexpr int kOrders = 3, kWidths = 3, kSplits = 3;
+constexpr int kSchedules = kOrders * kWidths * kSplits;
+constexpr int kSlotFloats = 128 * 256;  // one split-K partial-sum slot (128 x 256 FP32)
 
 struct TcPlan {
   dmrg_precision prec = DMRG_PREC_BF16X3;
@@ -130,8 +154,13 @@ struct TcPlan {
   // schedule sched[stage]
   TcTile* d_tiles[2][kSchedules] = {};
   int64_t ntiles[2][kSchedules] = {};
-  int nsched = kSchedules;  // TF32: the narrow schedules only
+  bool valid[2][kSchedules] = {};  // candidates of each stage (TF32: narrow; stage 1: no split)
   int64_t ntiles1 = 0, ntiles2 = 0;  // tiles of schedule 0 (all narrow)
+  int* d_ctr = nullptr;        // tile-list counters: 2 per stage, zero between launches
+  float* d_partial = nullptr;  // split-K partial sums: nslots slots of kSlotFloats
+  int64_t nslots = 0;
+  TcTile* d_groups[kSchedules] = {};  // split-K tiles of each stage-2 schedule (part 0)
+  int64_t ngroups[kSchedules] = {};
   int sched[2] = {0, 0};
   bool tuned = false;
   float tune_us[2][kSchedules] = {};
@@ -149,6 +178,7 @@ struct TcPlan {
 namespace tc {
 
 constexpr int kThreads = 192;
+constexpr int kRing = 8;  // tile indices in flight between the producer and the other roles
 
 #include "tc_ptx.cuh"
 #include "cvt.cuh"
@@ -240,7 +270,8 @@ tc_gemm_kernel(const TcTile* __restrict__ tiles, int ntiles, const TcJob* __rest
                const uint8_t* __restrict__ b1, const uint8_t* __restrict__ b2,
                const uint8_t* __restrict__ b3, uint8_t* __restrict__ out_img,
                double* __restrict__ y, const double* __restrict__ x, int* __restrict__ gerr,
-               const TcPtrs* __restrict__ ptrs, int gemm_stage) {
+               const TcPtrs* __restrict__ ptrs, int gemm_stage, int* __restrict__ tile_ctr,
+               float* __restrict__ partial) {
   using L = Layout<TF32>;
   constexpr uint32_t kStageA = PLANES * L::CHUNK;             // A operand of one stage
   constexpr uint32_t kSlotB = (WIDE ? 2 : 1) * L::CHUNK;      // one plane of B
@@ -253,6 +284,8 @@ tc_gemm_kernel(const TcTile* __restrict__ tiles, int ntiles, const TcJob* __rest
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
   __shared__ __align__(8) uint64_t full_bar[STAGES], empty_bar[STAGES];
   __shared__ __align__(8) uint64_t tfull_bar[2], tempty_bar[2], drain_bar;
+  __shared__ __align__(8) uint64_t tq_full[kRing], tq_empty[kRing];
+  __shared__ int tile_ring[kRing];
   __shared__ uint32_t tmem_slot;
   __shared__ volatile int abort_flag;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -267,6 +300,10 @@ tc_gemm_kernel(const TcTile* __restrict__ tiles, int ntiles, const TcJob* __rest
       mbar_init(smem_u32(&tempty_bar[a]), 128);
     }
     mbar_init(smem_u32(&drain_bar), 1);
+    for (int r = 0; r < kRing; ++r) {
+      mbar_init(smem_u32(&tq_full[r]), 1);
+      mbar_init(smem_u32(&tq_empty[r]), 5);  // the MMA lane and one lane per epilogue warp
+    }
     abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -284,6 +321,16 @@ tc_gemm_kernel(const TcTile* __restrict__ tiles, int ntiles, const TcJob* __rest
   // grouped launch (ptrs != NULL): the operand buffers and outputs of each tile are those
   // of its problem (tile.pad_), and tiles of inactive problems are skipped by all roles
   auto active = [&](const TcTile& tile) { return !ptrs || ptrs[tile.pad_].active != 0; };
+  // consumer side of the tile ring: the next tile index, -1 at the end (or on abort);
+  // called by the MMA lane alone or by a whole epilogue warp (one arrival per warp)
+  auto next_tile = [&](int& slot, uint32_t& phase, bool whole_warp, int code) -> int {
+    if (!mbar_wait(smem_u32(&tq_full[slot]), phase, &abort_flag, gerr, code)) return -1;
+    const int t = tile_ring[slot];
+    if (whole_warp) __syncwarp();
+    if ((threadIdx.x & 31) == 0) mbar_arrive(smem_u32(&tq_empty[slot]));
+    if (++slot == kRing) { slot = 0; phase ^= 1; }
+    return t;
+  };
 
   if (warp == 0) {
     // ------------------------------------------------ producer
@@ -291,8 +338,20 @@ tc_gemm_kernel(const TcTile* __restrict__ tiles, int ntiles, const TcJob* __rest
       int stage = 0;
       uint32_t phase = 0;
       int64_t issued = 0;
-      for (int t = blockIdx.x; t < ntiles && !abort_flag; t += gridDim.x) {
+      int rslot = 0;
+      uint32_t rphase = 0;
+      for (int t = blockIdx.x;;) {
+        // publish the tile (-1: none left) to the MMA and epilogue warps
+        if (!mbar_wait(smem_u32(&tq_empty[rslot]), rphase ^ 1, &abort_flag, gerr, 5)) break;
+        const bool done = t >= ntiles || abort_flag;
+        tile_ring[rslot] = done ? -1 : t;
+        mbar_arrive(smem_u32(&tq_full[rslot]));
+        if (++rslot == kRing) { rslot = 0; rphase ^= 1; }
+        if (done) break;
+        // the following tile, taken now and used once this one's copies are issued
+        const int t_next = (int)gridDim.x + atomicAdd(tile_ctr, 1);
         const TcTile tile = tiles[t];
+        t = t_next;
         if (!active(tile)) continue;
         const uint8_t* bufs[4] = {b0, b1, b2, b3};
         if (ptrs) {
@@ -302,12 +361,15 @@ tc_gemm_kernel(const TcTile* __restrict__ tiles, int ntiles, const TcJob* __rest
           bufs[3] = gemm_stage == 2 ? pt.inter : nullptr;
         }
         const TcJob job = jobs[tile.job];
+        int kbase = 0;  // K tiles of the job's earlier segments
         for (int si = job.seg_begin; si < job.seg_end && !abort_flag; ++si) {
           const TcSeg sg = segs[si];
+          const int k_lo = max(tile.kb - kbase, 0), k_hi = min(tile.ke - kbase, sg.nkt);
+          kbase += sg.nkt;
           const uint8_t* P = bufs[sg.p_buf] + sg.p_off + (int64_t)tile.mt * sg.p_nkt * kStageA;
           const uint8_t* Q = bufs[sg.q_buf] + sg.q_off + (int64_t)tile.nt * sg.q_nkt * kStageA;
           const bool wide = WIDE && tile.wide;
-          for (int kt = 0; kt < sg.nkt; ++kt) {
+          for (int kt = k_lo; kt < k_hi; ++kt) {
             if (!mbar_wait(smem_u32(&empty_bar[stage]), phase ^ 1, &abort_flag, gerr, 1)) break;
             const uint32_t sa = smem_u32(smem + stage * kStage);
             const uint32_t fb = smem_u32(&full_bar[stage]);
@@ -352,18 +414,25 @@ tc_gemm_kernel(const TcTile* __restrict__ tiles, int ntiles, const TcJob* __rest
       bool any = false;
       constexpr uint32_t idesc128 = instr_desc<TF32, 128>();
       constexpr uint32_t idesc256 = instr_desc<TF32, 256>();
-      for (int t = blockIdx.x; t < ntiles && !abort_flag; t += gridDim.x) {
-        if (!active(tiles[t])) continue;
-        const TcJob job = jobs[tiles[t].job];
-        if (job.seg_begin == job.seg_end) continue;
-        const uint32_t idesc = (WIDE && tiles[t].wide) ? idesc256 : idesc128;
+      int rslot = 0;
+      uint32_t rphase = 0;
+      while (!abort_flag) {
+        const int t = next_tile(rslot, rphase, false, 6);
+        if (t < 0) break;
+        const TcTile tile = tiles[t];
+        if (!active(tile) || tile.kb >= tile.ke) continue;
+        const TcJob job = jobs[tile.job];
+        const uint32_t idesc = (WIDE && tile.wide) ? idesc256 : idesc128;
         if (!mbar_wait(smem_u32(&tempty_bar[acc]), acc_phase ^ 1, &abort_flag, gerr, 2)) break;
         tc_fence_after();
         const uint32_t d_tmem = tmem_base + (uint32_t)(acc * kAccCols);
         uint32_t accumulate = 0;
+        int kbase = 0;
         for (int si = job.seg_begin; si < job.seg_end && !abort_flag; ++si) {
           const int nkt = segs[si].nkt;
-          for (int kt = 0; kt < nkt; ++kt) {
+          const int k_lo = max(tile.kb - kbase, 0), k_hi = min(tile.ke - kbase, nkt);
+          kbase += nkt;
+          for (int kt = k_lo; kt < k_hi; ++kt) {
             if (!mbar_wait(smem_u32(&full_bar[stage]), phase, &abort_flag, gerr, 3)) break;
             tc_fence_after();
             const uint32_t sa = smem_u32(smem + stage * kStage);
@@ -403,7 +472,11 @@ tc_gemm_kernel(const TcTile* __restrict__ tiles, int ntiles, const TcJob* __rest
     const int row = quarter * 32 + lane;
     int acc = 0;
     uint32_t acc_phase = 0;
-    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    int rslot = 0;
+    uint32_t rphase = 0;
+    for (;;) {
+      const int t = next_tile(rslot, rphase, true, 7);
+      if (t < 0) break;
       const TcTile tile = tiles[t];
       if (!active(tile)) continue;
       uint8_t* o_img = out_img;
@@ -416,7 +489,8 @@ tc_gemm_kernel(const TcTile* __restrict__ tiles, int ntiles, const TcJob* __rest
         i_x = pt.x;
       }
       const TcJob job = jobs[tile.job];
-      const bool has = job.seg_begin < job.seg_end;
+      const bool has = tile.kb < tile.ke;
+      const bool split = tile.nparts > 1;
       if (has) {
         if (!mbar_wait(smem_u32(&tfull_bar[acc]), acc_phase, &abort_flag, gerr, 4)) break;
         tc_fence_after();
@@ -432,7 +506,15 @@ tc_gemm_kernel(const TcTile* __restrict__ tiles, int ntiles, const TcJob* __rest
           for (int j = 0; j < 32; ++j) v[j] = 0u;
         }
         const int n0 = tile.nt * kRows + c0;
-        if (job.out_fp64) {
+        if (split) {
+          // FP32 partial sums of this part: slot, 32-column group, row, 32 values
+          float4* dst = reinterpret_cast<float4*>(
+              partial + (int64_t)(tile.red + tile.part) * kRows * 256 + (c0 >> 5) * kRows * 32 + row * 32);
+#pragma unroll
+          for (int j = 0; j < 8; ++j)
+            dst[j] = make_float4(__uint_as_float(v[4 * j]), __uint_as_float(v[4 * j + 1]),
+                                 __uint_as_float(v[4 * j + 2]), __uint_as_float(v[4 * j + 3]));
+        } else if (job.out_fp64) {
           if (m < job.M) {
             double* yr = o_y + job.out_off + m * job.N;
             const double* xr = i_x + job.x_off + m * job.N;
@@ -509,6 +591,53 @@ tc_gemm_kernel(const TcTile* __restrict__ tiles, int ntiles, const TcJob* __rest
                  "r"(kTmemCols)
                  : "memory");
   }
+  if (threadIdx.x == 0) {
+    // every CTA has taken its last tile: the last one to finish zeroes the tile counter
+    // for the next launch
+    __threadfence();
+    if (atomicAdd(tile_ctr + 1, 1) == (int)gridDim.x - 1) {
+      atomicExch(tile_ctr, 0);
+      atomicExch(tile_ctr + 1, 0);
+    }
+  }
+}
+
+// Split K: sums the FP32 partial sums of each split tile in part order (slots red ..
+// red + nparts - 1, laid out [32-column group][row][32]) and writes FP64 Y plus the
+// identity-identity term.  32 CTAs of 256 threads per split tile, 4 values per thread.
+__global__ void __launch_bounds__(256)
+split_reduce_kernel(const TcTile* __restrict__ groups, const TcJob* __restrict__ jobs,
+                    const float* __restrict__ partial, double* __restrict__ y,
+                    const double* __restrict__ x) {
+  const TcTile g = groups[blockIdx.x >> 5];
+  const TcJob job = jobs[g.job];
+  const int idx = (((int)blockIdx.x & 31) * 256 + (int)threadIdx.x) * 4;
+  const int grp = idx >> 12, row = (idx >> 5) & (kRows - 1), col = idx & 31;
+  if (grp * 32 >= (g.wide ? 256 : 128)) return;
+  const int64_t m = (int64_t)g.mt * kRows + row;
+  if (m >= job.M) return;
+  const float* src = partial + (int64_t)g.red * (kRows * 256) + idx;
+  float4 s = __ldcg(reinterpret_cast<const float4*>(src));
+  for (int p = 1; p < g.nparts; ++p) {
+    const float4 q = __ldcg(reinterpret_cast<const float4*>(src + (int64_t)p * (kRows * 256)));
+    s.x += q.x;
+    s.y += q.y;
+    s.z += q.z;
+    s.w += q.w;
+  }
+  const float v[4] = {s.x, s.y, s.z, s.w};
+  const int n0 = g.nt * kRows + grp * 32 + col;
+  double* yr = y + job.out_off + m * job.N;
+  const double* xr = x + job.x_off + m * job.N;
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    const int n = n0 + e;
+    if (n < job.N) {
+      double val = f32_to_f64(v[e]);  // exact, integer ops
+      if (job.axpy != 0.0) val = fma(job.axpy, xr[n], val);
+      yr[n] = val;
+    }
+  }
 }
 
 template <int PLANES, int STAGES, bool TF32, bool WIDE>
@@ -555,6 +684,9 @@ void free_tc(TcPlan* t) {
   cudaFree(t->d_xpack_chunks);
   cudaFree(t->d_jobs);
   cudaFree(t->d_segs);
+  cudaFree(t->d_ctr);
+  cudaFree(t->d_partial);
+  for (TcTile* d : t->d_groups) cudaFree(d);
   for (auto& st : t->d_tiles)
     for (TcTile* d : st) cudaFree(d);
   delete t;
@@ -580,6 +712,18 @@ bool tc_tiles_in_range(const TcPlan* t, int64_t n, const std::vector<TcJob>& job
   auto bytes = [&](int b) { return (int64_t)t->buf_bytes[b == TB_XB ? TB_XA : b]; };
   for (const TcTile& tl : tiles) {
     const TcJob& j = jobs[tl.job - job_base];
+    int64_t job_kt = 0;
+    for (int si = j.seg_begin; si < j.seg_end; ++si) job_kt += segs[si - seg_base].nkt;
+    if (tl.kb < 0 || tl.ke < tl.kb || tl.ke > job_kt) {
+      snprintf(why, why_len, "tile (job %d, %d, %d) has K range [%d, %d) outside 0..%lld",
+               tl.job, tl.mt, tl.nt, tl.kb, tl.ke, (long long)job_kt);
+      return false;
+    }
+    if (tl.nparts < 1 || (tl.nparts > 1 && (!j.out_fp64 || tl.part < 0 || tl.part >= tl.nparts || tl.red < 0 ||
+                          (int64_t)tl.red + tl.nparts > t->nslots))) {
+      snprintf(why, why_len, "tile (job %d, %d, %d) has bad split-K fields", tl.job, tl.mt, tl.nt);
+      return false;
+    }
     for (int si = j.seg_begin; si < j.seg_end; ++si) {
       const TcSeg& sg = segs[si - seg_base];
       const int64_t pe = sg.p_off + ((int64_t)tl.mt * sg.p_nkt + sg.nkt) * stageA;
@@ -790,13 +934,53 @@ dmrg_status build_tc(dmrg_plan* p, dmrg_precision prec, cudaStream_t st, TcPlan*
     const int nm = ceil_div(j.M, kRows), nn = ceil_div(j.N, kRows);
     const bool may_wide = !tf32 && (wpol == 2 || (wpol == 1 && 4 * job_cost[jb] <= mean_work[cur_stage]));
     auto width = [&](int nt) { return (may_wide && nt + 1 < nn) ? 2 : 1; };
+    const int ke = (int)job_cost[jb];
     if (col_major) {
       for (int nt = 0; nt < nn; nt += width(nt))
-        for (int mt = 0; mt < nm; ++mt) dst.push_back(TcTile{jb, mt, nt, 0, width(nt) - 1});
+        for (int mt = 0; mt < nm; ++mt) dst.push_back(make_tile(jb, mt, nt, 0, width(nt) - 1, 0, ke));
     } else {
       for (int mt = 0; mt < nm; ++mt)
-        for (int nt = 0; nt < nn; nt += width(nt)) dst.push_back(TcTile{jb, mt, nt, 0, width(nt) - 1});
+        for (int nt = 0; nt < nn; nt += width(nt)) dst.push_back(make_tile(jb, mt, nt, 0, width(nt) - 1, 0, ke));
     }
+  };
+  // estimated time of a tile in thirds of a 128-column K step: a 256-column K step takes
+  // about 1.3 times as long (measured on GB300; the 128-column step waits on its operand
+  // copies, the 256-column one is close to the MMA rate)
+  auto tile_cost = [](const TcTile& tl) { return (int64_t)(tl.ke - tl.kb) * (tl.wide ? 4 : 3); };
+  auto by_tile_cost = [&](std::vector<TcTile>& v) {
+    std::stable_sort(v.begin(), v.end(), [&](const TcTile& a, const TcTile& b) {
+      return tile_cost(a) > tile_cost(b);
+    });
+  };
+  // K split of the FP64-output tiles estimated above num / den of the mean time per SM
+  int64_t slots_used = 0;
+  auto split_k = [&](const std::vector<TcTile>& src, int num, int den) {
+    int64_t total = 0;
+    for (const TcTile& tl : src) total += tile_cost(tl);
+    const int64_t cap = std::max<int64_t>(1, total * num / den / std::max(1, t->sms));
+    std::vector<TcTile> res;
+    int64_t slot = 0;
+    for (const TcTile& tl : src) {
+      const int nk = tl.ke - tl.kb;
+      const int64_t c = tile_cost(tl);
+      const int np = (int)std::min<int64_t>({(c + cap - 1) / cap, (int64_t)nk, 8});
+      if (!jobs[tl.job].out_fp64 || np < 2) {
+        res.push_back(tl);
+        continue;
+      }
+      for (int q = 0; q < np; ++q) {
+        TcTile pt = tl;
+        pt.kb = tl.kb + (int)((int64_t)nk * q / np);
+        pt.ke = tl.kb + (int)((int64_t)nk * (q + 1) / np);
+        pt.part = q;
+        pt.nparts = np;
+        pt.red = (int)slot;
+        res.push_back(pt);
+      }
+      slot += np;
+    }
+    slots_used = std::max(slots_used, slot);
+    return res;
   };
   // jobs (already in descending cost) grouped by key; groups in descending total cost
   auto grouped = [&](const std::vector<std::pair<int64_t, int>>& order,
@@ -829,18 +1013,25 @@ dmrg_status build_tc(dmrg_plan* p, dmrg_precision prec, cudaStream_t st, TcPlan*
   };
   std::vector<int> job_pair(jobs.size(), -1);
   for (int q = 0; q < npairs; ++q) job_pair[stage2_job[q]] = q;
-  t->nsched = tf32 ? kOrders : kSchedules;
-  for (int c = 0; c < t->nsched; ++c) {
-    wpol = c / kOrders;
-    const int o = c % kOrders;
-    cur_stage = 0;
-    if (o == 0) for (const auto& pr : order1) add_tiles(sched1[c], pr.second, false);
-    if (o == 1) sched1[c] = grouped(order1, x_key, true);
-    if (o == 2) sched1[c] = grouped(order1, op_key, false);
+  for (int c = 0; c < kSchedules; ++c) {
+    const int o = c % kOrders, w = (c / kOrders) % kWidths, sp = c / (kOrders * kWidths);
+    t->valid[0][c] = sp == 0 && (!tf32 || w == 0);
+    t->valid[1][c] = !tf32 || w == 0;
+    if (!t->valid[1][c]) continue;
+    wpol = w;
+    if (sp == 0) {
+      cur_stage = 0;
+      if (o == 0) for (const auto& pr : order1) add_tiles(sched1[c], pr.second, false);
+      if (o == 1) sched1[c] = grouped(order1, x_key, true);
+      if (o == 2) sched1[c] = grouped(order1, op_key, false);
+      if (o == 0) by_tile_cost(sched1[c]);
+    }
     cur_stage = 1;
     if (o == 0) for (const auto& pr : order2) add_tiles(sched2[c], pr.second, false);
     if (o == 1) sched2[c] = grouped(order2, [&](int jb) { return (int64_t)p->pair_k[job_pair[jb]]; }, false);
     if (o == 2) sched2[c] = grouped(order2, [&](int jb) { return (int64_t)p->pair_i[job_pair[jb]]; }, false);
+    if (sp > 0) sched2[c] = split_k(sched2[c], 2, sp == 1 ? 3 : 5);
+    if (o == 0) by_tile_cost(sched2[c]);
   }
   tiles1 = sched1[0];
   tiles2 = sched2[0];
@@ -867,9 +1058,20 @@ dmrg_status build_tc(dmrg_plan* p, dmrg_precision prec, cudaStream_t st, TcPlan*
     p->device_bytes += t->buf_bytes[b];
   }
   t->buf[TB_XB] = t->buf[TB_XA];  // alias: B-form offsets follow the A-form tiles
+  // tile-list counters and the split-K scratch
+  t->nslots = slots_used;
+  if (cudaMalloc((void**)&t->d_ctr, 4 * sizeof(int)) != cudaSuccess ||
+      (t->nslots > 0 &&
+       cudaMalloc((void**)&t->d_partial, sizeof(float) * kSlotFloats * (size_t)t->nslots) != cudaSuccess)) {
+    cudaGetLastError();
+    set_error("cudaMalloc of the tile counters or the split-K scratch failed");
+    return fail(DMRG_ERR_OOM);
+  }
+  p->device_bytes += 4 * sizeof(int) + sizeof(float) * kSlotFloats * t->nslots;
+  DMRG_CUDA_TRY(cudaMemsetAsync(t->d_ctr, 0, 4 * sizeof(int), st));
   {
     char why[160];
-    for (int c = 0; c < t->nsched; ++c) {
+    for (int c = 0; c < kSchedules; ++c) {
       if (!tc_tiles_in_range(t, p->n, jobs, segs, sched1[c], 0, 0, why, sizeof(why)) ||
           !tc_tiles_in_range(t, p->n, jobs, segs, sched2[c], 0, 0, why, sizeof(why))) {
         set_error("internal: %s", why);
@@ -904,9 +1106,14 @@ dmrg_status build_tc(dmrg_plan* p, dmrg_precision prec, cudaStream_t st, TcPlan*
   t->n_xpack_chunks = (int64_t)x_chunks.size();
   if ((s = upload_vec(&t->d_jobs, jobs, st)) != DMRG_OK) return fail(s);
   if ((s = upload_vec(&t->d_segs, segs, st)) != DMRG_OK) return fail(s);
-  for (int c = 0; c < t->nsched; ++c) {
+  for (int c = 0; c < kSchedules; ++c) {
     if ((s = upload_vec(&t->d_tiles[0][c], sched1[c], st)) != DMRG_OK) return fail(s);
     if ((s = upload_vec(&t->d_tiles[1][c], sched2[c], st)) != DMRG_OK) return fail(s);
+    std::vector<TcTile> groups;
+    for (const TcTile& tl : sched2[c])
+      if (tl.nparts > 1 && tl.part == 0) groups.push_back(tl);
+    if ((s = upload_vec(&t->d_groups[c], groups, st)) != DMRG_OK) return fail(s);
+    t->ngroups[c] = (int64_t)groups.size();
     t->ntiles[0][c] = (int64_t)sched1[c].size();
     t->ntiles[1][c] = (int64_t)sched2[c].size();
   }
@@ -965,8 +1172,13 @@ dmrg_status run_tc_part(dmrg_plan* p, TcPlan* t, const double* x, double* y, int
   tc::tc_gemm_kernel<PLANES, STAGES, TF32, WIDE><<<grid, tc::kThreads, smem, st>>>(
       t->d_tiles[part - 1][c], (int)nt, t->d_jobs, t->d_segs, t->buf[TB_OPS], t->buf[TB_XA],
       t->buf[TB_XB], part == 1 ? nullptr : t->buf[TB_INTER], part == 1 ? t->buf[TB_INTER] : nullptr,
-      y, x, t->d_err, nullptr, part);
+      y, x, t->d_err, nullptr, part, t->d_ctr + 2 * (part - 1), t->d_partial);
   DMRG_LAUNCH_CHECK();
+  if (part == 2 && t->ngroups[c] > 0) {
+    tc::split_reduce_kernel<<<(unsigned)(t->ngroups[c] * 32), 256, 0, st>>>(
+        t->d_groups[c], t->d_jobs, t->d_partial, y, x);
+    DMRG_LAUNCH_CHECK();
+  }
   return DMRG_OK;
 }
 
@@ -1010,7 +1222,9 @@ dmrg_status tune_tc(dmrg_plan* p, TcPlan* t, const double* x, double* y, cudaStr
   for (int part = 1; part <= 2 && s == DMRG_OK; ++part) {
     float best = 0.0f;
     int arg = 0;
-    for (int c = 0; c < t->nsched && s == DMRG_OK; ++c) {
+    bool first = true;
+    for (int c = 0; c < kSchedules && s == DMRG_OK; ++c) {
+      if (!t->valid[part - 1][c]) continue;
       float ms[3] = {0.0f, 0.0f, 0.0f};
       s = run_tc_part<PLANES, STAGES, TF32>(p, t, x, y, part, c, st);
       for (int r = 0; r < 3 && s == DMRG_OK; ++r) {
@@ -1031,9 +1245,10 @@ dmrg_status tune_tc(dmrg_plan* p, TcPlan* t, const double* x, double* y, cudaStr
       if (s != DMRG_OK) break;
       std::sort(ms, ms + 3);
       t->tune_us[part - 1][c] = ms[1] * 1000.0f;
-      if (c == 0 || ms[1] < best) {
+      if (first || ms[1] < best) {
         best = ms[1];
         arg = c;
+        first = false;
       }
     }
     t->sched[part - 1] = arg;
@@ -1067,6 +1282,7 @@ struct TcBatch {
   PackChunk* d_pchunks = nullptr;
   int64_t nchunks = 0;
   TcPtrs* d_ptrs = nullptr;
+  int* d_ctr = nullptr;                     // tile-list counters, 2 per stage
   TcPtrs* h_ptrs[2] = {nullptr, nullptr};   // pinned ring: slot r reused after ev[r]
   cudaEvent_t ev[2] = {nullptr, nullptr};
   int slot = 0;
@@ -1084,6 +1300,7 @@ void tc_batch_destroy(TcBatch* b) {
   cudaFree(b->d_pjobs);
   cudaFree(b->d_pchunks);
   cudaFree(b->d_ptrs);
+  cudaFree(b->d_ctr);
   for (int r = 0; r < 2; ++r) {
     if (b->ev[r]) {
       cudaEventSynchronize(b->ev[r]);
@@ -1159,7 +1376,7 @@ dmrg_status tc_batch_create(dmrg_plan* const* plans, int nb, dmrg_precision prec
       for (int mt = 0; mt < ceil_div(j.M, kRows); ++mt)
         for (int nt = 0; nt < nn;) {
           const int w = (wide_tiles && nt + 1 < nn) ? 2 : 1;
-          tiles[g].push_back(TcTile{it.job, mt, nt, it.prob, w - 1});
+          tiles[g].push_back(make_tile(it.job, mt, nt, it.prob, w - 1, 0, (int)it.cost));
           nt += w;
         }
     }
@@ -1185,7 +1402,10 @@ dmrg_status tc_batch_create(dmrg_plan* const* plans, int nb, dmrg_precision prec
         j.seg_begin -= seg_base[i];
         j.seg_end -= seg_base[i];
         std::vector<TcJob> one(1, j);
-        std::vector<TcTile> onet(1, TcTile{0, tl.mt, tl.nt, 0, tl.wide});
+        TcTile one_tile = tl;
+        one_tile.job = 0;
+        one_tile.pad_ = 0;
+        std::vector<TcTile> onet(1, one_tile);
         if (j.seg_begin < 0 || j.seg_end > (int)t->h_segs.size() ||
             !tc_tiles_in_range(t, plans[i]->n, one, t->h_segs, onet, 0, 0, why, sizeof(why))) {
           set_error("internal: grouped launch, problem %d: %s", i, why);
@@ -1209,6 +1429,7 @@ dmrg_status tc_batch_create(dmrg_plan* const* plans, int nb, dmrg_precision prec
   if ((e = upload_vec(&b->d_pchunks, pchunks, st)) != DMRG_OK) return fail(e);
   b->nchunks = (int64_t)pchunks.size();
   if (cudaMalloc((void**)&b->d_ptrs, sizeof(TcPtrs) * std::max(nb, 1)) != cudaSuccess ||
+      cudaMalloc((void**)&b->d_ctr, 4 * sizeof(int)) != cudaSuccess ||
       cudaHostAlloc((void**)&b->h_ptrs[0], sizeof(TcPtrs) * std::max(nb, 1), cudaHostAllocDefault) != cudaSuccess ||
       cudaHostAlloc((void**)&b->h_ptrs[1], sizeof(TcPtrs) * std::max(nb, 1), cudaHostAllocDefault) != cudaSuccess ||
       cudaEventCreateWithFlags(&b->ev[0], cudaEventDisableTiming) != cudaSuccess ||
@@ -1220,6 +1441,7 @@ dmrg_status tc_batch_create(dmrg_plan* const* plans, int nb, dmrg_precision prec
     return fail(DMRG_ERR_OOM);
   }
   *b->h_err = 0;
+  DMRG_CUDA_TRY(cudaMemsetAsync(b->d_ctr, 0, 4 * sizeof(int), st));
   DMRG_CUDA_TRY(cudaStreamSynchronize(st));
   *out = b;
   return DMRG_OK;
@@ -1250,7 +1472,7 @@ dmrg_status run_batch(TcBatch* b, cudaStream_t st) {
     const int grid = (int)std::min<int64_t>(nt, b->sms);
     tc::tc_gemm_kernel<PLANES, STAGES, TF32, WIDE><<<grid, tc::kThreads, smem, st>>>(
         b->d_tiles[part - 1], (int)nt, b->d_jobs, b->d_segs, nullptr, nullptr, nullptr, nullptr,
-        nullptr, nullptr, nullptr, b->d_err, b->d_ptrs, part);
+        nullptr, nullptr, nullptr, b->d_err, b->d_ptrs, part, b->d_ctr + 2 * (part - 1), nullptr);
     DMRG_LAUNCH_CHECK();
   }
   return DMRG_OK;
@@ -1347,6 +1569,29 @@ dmrg_status tune_project_tc(dmrg_plan* p, dmrg_precision prec, cudaStream_t st) 
                                          : tune_tc<3, 3, false>(p, t, p->D, y, st);
   cudaFreeAsync(y, st);
   return s;
+}
+
+dmrg_status set_schedule_tc(dmrg_plan* p, dmrg_precision prec, int stage1, int stage2,
+                            cudaStream_t st) {
+  const int slot = prec == DMRG_PREC_TF32 ? 0 : 1;
+  if (!p->tc[slot]) {
+    TcPlan* t = nullptr;
+    DMRG_TRY(build_tc(p, prec, st, &t));
+    p->tc[slot] = t;
+  }
+  TcPlan* t = p->tc[slot];
+  const int want[2] = {stage1, stage2};
+  for (int g = 0; g < 2; ++g) {
+    if (want[g] < 0 || want[g] >= kSchedules || !t->valid[g][want[g]]) {
+      set_error("tile schedule %d is not a candidate of GEMM stage %d in this precision",
+                want[g], g + 1);
+      return DMRG_ERR_INVALID_ARG;
+    }
+  }
+  t->sched[0] = stage1;
+  t->sched[1] = stage2;
+  t->tuned = true;  // fixed: the first projection does not autotune
+  return DMRG_OK;
 }
 
 void tc_schedule_stats(const dmrg_plan* p, int32_t sched[2], float us[2][DMRG_TILE_SCHEDULES]) {

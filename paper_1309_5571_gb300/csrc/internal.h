@@ -146,6 +146,8 @@ dmrg_status launch_project_tc(dmrg_plan* plan, dmrg_precision prec, const double
                               double* y, cudaStream_t stream);
 // builds the tensor-core plan of prec if needed and times its tile schedules
 dmrg_status tune_project_tc(dmrg_plan* plan, dmrg_precision prec, cudaStream_t stream);
+dmrg_status set_schedule_tc(dmrg_plan* plan, dmrg_precision prec, int stage1, int stage2,
+                            cudaStream_t stream);
 // chosen schedule per GEMM stage (-1: no tensor-core plan) and the tuning times (us)
 void tc_schedule_stats(const dmrg_plan* plan, int32_t sched[2], float us[2][DMRG_TILE_SCHEDULES]);
 // grouped launch of the low-precision projections of several distinct plans

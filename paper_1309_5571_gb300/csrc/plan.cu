@@ -529,6 +529,23 @@ dmrg_status dmrg_plan_autotune(dmrg_plan* p, dmrg_precision prec, void* stream) 
   return DMRG_OK;
 }
 
+dmrg_status dmrg_plan_set_tile_schedule(dmrg_plan* p, dmrg_precision prec, int32_t stage1,
+                                        int32_t stage2, void* stream) {
+  if (!p) {
+    set_error("NULL plan");
+    return DMRG_ERR_INVALID_ARG;
+  }
+  if (prec != DMRG_PREC_TF32 && prec != DMRG_PREC_BF16X3) {
+    set_error("tile schedule: precision must be DMRG_PREC_TF32 or DMRG_PREC_BF16X3");
+    return DMRG_ERR_INVALID_ARG;
+  }
+  if (p->n == 0) return DMRG_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  DMRG_TRY(set_schedule_tc(p, prec, stage1, stage2, st));
+  DMRG_CUDA_TRY(cudaStreamSynchronize(st));
+  return DMRG_OK;
+}
+
 dmrg_status dmrg_diagonal(dmrg_plan* p, double* d, void* stream) {
   if (!p || (!d && p->n)) {
     set_error("NULL argument");

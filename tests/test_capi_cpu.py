@@ -114,3 +114,40 @@ def test_gemv_trans_argument_checks(lib):
     buf = (C.c_double * 4)()
     assert lib.dmrg_gemv_trans(buf, 1, 4, 1, buf, buf, None) == 1     # ldv < n
     assert lib.dmrg_gemv_trans(buf, 4, 4, 25, buf, buf, None) == 1    # k > 24
+
+
+def test_schedule_calls_check_arguments(lib):
+    # NULL plan and precisions without tile schedules are rejected on the host
+    assert lib.dmrg_plan_set_tile_schedule(None, 2, 0, 0, None) == 1
+    assert lib.dmrg_plan_autotune(None, 2, None) == 1
+
+
+def test_binding_structs_match_the_header(tmp_path):
+    # the ctypes mirrors have the size and field offsets that a C compiler gives the
+    # header's structs (compiled with the host C compiler, no GPU)
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no host C compiler")
+    pairs = [(capi.Block, "dmrg_block"), (capi.Operator, "dmrg_operator"),
+             (capi.Term, "dmrg_term"), (capi.SuperblockDesc, "dmrg_superblock_desc"),
+             (capi.Options, "dmrg_options"), (capi.SolveInfo, "dmrg_solve_info"),
+             (capi.PlanStats, "dmrg_plan_stats")]
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "dmrg.h"', "int main(void) {",
+             '  printf("%d\\n", (int)DMRG_TILE_SCHEDULES);']
+    expect = [str(capi.TILE_SCHEDULES)]
+    for cls, cname in pairs:
+        lines.append(f'  printf("%zu\\n", sizeof({cname}));')
+        expect.append(str(C.sizeof(cls)))
+        for f, _ in cls._fields_:
+            lines.append(f'  printf("%zu\\n", offsetof({cname}, {f}));')
+            expect.append(str(getattr(cls, f).offset))
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "abi.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "abi"
+    subprocess.run([cc, "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                   check=True)
+    got = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()
+    assert got == expect

@@ -70,24 +70,73 @@ def test_mixed_davidson_matches_oracle(name, prec):
     assert info["fp64_projections"] >= 1 and info["projections"] >= 1
 
 
+NSCHED = capi.TILE_SCHEDULES  # (3 s + w) 3 + o: K split s, tile width w, order o
+
+
+def candidates(prec, stage):
+    """Tile schedules of a GEMM stage: stage 1 takes no K split, TF32 only 128-column tiles."""
+    return [c for c in range(NSCHED)
+            if (stage == 2 or c // 9 == 0) and (prec == "bf16x3" or (c // 3) % 3 == 0)]
+
+
 @pytest.mark.parametrize("prec", ["bf16x3", "tf32"])
-def test_autotuned_schedule_gives_identical_projection(prec):
-    # every tile schedule computes each output tile in the same CTA arithmetic, so the
-    # tuned plan and the untuned (descending-cost) plan agree bit for bit
+def test_autotuned_schedule(prec):
+    # the tuner times exactly the candidates of each stage and keeps one of them; schedules
+    # without a K split compute every output element in the same CTA arithmetic, so the
+    # tuned plan agrees with the untuned one bit for bit unless stage 2 took a split
     sb = problem("ragged")
-    x = cuda(np.random.default_rng(11).standard_normal(sb.n))
+    xh = np.random.default_rng(11).standard_normal(sb.n)
+    x = cuda(xh)
     fixed = Plan(sb, prec=prec, autotune=False)
     y0 = fixed.project(x).cpu().numpy()
     assert fixed.get_stats()["tc_schedule"] == [0, 0]
     tuned = Plan(sb, prec=prec)
     st = tuned.autotune(prec)
-    ncand = 9 if prec == "bf16x3" else 3  # TF32 tiles are always 128 wide
-    assert all(0 <= c < ncand for c in st["tc_schedule"])
-    assert all(t > 0 for row in st["tc_tune_us"] for t in row[:ncand])
+    for g in (0, 1):
+        cand = candidates(prec, g + 1)
+        assert st["tc_schedule"][g] in cand
+        assert all((t > 0) == (c in cand) for c, t in enumerate(st["tc_tune_us"][g]))
     y1 = tuned.project(x).cpu().numpy()
-    np.testing.assert_array_equal(y0, y1)
-    # tuning on first use, inside the projection call, gives the same values
-    np.testing.assert_array_equal(y0, Plan(sb, prec=prec).project(x).cpu().numpy())
+    assert rel_err(y1, oproj.project_blocks(sb, xh)) <= TOL[prec]
+    if st["tc_schedule"][1] < 9:
+        np.testing.assert_array_equal(y0, y1)
+    # tuning on first use, inside the projection call, picks a candidate too
+    p2 = Plan(sb, prec=prec)
+    assert rel_err(p2.project(x).cpu().numpy(), oproj.project_blocks(sb, xh)) <= TOL[prec]
+    assert all(c in candidates(prec, g + 1) for g, c in enumerate(p2.get_stats()["tc_schedule"]))
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "tf32"])
+@pytest.mark.parametrize("name", ["hub_L8_m40", "ragged", "heis_L16_m64"])
+def test_every_tile_schedule_matches_oracle(name, prec):
+    # each candidate schedule of each stage (the other stage on schedule 0) against the
+    # oracle; every schedule is repeatable bit for bit, and the unsplit ones agree with
+    # schedule (0, 0) bit for bit (small problems: the K split cuts most stage-2 tiles)
+    sb = problem(name)
+    xh = np.random.default_rng(7).standard_normal(sb.n)
+    y_ref = oproj.project_blocks(sb, xh)
+    x = cuda(xh)
+    plan = Plan(sb, prec=prec, autotune=False)
+    base = plan.project(x).cpu().numpy()
+    pairs = [(c, 0) for c in candidates(prec, 1)] + [(0, c) for c in candidates(prec, 2)]
+    for s1, s2 in pairs:
+        assert plan.set_tile_schedule(s1, s2, prec=prec)["tc_schedule"] == [s1, s2]
+        y = plan.project(x).cpu().numpy()
+        assert rel_err(y, y_ref) <= TOL[prec], (s1, s2, rel_err(y, y_ref))
+        np.testing.assert_array_equal(y, plan.project(x).cpu().numpy())
+        if s2 < 9:
+            np.testing.assert_array_equal(y, base)
+
+
+def test_tile_schedule_rejects_non_candidates():
+    sb = problem("ragged")
+    plan = Plan(sb, prec="bf16x3", autotune=False)
+    for bad in ((9, 0), (-1, 0), (0, NSCHED)):
+        with pytest.raises(capi.DmrgError):
+            plan.set_tile_schedule(*bad)
+    tf = Plan(sb, prec="tf32", autotune=False)
+    with pytest.raises(capi.DmrgError):
+        tf.set_tile_schedule(0, 3, prec="tf32")   # 256-column tiles: BF16x3 only
 
 
 @pytest.mark.parametrize("name", ["heis_L16_m64", "hub_quarter_L12_m48", "ragged"])
@@ -121,6 +170,11 @@ def test_full_size_projection_hubbard_m2048_bf16x3(hub_L64_m2048):
     assert rel_err(y, y_ref) <= TOL["bf16x3"]
     y64 = plan.project(cuda(x), prec="fp64").cpu().numpy()
     assert rel_err(y64, y_ref) <= 1e-12
+    # the K-split schedules of stage 2 (both split bounds, LPT order, narrow and wide tiles)
+    for s2 in (9, 18, 24, 25):
+        plan.set_tile_schedule(4, s2)
+        ys = plan.project(cuda(x)).cpu().numpy()
+        assert rel_err(ys, y_ref) <= TOL["bf16x3"], (s2, rel_err(ys, y_ref))
 
 
 def test_full_size_mixed_solve_hubbard_m2048_properties(hub_L64_m2048):
