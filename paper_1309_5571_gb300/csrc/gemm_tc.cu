@@ -194,6 +194,7 @@ pack_kernel(const PackChunk* __restrict__ chunks, const PackJob* __restrict__ jo
   using L = Layout<TF32>;
   constexpr int EPG = TF32 ? 4 : 8;  // elements per 16-byte group
   constexpr int KT = L::KT;
+  grid_dep_wait();
   const PackChunk ch = chunks[blockIdx.x];
   if (ptrs) {  // grouped launch: the chunk's problem
     const TcPtrs& pt = ptrs[ch.pad_];
@@ -257,6 +258,7 @@ pack_kernel(const PackChunk* __restrict__ chunks, const PackJob* __restrict__ jo
       }
     }
   }
+  grid_dep_launch();
 }
 
 // ---------------------------------------------------------------- grouped GEMM kernel
@@ -318,6 +320,7 @@ tc_gemm_kernel(const TcTile* __restrict__ tiles, int ntiles, const TcJob* __rest
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem_base = tmem_slot;
+  grid_dep_wait();  // inputs of this launch are written by the previous one
   // grouped launch (ptrs != NULL): the operand buffers and outputs of each tile are those
   // of its problem (tile.pad_), and tiles of inactive problems are skipped by all roles
   auto active = [&](const TcTile& tile) { return !ptrs || ptrs[tile.pad_].active != 0; };
@@ -347,7 +350,10 @@ tc_gemm_kernel(const TcTile* __restrict__ tiles, int ntiles, const TcJob* __rest
         tile_ring[rslot] = done ? -1 : t;
         mbar_arrive(smem_u32(&tq_full[rslot]));
         if (++rslot == kRing) { rslot = 0; rphase ^= 1; }
-        if (done) break;
+        if (done) {
+          grid_dep_launch();  // no tile left to take: the next launch may be scheduled
+          break;
+        }
         // the following tile, taken now and used once this one's copies are issued
         const int t_next = (int)gridDim.x + atomicAdd(tile_ctr, 1);
         const TcTile tile = tiles[t];
@@ -609,6 +615,7 @@ __global__ void __launch_bounds__(256)
 split_reduce_kernel(const TcTile* __restrict__ groups, const TcJob* __restrict__ jobs,
                     const float* __restrict__ partial, double* __restrict__ y,
                     const double* __restrict__ x) {
+  grid_dep_wait();
   const TcTile g = groups[blockIdx.x >> 5];
   const TcJob job = jobs[g.job];
   const int idx = (((int)blockIdx.x & 31) * 256 + (int)threadIdx.x) * 4;
@@ -638,6 +645,7 @@ split_reduce_kernel(const TcTile* __restrict__ groups, const TcJob* __restrict__
       yr[n] = val;
     }
   }
+  grid_dep_launch();
 }
 
 template <int PLANES, int STAGES, bool TF32, bool WIDE>
@@ -1160,8 +1168,9 @@ dmrg_status run_tc_part(dmrg_plan* p, TcPlan* t, const double* x, double* y, int
   constexpr size_t smem = tc::smem_bytes<PLANES, STAGES, TF32, WIDE>();
   if (part == 0) {
     if (t->n_xpack_chunks > 0) {  // X -> A-form and B-form images
-      tc::pack_kernel<PLANES, TF32><<<(unsigned)t->n_xpack_chunks, 256, 0, st>>>(
-          t->d_xpack_chunks, t->d_xpack_jobs, p->arena, x, t->buf[TB_XA], nullptr);
+      DMRG_CUDA_TRY(launch_pdl(tc::pack_kernel<PLANES, TF32>, dim3((unsigned)t->n_xpack_chunks), dim3(256),
+                               0, st, (const PackChunk*)t->d_xpack_chunks, (const PackJob*)t->d_xpack_jobs,
+                               (const double*)p->arena, x, t->buf[TB_XA], (const TcPtrs*)nullptr));
       DMRG_LAUNCH_CHECK();
     }
     return DMRG_OK;
@@ -1169,14 +1178,17 @@ dmrg_status run_tc_part(dmrg_plan* p, TcPlan* t, const double* x, double* y, int
   const int64_t nt = t->ntiles[part - 1][c];
   if (nt == 0) return DMRG_OK;
   const int grid = (int)std::min<int64_t>(nt, t->sms);
-  tc::tc_gemm_kernel<PLANES, STAGES, TF32, WIDE><<<grid, tc::kThreads, smem, st>>>(
-      t->d_tiles[part - 1][c], (int)nt, t->d_jobs, t->d_segs, t->buf[TB_OPS], t->buf[TB_XA],
-      t->buf[TB_XB], part == 1 ? nullptr : t->buf[TB_INTER], part == 1 ? t->buf[TB_INTER] : nullptr,
-      y, x, t->d_err, nullptr, part, t->d_ctr + 2 * (part - 1), t->d_partial);
+  DMRG_CUDA_TRY(launch_pdl(
+      tc::tc_gemm_kernel<PLANES, STAGES, TF32, WIDE>, dim3(grid), dim3(tc::kThreads), smem, st,
+      (const TcTile*)t->d_tiles[part - 1][c], (int)nt, (const TcJob*)t->d_jobs, (const TcSeg*)t->d_segs,
+      (const uint8_t*)t->buf[TB_OPS], (const uint8_t*)t->buf[TB_XA], (const uint8_t*)t->buf[TB_XB],
+      (const uint8_t*)(part == 1 ? nullptr : t->buf[TB_INTER]), part == 1 ? t->buf[TB_INTER] : nullptr, y, x,
+      t->d_err, (const TcPtrs*)nullptr, part, t->d_ctr + 2 * (part - 1), t->d_partial));
   DMRG_LAUNCH_CHECK();
   if (part == 2 && t->ngroups[c] > 0) {
-    tc::split_reduce_kernel<<<(unsigned)(t->ngroups[c] * 32), 256, 0, st>>>(
-        t->d_groups[c], t->d_jobs, t->d_partial, y, x);
+    DMRG_CUDA_TRY(launch_pdl(tc::split_reduce_kernel, dim3((unsigned)(t->ngroups[c] * 32)), dim3(256), 0, st,
+                             (const TcTile*)t->d_groups[c], (const TcJob*)t->d_jobs,
+                             (const float*)t->d_partial, y, x));
     DMRG_LAUNCH_CHECK();
   }
   return DMRG_OK;

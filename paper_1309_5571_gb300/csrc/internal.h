@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "dmrg.h"
@@ -37,6 +38,36 @@ void note_launch();
     ::dmrg::note_launch();                   \
     DMRG_CUDA_TRY(cudaGetLastError());       \
   } while (0)
+
+#ifdef __CUDACC__
+// Programmatic dependent launch, device side: wait until the grids this one depends on have
+// completed and their writes are visible (returns at once for a grid launched without the
+// attribute); allow the next grid in the stream to be scheduled (it still waits for this
+// one to complete before it reads anything).
+__device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void grid_dep_launch() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+#endif
+
+// Launch with programmatic dependent launch allowed: the kernel may be scheduled while the
+// previous kernel in the stream is finishing, so it must execute griddepcontrol.wait before
+// it touches memory that earlier work writes (every kernel launched this way does so first).
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                       cudaStream_t st, Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
 
 // ---------------------------------------------------------------- operand addressing
 // Operands of the FP64 projection GEMMs are addressed relative to one of four base

@@ -35,6 +35,11 @@ def test_batched_equals_one_by_one(prec):
     sbs = _mixed_bag()
     plans = [Plan(sb, prec=prec) for sb in sbs]
     x0s = [torch.from_numpy(warmup.start_vector(sb.n, seed=i)).cuda() for i, sb in enumerate(sbs)]
+    if prec == "bf16x3":
+        # the grouped launch takes no K split; neither does this schedule (a split changes
+        # the FP32 summation order; every unsplit schedule gives the same bits)
+        for p in plans:
+            p.set_tile_schedule(0, 0)
     xs, infos = solve_batched(plans, x0s)
     for p, x0, x, info in zip(plans, x0s, xs, infos):
         x1, info1 = p.solve(x0)
@@ -50,6 +55,7 @@ def test_batched_problems_sharing_a_plan_stay_ordered():
     sb = warmup.warmup_superblock("heisenberg", 24, m=64)
     plan = Plan(sb, prec="bf16x3")
     x0s = [torch.from_numpy(warmup.start_vector(sb.n, seed=i)).cuda() for i in range(6)]
+    plan.set_tile_schedule(0, 0)  # the same tile schedule in both runs
     xs, infos = solve_batched([plan] * 6, x0s)
     for x0, x, info in zip(x0s, xs, infos):
         x1, info1 = plan.solve(x0)
