@@ -501,80 +501,107 @@ tc_gemm_kernel(const TcTile* __restrict__ tiles, int ntiles, const TcJob* __rest
         if (!mbar_wait(smem_u32(&tfull_bar[acc]), acc_phase, &abort_flag, gerr, 4)) break;
         tc_fence_after();
       }
-      const int64_t m = (int64_t)tile.mt * kRows + row;
       const int ncols = (WIDE && tile.wide) ? 256 : 128;
-      for (int c0 = 0; c0 < ncols; c0 += 32) {
-        uint32_t v[32];
-        if (has) {
-          tmem_ld32(tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(acc * kAccCols + c0), v);
-        } else {
+      if (job.out_fp64) {
+        // FP64 Y (or the FP32 partial sums of a split part) from 16-lane TMEM loads: four
+        // consecutive threads hold eight consecutive columns of one row, so each store
+        // instruction writes 64-byte row segments instead of one element of 32 rows
+        for (int c0 = 0; c0 < ncols; c0 += 32) {
 #pragma unroll
-          for (int j = 0; j < 32; ++j) v[j] = 0u;
-        }
-        const int n0 = tile.nt * kRows + c0;
-        if (split) {
-          // FP32 partial sums of this part: slot, 32-column group, row, 32 values
-          float4* dst = reinterpret_cast<float4*>(
-              partial + (int64_t)(tile.red + tile.part) * kRows * 256 + (c0 >> 5) * kRows * 32 + row * 32);
+          for (int half = 0; half < 2; ++half) {
+            uint32_t v[16];
+            if (has) {
+              tmem_ld16x256_x4(tmem_base + ((uint32_t)(quarter * 32 + half * 16) << 16) +
+                                   (uint32_t)(acc * kAccCols + c0), v);
+            } else {
 #pragma unroll
-          for (int j = 0; j < 8; ++j)
-            dst[j] = make_float4(__uint_as_float(v[4 * j]), __uint_as_float(v[4 * j + 1]),
-                                 __uint_as_float(v[4 * j + 2]), __uint_as_float(v[4 * j + 3]));
-        } else if (job.out_fp64) {
-          if (m < job.M) {
-            double* yr = o_y + job.out_off + m * job.N;
-            const double* xr = i_x + job.x_off + m * job.N;
+              for (int j = 0; j < 16; ++j) v[j] = 0u;
+            }
 #pragma unroll
-            for (int j = 0; j < 32; ++j) {
-              const int n = n0 + j;
-              if (n < job.N) {
-                double val = f32_to_f64(__uint_as_float(v[j]));  // exact, integer ops
-                if (job.axpy != 0.0) val = fma(job.axpy, xr[n], val);
-                yr[n] = val;
+            for (int hr = 0; hr < 2; ++hr) {
+              const int r = quarter * 32 + half * 16 + hr * 8 + (lane >> 2);
+              const int64_t mr = (int64_t)tile.mt * kRows + r;
+#pragma unroll
+              for (int j = 0; j < 4; ++j) {
+                const int cc = c0 + 8 * j + 2 * (lane & 3);  // column in the tile
+                const float f0 = __uint_as_float(v[4 * j + 2 * hr]);
+                const float f1 = __uint_as_float(v[4 * j + 2 * hr + 1]);
+                if (split) {
+                  // partial sums of this part: slot red + part, row-major 128 x 256
+                  *reinterpret_cast<float2*>(partial + (int64_t)(tile.red + tile.part) * kSlotFloats +
+                                             r * 256 + cc) = make_float2(f0, f1);
+                } else if (mr < job.M) {
+                  const int n = tile.nt * kRows + cc;
+                  double* yp = o_y + job.out_off + mr * job.N + n;
+                  double d0 = f32_to_f64(f0), d1 = f32_to_f64(f1);  // exact, integer ops
+                  if (job.axpy != 0.0) {
+                    const double* xp = i_x + job.x_off + mr * job.N + n;
+                    if (n < job.N) d0 = fma(job.axpy, xp[0], d0);
+                    if (n + 1 < job.N) d1 = fma(job.axpy, xp[1], d1);
+                  }
+                  if (n + 1 < job.N && (reinterpret_cast<uintptr_t>(yp) & 15) == 0) {
+                    *reinterpret_cast<double2*>(yp) = make_double2(d0, d1);
+                  } else {
+                    if (n < job.N) yp[0] = d0;
+                    if (n + 1 < job.N) yp[1] = d1;
+                  }
+                }
               }
             }
           }
-        } else {
-          const int kt = n0 / KT;
-          if (kt < job.out_nkt) {
-            uint8_t* tb = o_img + job.out_off + ((int64_t)tile.mt * job.out_nkt + kt) * PLANES * L::CHUNK;
-            if constexpr (TF32) {
+        }
+      } else {
+        for (int c0 = 0; c0 < ncols; c0 += 32) {
+          uint32_t v[32];
+          if (has) {
+            tmem_ld32(tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(acc * kAccCols + c0), v);
+          } else {
 #pragma unroll
-              for (int g = 0; g < 8; ++g) {
-                uint4 q;
-                q.x = __float_as_uint(to_tf32(__uint_as_float(v[4 * g + 0])));
-                q.y = __float_as_uint(to_tf32(__uint_as_float(v[4 * g + 1])));
-                q.z = __float_as_uint(to_tf32(__uint_as_float(v[4 * g + 2])));
-                q.w = __float_as_uint(to_tf32(__uint_as_float(v[4 * g + 3])));
-                *reinterpret_cast<uint4*>(tb + L::off(row, g)) = q;
-              }
-            } else {
-              const int gbase = (n0 % KT) / 8;
+            for (int j = 0; j < 32; ++j) v[j] = 0u;
+          }
+          const int n0 = tile.nt * kRows + c0;
+          {
+            const int kt = n0 / KT;
+            if (kt < job.out_nkt) {
+              uint8_t* tb = o_img + job.out_off + ((int64_t)tile.mt * job.out_nkt + kt) * PLANES * L::CHUNK;
+              if constexpr (TF32) {
 #pragma unroll
-              for (int g = 0; g < 4; ++g) {
-                uint32_t w0[4], w1[4], w2[4];
-#pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                  __nv_bfloat16 h[2][3];
-#pragma unroll
-                  for (int u = 0; u < 2; ++u) {
-                    const float f = __uint_as_float(v[8 * g + 2 * e + u]);
-                    const __nv_bfloat16 h0 = __float2bfloat16_rn(f);
-                    const float r1 = f - __bfloat162float(h0);
-                    const __nv_bfloat16 h1 = __float2bfloat16_rn(r1);
-                    const float r2 = r1 - __bfloat162float(h1);
-                    h[u][0] = h0;
-                    h[u][1] = h1;
-                    h[u][2] = __float2bfloat16_rn(r2);
-                  }
-                  w0[e] = pack2_bf16(h[0][0], h[1][0]);
-                  w1[e] = pack2_bf16(h[0][1], h[1][1]);
-                  w2[e] = pack2_bf16(h[0][2], h[1][2]);
+                for (int g = 0; g < 8; ++g) {
+                  uint4 q;
+                  q.x = __float_as_uint(to_tf32(__uint_as_float(v[4 * g + 0])));
+                  q.y = __float_as_uint(to_tf32(__uint_as_float(v[4 * g + 1])));
+                  q.z = __float_as_uint(to_tf32(__uint_as_float(v[4 * g + 2])));
+                  q.w = __float_as_uint(to_tf32(__uint_as_float(v[4 * g + 3])));
+                  *reinterpret_cast<uint4*>(tb + L::off(row, g)) = q;
                 }
-                const uint32_t off = L::off(row, gbase + g);
-                *reinterpret_cast<uint4*>(tb + off) = make_uint4(w0[0], w0[1], w0[2], w0[3]);
-                *reinterpret_cast<uint4*>(tb + L::CHUNK + off) = make_uint4(w1[0], w1[1], w1[2], w1[3]);
-                *reinterpret_cast<uint4*>(tb + 2 * L::CHUNK + off) = make_uint4(w2[0], w2[1], w2[2], w2[3]);
+              } else {
+                const int gbase = (n0 % KT) / 8;
+#pragma unroll
+                for (int g = 0; g < 4; ++g) {
+                  uint32_t w0[4], w1[4], w2[4];
+#pragma unroll
+                  for (int e = 0; e < 4; ++e) {
+                    __nv_bfloat16 h[2][3];
+#pragma unroll
+                    for (int u = 0; u < 2; ++u) {
+                      const float f = __uint_as_float(v[8 * g + 2 * e + u]);
+                      const __nv_bfloat16 h0 = __float2bfloat16_rn(f);
+                      const float r1 = f - __bfloat162float(h0);
+                      const __nv_bfloat16 h1 = __float2bfloat16_rn(r1);
+                      const float r2 = r1 - __bfloat162float(h1);
+                      h[u][0] = h0;
+                      h[u][1] = h1;
+                      h[u][2] = __float2bfloat16_rn(r2);
+                    }
+                    w0[e] = pack2_bf16(h[0][0], h[1][0]);
+                    w1[e] = pack2_bf16(h[0][1], h[1][1]);
+                    w2[e] = pack2_bf16(h[0][2], h[1][2]);
+                  }
+                  const uint32_t off = L::off(row, gbase + g);
+                  *reinterpret_cast<uint4*>(tb + off) = make_uint4(w0[0], w0[1], w0[2], w0[3]);
+                  *reinterpret_cast<uint4*>(tb + L::CHUNK + off) = make_uint4(w1[0], w1[1], w1[2], w1[3]);
+                  *reinterpret_cast<uint4*>(tb + 2 * L::CHUNK + off) = make_uint4(w2[0], w2[1], w2[2], w2[3]);
+                }
               }
             }
           }
@@ -609,8 +636,8 @@ tc_gemm_kernel(const TcTile* __restrict__ tiles, int ntiles, const TcJob* __rest
 }
 
 // Split K: sums the FP32 partial sums of each split tile in part order (slots red ..
-// red + nparts - 1, laid out [32-column group][row][32]) and writes FP64 Y plus the
-// identity-identity term.  32 CTAs of 256 threads per split tile, 4 values per thread.
+// red + nparts - 1, row-major 128 x 256) and writes FP64 Y plus the identity-identity
+// term.  32 CTAs of 256 threads per split tile, 4 consecutive values per thread.
 __global__ void __launch_bounds__(256)
 split_reduce_kernel(const TcTile* __restrict__ groups, const TcJob* __restrict__ jobs,
                     const float* __restrict__ partial, double* __restrict__ y,
@@ -619,30 +646,30 @@ split_reduce_kernel(const TcTile* __restrict__ groups, const TcJob* __restrict__
   const TcTile g = groups[blockIdx.x >> 5];
   const TcJob job = jobs[g.job];
   const int idx = (((int)blockIdx.x & 31) * 256 + (int)threadIdx.x) * 4;
-  const int grp = idx >> 12, row = (idx >> 5) & (kRows - 1), col = idx & 31;
-  if (grp * 32 >= (g.wide ? 256 : 128)) return;
+  const int row = idx >> 8, col = idx & 255;
   const int64_t m = (int64_t)g.mt * kRows + row;
-  if (m >= job.M) return;
-  const float* src = partial + (int64_t)g.red * (kRows * 256) + idx;
-  float4 s = __ldcg(reinterpret_cast<const float4*>(src));
-  for (int p = 1; p < g.nparts; ++p) {
-    const float4 q = __ldcg(reinterpret_cast<const float4*>(src + (int64_t)p * (kRows * 256)));
-    s.x += q.x;
-    s.y += q.y;
-    s.z += q.z;
-    s.w += q.w;
-  }
-  const float v[4] = {s.x, s.y, s.z, s.w};
-  const int n0 = g.nt * kRows + grp * 32 + col;
-  double* yr = y + job.out_off + m * job.N;
-  const double* xr = x + job.x_off + m * job.N;
+  if (col < (g.wide ? 256 : 128) && m < job.M) {
+    const float* src = partial + (int64_t)g.red * kSlotFloats + idx;
+    float4 s = __ldcg(reinterpret_cast<const float4*>(src));
+    for (int p = 1; p < g.nparts; ++p) {
+      const float4 q = __ldcg(reinterpret_cast<const float4*>(src + (int64_t)p * kSlotFloats));
+      s.x += q.x;
+      s.y += q.y;
+      s.z += q.z;
+      s.w += q.w;
+    }
+    const float v[4] = {s.x, s.y, s.z, s.w};
+    const int n0 = g.nt * kRows + col;
+    double* yr = y + job.out_off + m * job.N;
+    const double* xr = x + job.x_off + m * job.N;
 #pragma unroll
-  for (int e = 0; e < 4; ++e) {
-    const int n = n0 + e;
-    if (n < job.N) {
-      double val = f32_to_f64(v[e]);  // exact, integer ops
-      if (job.axpy != 0.0) val = fma(job.axpy, xr[n], val);
-      yr[n] = val;
+    for (int e = 0; e < 4; ++e) {
+      const int n = n0 + e;
+      if (n < job.N) {
+        double val = f32_to_f64(v[e]);  // exact, integer ops
+        if (job.axpy != 0.0) val = fma(job.axpy, xr[n], val);
+        yr[n] = val;
+      }
     }
   }
   grid_dep_launch();
