@@ -153,8 +153,8 @@ __host__ __device__ __forceinline__ uint32_t swz(int r, int g) {
 //   BF16x3 planes: 64-byte rows, 64-byte swizzle (8-row atoms of 512 bytes; the 16-byte
 //                  group g of row r sits at group g ^ ((r >> 1) & 3) of its row), 8 KB
 //   TF32:          128-byte rows, 128-byte swizzle (1024-byte atoms, g ^ (r & 7)), 16 KB
-// so that a pipeline stage of BF16x3 (three planes of A and of B) is 48 KB and four stages
-// fit in shared memory.
+// so that a pipeline stage of BF16x3 holds three planes of A (24 KB) and three planes of a
+// 128- or 256-row B (up to 48 KB), and three such 72 KB stages fit in shared memory.
 template <bool TF32>
 struct Layout {
   static constexpr int ROWB = TF32 ? 128 : 64;  // bytes per image row
