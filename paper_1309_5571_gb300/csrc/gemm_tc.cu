@@ -3,7 +3,7 @@
 // Eq. 11 is evaluated in the same two stages as the FP64 path (stage 1: one GEMM per
 // record with two proper factors; stage 2: one GEMM per output segment whose K dimension
 // concatenates every record writing that segment), but every GEMM runs as
-//     D[128 x 128] (FP32, in TMEM) += A_tile[128 x K] . B_tile[128 x K]^T
+//     D[128 x N] (FP32, in TMEM) += A_tile[128 x K] . B_tile[N x K]^T,  N = 128 or 256
 // with both operands K-major in shared memory.  Two arithmetics:
 //   TF32   : operands stored as FP32 rounded to TF32, one product per K step;
 //   BF16x3 : every operand stored as three BF16 planes x = x0 + x1 + x2 (24 significant
@@ -31,7 +31,8 @@
 //              accumulators
 //   warps 2-5  epilogue: tcgen05.ld of the accumulator (warp w reads TMEM lanes
 //              32 (w % 4) .. + 31), then either an image of the result (stage 1) or FP64 Y
-//              plus the identity-identity term (stage 2).  A stage-2 tile whose K range is
+//              plus the identity-identity term (stage 2, from 16-lane loads so that the
+//              stores write 64-byte row segments).  A stage-2 tile whose K range is
 //              split into parts writes its FP32 partial sums to a scratch slot of its own;
 //              a small kernel after the stage adds the slots in part order and writes Y,
 //              so the result does not depend on which CTA ran which part.
@@ -565,48 +566,46 @@ tc_gemm_kernel(const TcTile* __restrict__ tiles, int ntiles, const TcJob* __rest
             for (int j = 0; j < 32; ++j) v[j] = 0u;
           }
           const int n0 = tile.nt * kRows + c0;
-          {
-            const int kt = n0 / KT;
-            if (kt < job.out_nkt) {
-              uint8_t* tb = o_img + job.out_off + ((int64_t)tile.mt * job.out_nkt + kt) * PLANES * L::CHUNK;
-              if constexpr (TF32) {
+          const int kt = n0 / KT;
+          if (kt < job.out_nkt) {
+            uint8_t* tb = o_img + job.out_off + ((int64_t)tile.mt * job.out_nkt + kt) * PLANES * L::CHUNK;
+            if constexpr (TF32) {
 #pragma unroll
-                for (int g = 0; g < 8; ++g) {
-                  uint4 q;
-                  q.x = __float_as_uint(to_tf32(__uint_as_float(v[4 * g + 0])));
-                  q.y = __float_as_uint(to_tf32(__uint_as_float(v[4 * g + 1])));
-                  q.z = __float_as_uint(to_tf32(__uint_as_float(v[4 * g + 2])));
-                  q.w = __float_as_uint(to_tf32(__uint_as_float(v[4 * g + 3])));
-                  *reinterpret_cast<uint4*>(tb + L::off(row, g)) = q;
-                }
-              } else {
-                const int gbase = (n0 % KT) / 8;
+              for (int g = 0; g < 8; ++g) {
+                uint4 q;
+                q.x = __float_as_uint(to_tf32(__uint_as_float(v[4 * g + 0])));
+                q.y = __float_as_uint(to_tf32(__uint_as_float(v[4 * g + 1])));
+                q.z = __float_as_uint(to_tf32(__uint_as_float(v[4 * g + 2])));
+                q.w = __float_as_uint(to_tf32(__uint_as_float(v[4 * g + 3])));
+                *reinterpret_cast<uint4*>(tb + L::off(row, g)) = q;
+              }
+            } else {
+              const int gbase = (n0 % KT) / 8;
 #pragma unroll
-                for (int g = 0; g < 4; ++g) {
-                  uint32_t w0[4], w1[4], w2[4];
+              for (int g = 0; g < 4; ++g) {
+                uint32_t w0[4], w1[4], w2[4];
 #pragma unroll
-                  for (int e = 0; e < 4; ++e) {
-                    __nv_bfloat16 h[2][3];
+                for (int e = 0; e < 4; ++e) {
+                  __nv_bfloat16 h[2][3];
 #pragma unroll
-                    for (int u = 0; u < 2; ++u) {
-                      const float f = __uint_as_float(v[8 * g + 2 * e + u]);
-                      const __nv_bfloat16 h0 = __float2bfloat16_rn(f);
-                      const float r1 = f - __bfloat162float(h0);
-                      const __nv_bfloat16 h1 = __float2bfloat16_rn(r1);
-                      const float r2 = r1 - __bfloat162float(h1);
-                      h[u][0] = h0;
-                      h[u][1] = h1;
-                      h[u][2] = __float2bfloat16_rn(r2);
-                    }
-                    w0[e] = pack2_bf16(h[0][0], h[1][0]);
-                    w1[e] = pack2_bf16(h[0][1], h[1][1]);
-                    w2[e] = pack2_bf16(h[0][2], h[1][2]);
+                  for (int u = 0; u < 2; ++u) {
+                    const float f = __uint_as_float(v[8 * g + 2 * e + u]);
+                    const __nv_bfloat16 h0 = __float2bfloat16_rn(f);
+                    const float r1 = f - __bfloat162float(h0);
+                    const __nv_bfloat16 h1 = __float2bfloat16_rn(r1);
+                    const float r2 = r1 - __bfloat162float(h1);
+                    h[u][0] = h0;
+                    h[u][1] = h1;
+                    h[u][2] = __float2bfloat16_rn(r2);
                   }
-                  const uint32_t off = L::off(row, gbase + g);
-                  *reinterpret_cast<uint4*>(tb + off) = make_uint4(w0[0], w0[1], w0[2], w0[3]);
-                  *reinterpret_cast<uint4*>(tb + L::CHUNK + off) = make_uint4(w1[0], w1[1], w1[2], w1[3]);
-                  *reinterpret_cast<uint4*>(tb + 2 * L::CHUNK + off) = make_uint4(w2[0], w2[1], w2[2], w2[3]);
+                  w0[e] = pack2_bf16(h[0][0], h[1][0]);
+                  w1[e] = pack2_bf16(h[0][1], h[1][1]);
+                  w2[e] = pack2_bf16(h[0][2], h[1][2]);
                 }
+                const uint32_t off = L::off(row, gbase + g);
+                *reinterpret_cast<uint4*>(tb + off) = make_uint4(w0[0], w0[1], w0[2], w0[3]);
+                *reinterpret_cast<uint4*>(tb + L::CHUNK + off) = make_uint4(w1[0], w1[1], w1[2], w1[3]);
+                *reinterpret_cast<uint4*>(tb + 2 * L::CHUNK + off) = make_uint4(w2[0], w2[1], w2[2], w2[3]);
               }
             }
           }
