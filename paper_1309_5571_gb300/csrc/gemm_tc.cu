@@ -612,45 +612,33 @@ tc_gemm_kernel(const TcTile* __restrict__ tiles, int ntiles, const TcJob* __rest
 
 // Split K: sums the FP32 partial sums of each split tile in part order (slots red ..
 // red + nparts - 1, row-major 128 x 256) and writes FP64 Y plus the identity-identity
-// term.  16 CTAs of 256 threads per split tile, 8 consecutive values per thread; a thread
-// issues the loads of up to four parts before it adds them.
-constexpr int kMaxParts = 8;  // the K split cuts a tile into at most 8 parts
-__global__ void __launch_bounds__(256, 4)
+// term.  32 CTAs of 256 threads per split tile, 4 consecutive values per thread.
+__global__ void __launch_bounds__(256)
 split_reduce_kernel(const TcTile* __restrict__ groups, const TcJob* __restrict__ jobs,
                     const float* __restrict__ partial, double* __restrict__ y,
                     const double* __restrict__ x) {
   grid_dep_wait();
-  const TcTile g = groups[blockIdx.x >> 4];
+  const TcTile g = groups[blockIdx.x >> 5];
   const TcJob job = jobs[g.job];
-  const int idx = (((int)blockIdx.x & 15) * 256 + (int)threadIdx.x) * 8;
+  const int idx = (((int)blockIdx.x & 31) * 256 + (int)threadIdx.x) * 4;
   const int row = idx >> 8, col = idx & 255;
   const int64_t m = (int64_t)g.mt * kRows + row;
   if (col < (g.wide ? 256 : 128) && m < job.M) {
     const float* src = partial + (int64_t)g.red * kSlotFloats + idx;
-    float v[8];
-    for (int p0 = 0; p0 < g.nparts; p0 += 4) {
-      float4 lo[4], hi[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        if (p0 + u < g.nparts) {
-          lo[u] = __ldcg(reinterpret_cast<const float4*>(src + (int64_t)(p0 + u) * kSlotFloats));
-          hi[u] = __ldcg(reinterpret_cast<const float4*>(src + (int64_t)(p0 + u) * kSlotFloats + 4));
-        }
-      }
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        if (p0 + u < g.nparts) {
-          const float w[8] = {lo[u].x, lo[u].y, lo[u].z, lo[u].w, hi[u].x, hi[u].y, hi[u].z, hi[u].w};
-#pragma unroll
-          for (int e = 0; e < 8; ++e) v[e] = (p0 + u == 0) ? w[e] : v[e] + w[e];
-        }
-      }
+    float4 s = __ldcg(reinterpret_cast<const float4*>(src));
+    for (int p = 1; p < g.nparts; ++p) {
+      const float4 q = __ldcg(reinterpret_cast<const float4*>(src + (int64_t)p * kSlotFloats));
+      s.x += q.x;
+      s.y += q.y;
+      s.z += q.z;
+      s.w += q.w;
     }
+    const float v[4] = {s.x, s.y, s.z, s.w};
     const int n0 = g.nt * kRows + col;
     double* yr = y + job.out_off + m * job.N;
     const double* xr = x + job.x_off + m * job.N;
 #pragma unroll
-    for (int e = 0; e < 8; ++e) {
+    for (int e = 0; e < 4; ++e) {
       const int n = n0 + e;
       if (n < job.N) {
         double val = f32_to_f64(v[e]);  // exact, integer ops
@@ -741,8 +729,7 @@ bool tc_tiles_in_range(const TcPlan* t, int64_t n, const std::vector<TcJob>& job
                tl.job, tl.mt, tl.nt, tl.kb, tl.ke, (long long)job_kt);
       return false;
     }
-    if (tl.nparts < 1 || tl.nparts > tc::kMaxParts ||
-        (tl.nparts > 1 && (!j.out_fp64 || tl.part < 0 || tl.part >= tl.nparts || tl.red < 0 ||
+    if (tl.nparts < 1 || (tl.nparts > 1 && (!j.out_fp64 || tl.part < 0 || tl.part >= tl.nparts || tl.red < 0 ||
                           (int64_t)tl.red + tl.nparts > t->nslots))) {
       snprintf(why, why_len, "tile (job %d, %d, %d) has bad split-K fields", tl.job, tl.mt, tl.nt);
       return false;
@@ -986,7 +973,7 @@ dmrg_status build_tc(dmrg_plan* p, dmrg_precision prec, cudaStream_t st, TcPlan*
     for (const TcTile& tl : src) {
       const int nk = tl.ke - tl.kb;
       const int64_t c = tile_cost(tl);
-      const int np = (int)std::min<int64_t>({(c + cap - 1) / cap, (int64_t)nk, (int64_t)tc::kMaxParts});
+      const int np = (int)std::min<int64_t>({(c + cap - 1) / cap, (int64_t)nk, 8});
       if (!jobs[tl.job].out_fp64 || np < 2) {
         res.push_back(tl);
         continue;
@@ -1201,7 +1188,7 @@ dmrg_status run_tc_part(dmrg_plan* p, TcPlan* t, const double* x, double* y, int
       t->d_err, (const TcPtrs*)nullptr, part, t->d_ctr + 2 * (part - 1), t->d_partial));
   DMRG_LAUNCH_CHECK();
   if (part == 2 && t->ngroups[c] > 0) {
-    DMRG_CUDA_TRY(launch_pdl(tc::split_reduce_kernel, dim3((unsigned)(t->ngroups[c] * 16)), dim3(256), 0, st,
+    DMRG_CUDA_TRY(launch_pdl(tc::split_reduce_kernel, dim3((unsigned)(t->ngroups[c] * 32)), dim3(256), 0, st,
                              (const TcTile*)t->d_groups[c], (const TcJob*)t->d_jobs,
                              (const float*)t->d_partial, y, x));
     DMRG_LAUNCH_CHECK();
