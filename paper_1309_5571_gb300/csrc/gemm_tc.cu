@@ -241,12 +241,27 @@ pack_kernel(const PackChunk* __restrict__ chunks, const PackJob* __restrict__ jo
       q.w = __float_as_uint(to_tf32(v[3]));
       *reinterpret_cast<uint4*>(base + off) = q;
     } else {
-      uint32_t w[3][4];
+      __nv_bfloat16 h[3][8];
 #pragma unroll
-      for (int e = 0; e < 4; ++e) split3_bf16x2(v[2 * e], v[2 * e + 1], w[0][e], w[1][e], w[2][e]);
+      for (int e = 0; e < 8; ++e) {
+        const float a = v[e];
+        const __nv_bfloat16 h0 = __float2bfloat16_rn(a);
+        const float r1 = a - __bfloat162float(h0);
+        const __nv_bfloat16 h1 = __float2bfloat16_rn(r1);
+        const float r2 = r1 - __bfloat162float(h1);
+        h[0][e] = h0;
+        h[1][e] = h1;
+        h[2][e] = __float2bfloat16_rn(r2);
+      }
 #pragma unroll
-      for (int p = 0; p < PLANES; ++p)
-        *reinterpret_cast<uint4*>(base + p * L::CHUNK + off) = make_uint4(w[p][0], w[p][1], w[p][2], w[p][3]);
+      for (int p = 0; p < PLANES; ++p) {
+        uint4 q;
+        q.x = pack2_bf16(h[p][0], h[p][1]);
+        q.y = pack2_bf16(h[p][2], h[p][3]);
+        q.z = pack2_bf16(h[p][4], h[p][5]);
+        q.w = pack2_bf16(h[p][6], h[p][7]);
+        *reinterpret_cast<uint4*>(base + p * L::CHUNK + off) = q;
+      }
     }
   }
   grid_dep_launch();
@@ -570,9 +585,23 @@ tc_gemm_kernel(const TcTile* __restrict__ tiles, int ntiles, const TcJob* __rest
               for (int g = 0; g < 4; ++g) {
                 uint32_t w0[4], w1[4], w2[4];
 #pragma unroll
-                for (int e = 0; e < 4; ++e)
-                  split3_bf16x2(__uint_as_float(v[8 * g + 2 * e]), __uint_as_float(v[8 * g + 2 * e + 1]),
-                                w0[e], w1[e], w2[e]);
+                for (int e = 0; e < 4; ++e) {
+                  __nv_bfloat16 h[2][3];
+#pragma unroll
+                  for (int u = 0; u < 2; ++u) {
+                    const float f = __uint_as_float(v[8 * g + 2 * e + u]);
+                    const __nv_bfloat16 h0 = __float2bfloat16_rn(f);
+                    const float r1 = f - __bfloat162float(h0);
+                    const __nv_bfloat16 h1 = __float2bfloat16_rn(r1);
+                    const float r2 = r1 - __bfloat162float(h1);
+                    h[u][0] = h0;
+                    h[u][1] = h1;
+                    h[u][2] = __float2bfloat16_rn(r2);
+                  }
+                  w0[e] = pack2_bf16(h[0][0], h[1][0]);
+                  w1[e] = pack2_bf16(h[0][1], h[1][1]);
+                  w2[e] = pack2_bf16(h[0][2], h[1][2]);
+                }
                 const uint32_t off = L::off(row, gbase + g);
                 *reinterpret_cast<uint4*>(tb + off) = make_uint4(w0[0], w0[1], w0[2], w0[3]);
                 *reinterpret_cast<uint4*>(tb + L::CHUNK + off) = make_uint4(w1[0], w1[1], w1[2], w1[3]);

@@ -143,21 +143,6 @@ __device__ __forceinline__ float to_tf32(float x) {
 __device__ __forceinline__ uint32_t pack2_bf16(__nv_bfloat16 a, __nv_bfloat16 b) {
   return (uint32_t)__bfloat16_as_ushort(a) | ((uint32_t)__bfloat16_as_ushort(b) << 16);
 }
-// Two FP32 values a (low half) and b (high half) as three BF16 planes, each value split
-// x = h0 + h1 + h2 with h0 = bf16_rn(x), h1 = bf16_rn(x - h0), h2 = bf16_rn(x - h0 - h1)
-// (exact: the three terms hold the 24 significant bits); one paired conversion per plane
-__device__ __forceinline__ void split3_bf16x2(float a, float b, uint32_t& w0, uint32_t& w1,
-                                              uint32_t& w2) {
-  const __nv_bfloat162 h0 = __floats2bfloat162_rn(a, b);
-  const float2 f0 = __bfloat1622float2(h0);
-  const float ra = a - f0.x, rb = b - f0.y;
-  const __nv_bfloat162 h1 = __floats2bfloat162_rn(ra, rb);
-  const float2 f1 = __bfloat1622float2(h1);
-  const __nv_bfloat162 h2 = __floats2bfloat162_rn(ra - f1.x, rb - f1.y);
-  w0 = pack2_bf16(h0.x, h0.y);
-  w1 = pack2_bf16(h1.x, h1.y);
-  w2 = pack2_bf16(h2.x, h2.y);
-}
 
 // byte offset of the 16-byte group g of row r inside one plane of an image tile
 __host__ __device__ __forceinline__ uint32_t swz(int r, int g) {
