@@ -208,12 +208,7 @@ pack_kernel(const PackChunk* __restrict__ chunks, const PackJob* __restrict__ jo
   const double* src = (jb.src_space ? x : arena) + jb.src_off;
   uint8_t* base = dst + jb.dst_off + ((int64_t)ch.rt * jb.nkt + ch.kt) * PLANES * L::CHUNK;
   const bool kfast = jb.cs == 1;
-  // a fixed trip count (the kernel runs 256 threads) so that the loads of all of a thread's
-  // groups can be issued before the first conversion
-  static_assert(kRows * L::GROUPS % 256 == 0, "groups per thread");
-#pragma unroll
-  for (int it = 0; it < kRows * L::GROUPS / 256; ++it) {
-    const int idx = (int)threadIdx.x + 256 * it;
+  for (int idx = threadIdx.x; idx < kRows * L::GROUPS; idx += blockDim.x) {
     int r, g;
     if (kfast) { g = idx % L::GROUPS; r = idx / L::GROUPS; }
     else { r = idx & (kRows - 1); g = idx >> 7; }
