@@ -441,7 +441,10 @@ def main():
     traffic = TC_TRAFFIC if (prec == "bf16x3" and args.workload == WORKLOAD) else None
     roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
                 "frac": achieved / peak, "traffic": traffic, "kernel": f"projection ({prec})",
-                "peak_source": peak_note}
+                "peak_source": peak_note,
+                "traffic_source": ("ncu dram__bytes_read.sum + dram__bytes_write.sum of pack, both "
+                                   "GEMM stages and the split-K reduction, tile schedules [6, 17] "
+                                   "(profiles/tc_gemm_bf16x3_hub_L64_m2048.md)") if traffic else None}
 
     # ---- CPU oracle baseline (rank 0, N = 1 only), bounded sample
     cpu = None
