@@ -19,11 +19,11 @@ Readings where the paper is silent (Sec. 6 names the Sadkane-Sidje variant only)
 * orthogonalisation: classical Gram-Schmidt applied twice; if the norm left after it is
   below 1e-10 of the norm before, the raw residual r is used instead, and if that also
   collapses the iteration reports a breakdown;
-* subspace limit: 20 columns (Sec. 6.1); when the basis is full, it is collapsed to the
-  current Ritz vector x (restart_keep=1, the default, as on the GPU) or to x and the
-  previous iteration's Ritz vector orthogonalised against it (restart_keep=2), with W
-  replaced by the same
-  combinations of its columns, before the new direction is added;
+* subspace limit: 20 columns (Sec. 6.1); when the basis is full it is collapsed, before
+  the new direction is added, to the current Ritz vector x alone (restart_keep=1) or to x
+  and the previous iteration's Ritz vector orthonormalised against it (restart_keep=2, the
+  default, which is also the default of the CUDA library), with W and B replaced by the
+  same combinations of their columns;
 * convergence: ||r||_2 <= tol on a normalised x; at most ``max_iter`` iterations.
 """
 from __future__ import annotations
@@ -47,9 +47,40 @@ def _cgs2(V: np.ndarray, t: np.ndarray) -> np.ndarray:
     return t
 
 
+def restart_coefficients(y: np.ndarray, y_prev, keep: int) -> np.ndarray:
+    """Columns C (k x 1 or k x 2) of the collapsed basis V C in the current basis.
+
+    Column 0 is the Ritz vector's coefficient vector y.  With keep == 2, column 1 is the
+    previous iteration's Ritz vector: its coefficients y_prev refer to the basis as it was
+    one column shorter, so they are padded with a zero for the newest column, then
+    orthogonalised against y (twice) and normalised; it is dropped if nothing is left."""
+    k = y.shape[0]
+    C = y[:, None]
+    if keep == 2 and y_prev is not None:
+        c2 = np.zeros(k)
+        c2[:len(y_prev)] = y_prev
+        c2 -= y * (y @ c2)
+        c2 -= y * (y @ c2)
+        if np.linalg.norm(c2) > 1e-8:
+            C = np.column_stack([y, c2 / np.linalg.norm(c2)])
+    return C
+
+
+def collapse(V: np.ndarray, W: np.ndarray, B: np.ndarray, C: np.ndarray):
+    """The collapsed basis V C, its projections W C = H V C and C^T B C (all in exact
+    arithmetic consequences of W = H V and B = V^T H V)."""
+    return V @ C, W @ C, C.T @ B @ C
+
+
 def davidson(matvec, D: np.ndarray, x0: np.ndarray, tol: float = 1e-10,
-             max_iter: int = 1000, max_subspace: int = 20, restart_keep: int = 1):
-    """Lowest eigenpair of the symmetric operator ``matvec``; returns (lam, x, info)."""
+             max_iter: int = 1000, max_subspace: int = 20, restart_keep: int = 2,
+             on_restart=None):
+    """Lowest eigenpair of the symmetric operator ``matvec``; returns (lam, x, info).
+
+    ``on_restart(V, W, B, x_prev)``, if given, is called after every collapse of the basis
+    with the new basis, its projections and small matrix (k = 1 or 2 columns) and the
+    previous iteration's Ritz vector (None at the first iteration); tests use it to check
+    the invariants of a restart."""
     n = x0.shape[0]
     V = np.zeros((n, max_subspace))
     W = np.zeros((n, max_subspace))
@@ -57,8 +88,10 @@ def davidson(matvec, D: np.ndarray, x0: np.ndarray, tol: float = 1e-10,
     V[:, 0] = x0 / np.linalg.norm(x0)
     k = 1
     history = []
+    restarts = 0
     lam, x, rn = np.nan, V[:, 0].copy(), np.inf
     y_prev = None
+    x_prev = None
     for it in range(1, max_iter + 1):
         W[:, k - 1] = matvec(V[:, k - 1])
         col = V[:, :k].T @ W[:, k - 1]
@@ -72,25 +105,23 @@ def davidson(matvec, D: np.ndarray, x0: np.ndarray, tol: float = 1e-10,
         rn = float(np.linalg.norm(r))
         history.append((lam, rn))
         if rn <= tol:
-            return lam, x, {"iters": it, "resnorm": rn, "converged": True, "history": history}
+            return lam, x, {"iters": it, "resnorm": rn, "converged": True, "history": history,
+                            "restarts": restarts}
         t = correct(r, lam, D)
         if k == max_subspace:          # restart with the Ritz vector (and the previous one)
-            C = y[:, None]
-            if restart_keep == 2 and y_prev is not None:
-                c2 = np.zeros(k)
-                c2[:len(y_prev)] = y_prev
-                c2 -= y * (y @ c2)
-                c2 -= y * (y @ c2)
-                if np.linalg.norm(c2) > 1e-8:
-                    C = np.column_stack([y, c2 / np.linalg.norm(c2)])
-            Vn, Wn = V[:, :k] @ C, W[:, :k] @ C
-            Bn = C.T @ B[:k, :k] @ C
+            C = restart_coefficients(y, y_prev, restart_keep)
+            Vn, Wn, Bn = collapse(V[:, :k], W[:, :k], B[:k, :k], C)
             k = C.shape[1]
             V[:, :k], W[:, :k] = Vn, Wn
             B[:, :] = 0.0
             B[:k, :k] = Bn
             y = C.T @ y            # the Ritz vector in the new basis: e_1
+            restarts += 1
+            if on_restart is not None:
+                on_restart(V[:, :k].copy(), W[:, :k].copy(), B[:k, :k].copy(),
+                           None if x_prev is None else x_prev.copy())
         y_prev = y
+        x_prev = x
         before = np.linalg.norm(t)
         t_o = _cgs2(V[:, :k], t)
         if np.linalg.norm(t_o) < BREAKDOWN * before:
@@ -98,7 +129,8 @@ def davidson(matvec, D: np.ndarray, x0: np.ndarray, tol: float = 1e-10,
             t_o = _cgs2(V[:, :k], r)
             if np.linalg.norm(t_o) < BREAKDOWN * before:
                 return lam, x, {"iters": it, "resnorm": rn, "converged": False,
-                                "history": history, "breakdown": True}
+                                "history": history, "breakdown": True, "restarts": restarts}
         V[:, k] = t_o / np.linalg.norm(t_o)
         k += 1
-    return lam, x, {"iters": max_iter, "resnorm": rn, "converged": False, "history": history}
+    return lam, x, {"iters": max_iter, "resnorm": rn, "converged": False, "history": history,
+                    "restarts": restarts}

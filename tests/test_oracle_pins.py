@@ -150,18 +150,129 @@ def test_flop_count_small_case():
 
 
 # ---------------------------------------------------------------- Davidson
+@pytest.mark.parametrize("keep", [1, 2])
 @pytest.mark.parametrize("max_subspace", [20, 4])
-def test_davidson_equals_eigh(max_subspace):
+def test_davidson_equals_eigh(max_subspace, keep):
+    # both restart readings (Ritz vector alone, or with the previous Ritz vector) reach
+    # LAPACK's lowest eigenpair; the problem needs several subspace-limit restarts
     sb = PROBLEMS[3]
     H = projection.superblock_dense(sb)
     w, v = np.linalg.eigh(H)
     x0 = warmup.start_vector(sb.n, seed=0)
     lam, x, info = dav.davidson(lambda z: H @ z, np.diag(H).copy(), x0, tol=1e-10,
-                                max_subspace=max_subspace)
-    assert info["converged"]
+                                max_subspace=max_subspace, restart_keep=keep)
+    assert info["converged"] and info["restarts"] >= 2
     assert lam == pytest.approx(w[0], abs=1e-10)
     assert abs(x @ v[:, 0]) >= 1 - 1e-10
     assert np.linalg.norm(H @ x - lam * x) <= 1e-10 * 1.0001
+
+
+def _random_operator(n=400, seed=1):
+    # diagonally dominated symmetric matrix: the diagonal preconditioner helps, but the
+    # iteration still needs several restarts at both subspace limits
+    rng = np.random.default_rng(seed)
+    A = rng.standard_normal((n, n))
+    return np.diag(np.linspace(0.0, 20.0, n)) + 0.25 * (A + A.T)
+
+
+class _RestartLog:
+    """Collects, at every restart, how far the collapsed basis is from the invariants that
+    hold in exact arithmetic: V^T V = I, W = H V, B = V^T H V, and (keeping two vectors)
+    the previous Ritz vector lies in span(V)."""
+
+    def __init__(self, H):
+        self.H = H
+        self.orth, self.w, self.b, self.prev, self.k = [], [], [], [], []
+
+    def __call__(self, V, W, B, x_prev):
+        H = self.H
+        k = V.shape[1]
+        self.k.append(k)
+        self.orth.append(np.linalg.norm(V.T @ V - np.eye(k)))
+        self.w.append(np.linalg.norm(W - H @ V) / np.linalg.norm(H, 2))
+        self.b.append(np.linalg.norm(B - V.T @ H @ V) / np.linalg.norm(H, 2))
+        if x_prev is not None and k == 2:
+            self.prev.append(np.linalg.norm(x_prev - V @ (V.T @ x_prev)) / np.linalg.norm(x_prev))
+
+
+@pytest.mark.parametrize("max_subspace", [4, 20])
+@pytest.mark.parametrize("keep", [1, 2])
+def test_davidson_restart_invariants(keep, max_subspace):
+    H = _random_operator()
+    w, v = np.linalg.eigh(H)
+    log = _RestartLog(H)
+    lam, x, info = dav.davidson(lambda z: H @ z, np.diag(H).copy(), warmup.start_vector(H.shape[0], 0),
+                                tol=1e-10, max_subspace=max_subspace, restart_keep=keep,
+                                on_restart=log)
+    assert info["converged"] and info["restarts"] >= 3 and len(log.k) == info["restarts"]
+    assert lam == pytest.approx(w[0], abs=1e-10)
+    assert abs(x @ v[:, 0]) >= 1 - 1e-10
+    assert max(log.orth) <= 1e-12
+    assert max(log.w) <= 1e-12 and max(log.b) <= 1e-12
+    if keep == 2:
+        # two vectors kept at the restarts (one only where the previous Ritz vector has
+        # become parallel to the current one, close to convergence), and the previous Ritz
+        # vector lies in the span of the kept pair
+        assert log.k.count(2) >= 3 and log.k[0] == 2
+        assert max(log.prev) <= 1e-10
+    else:
+        assert set(log.k) == {1}
+
+
+def test_planted_restart_w_not_recombined_is_caught(monkeypatch):
+    # W kept as its first columns instead of W C: W = H V breaks after the first restart
+    H = _random_operator()
+    orig = dav.collapse
+
+    def bad(V, W, B, C):
+        Vn, _, Bn = orig(V, W, B, C)
+        return Vn, W[:, :C.shape[1]].copy(), Bn
+
+    monkeypatch.setattr(dav, "collapse", bad)
+    log = _RestartLog(H)
+    dav.davidson(lambda z: H @ z, np.diag(H).copy(), warmup.start_vector(H.shape[0], 0),
+                 tol=1e-10, max_subspace=4, restart_keep=2, max_iter=60, on_restart=log)
+    assert max(log.w) > 1e-3
+
+
+def test_planted_restart_b_not_transformed_is_caught(monkeypatch):
+    H = _random_operator()
+    orig = dav.collapse
+
+    def bad(V, W, B, C):
+        Vn, Wn, _ = orig(V, W, B, C)
+        m = C.shape[1]
+        return Vn, Wn, B[:m, :m].copy()
+
+    monkeypatch.setattr(dav, "collapse", bad)
+    log = _RestartLog(H)
+    dav.davidson(lambda z: H @ z, np.diag(H).copy(), warmup.start_vector(H.shape[0], 0),
+                 tol=1e-10, max_subspace=4, restart_keep=2, max_iter=60, on_restart=log)
+    assert max(log.b) > 1e-3
+
+
+def test_planted_restart_previous_vector_misaligned_is_caught(monkeypatch):
+    # the previous Ritz coefficients padded at the front instead of for the newest column:
+    # the kept second vector is then not the previous Ritz vector
+    H = _random_operator()
+
+    def bad(y, y_prev, keep):
+        k = y.shape[0]
+        C = y[:, None]
+        if keep == 2 and y_prev is not None:
+            c2 = np.zeros(k)
+            c2[k - len(y_prev):] = y_prev
+            c2 -= y * (y @ c2)
+            c2 -= y * (y @ c2)
+            if np.linalg.norm(c2) > 1e-8:
+                C = np.column_stack([y, c2 / np.linalg.norm(c2)])
+        return C
+
+    monkeypatch.setattr(dav, "restart_coefficients", bad)
+    log = _RestartLog(H)
+    dav.davidson(lambda z: H @ z, np.diag(H).copy(), warmup.start_vector(H.shape[0], 0),
+                 tol=1e-10, max_subspace=4, restart_keep=2, max_iter=60, on_restart=log)
+    assert max(log.prev) > 1e-3
 
 
 def test_davidson_reports_nonconvergence():
