@@ -54,15 +54,16 @@ def peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
 
 
-# measured on this machine's GB300 with torch.matmul float64 8192^3 (cuBLAS dgemm), see
-# profiles/peaks_fp64_tf32_probe.txt
+# measured on this machine's GB300 with torch.matmul 8192^3 (cuBLAS dgemm and TF32 GEMM;
+# `python bench.py --mode peaks`)
 FP64_DGEMM_TFLOPS = 1.10
 TF32_TFLOPS = 1006.0
-# DRAM bytes (read + write) of one BF16x3 projection of the default workload (pack, the two
-# tcgen05 GEMM launches and the split-K reduction: 30.1 + 156.7 + 319.8 + 28.7 MB with the
-# tile schedules [6, 17]), from the ncu capture of the current kernels in
-# profiles/tc_gemm_bf16x3_hub_L64_m2048.md
-TC_TRAFFIC = 535.3e6
+# DRAM bytes (ncu dram__bytes_read.sum + dram__bytes_write.sum) of one low-precision
+# projection of the default workload, summed over its launches (pack, the two tcgen05 GEMM
+# stages, the split-K reduction when stage 2 splits), keyed by arithmetic and by the tile
+# schedules of the two GEMM stages the capture ran with; the traffic of a run whose
+# autotuner picked other schedules is not known and is reported as null
+TC_TRAFFIC = {("bf16x3", (6, 17)): 535.3e6}
 
 
 class ClockSampler:
@@ -146,18 +147,19 @@ def job_throughput(units_per_rank: float, world: int, seconds: float) -> float:
 
 
 def cpu_oracle_projection_sample(sb, x, budget_s=15.0):
-    """Time the FP64 oracle's projection (Eq. 11 in NumPy) on the host cores."""
+    """Time the FP64 oracle's projection (Eq. 11 in NumPy) on the host cores; also returns
+    its result, the reference for the projection errors of the GPU arithmetics."""
     from oracle import projection as oproj
     flops = oproj.flop_count(sb)["flops"]
     t0 = time.perf_counter()
     reps = 0
     while True:
-        oproj.project_blocks(sb, x)
+        y = oproj.project_blocks(sb, x)
         reps += 1
         if time.perf_counter() - t0 >= budget_s or reps >= 20:
             break
     dt = (time.perf_counter() - t0) / reps
-    return flops / dt / 1e12, reps, dt
+    return flops / dt / 1e12, reps, dt, y
 
 
 def run_reference(args):
@@ -301,7 +303,7 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--prec", default="auto", choices=["auto", "fp64", "tf32", "bf16x3", "fp64tc"])
+    ap.add_argument("--prec", default="auto", choices=["auto", "fp64", "tf32", "bf16x3", "bf16x2", "fp64tc"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--proj-reps", type=int, default=10)
     ap.add_argument("--mode", default="solve", choices=["solve", "project", "peaks", "batched"])
@@ -372,8 +374,11 @@ def main():
         # without a profiler
         torch.cuda.profiler.start()
         ev0.record(stream)
+        step_ms = []
         for s in range(args.steps):
+            ts = time.perf_counter()
             x, info = plan.solve(x0s_t[s % len(x0s_t)])
+            step_ms.append((time.perf_counter() - ts) * 1e3)
             infos.append(info)
         ev1.record(stream)
         barrier()
@@ -390,11 +395,13 @@ def main():
     t_e2e = time.perf_counter() - te
     e2e_val = (infoh["projections"] + infoh["fp64_projections"]) * flops / t_e2e / 1e12
 
-    # ---- the dominant kernel: the projection (stage-1 + stage-2 launches), timed alone
+    # ---- the dominant kernel: the projection (all its launches), timed alone in every
+    # arithmetic, L2 flushed before each
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     y = torch.empty_like(x0_t)
-    proj = {}
-    for p in sorted({prec, "fp64", "fp64tc"}):
+    proj, proj_out = {}, {}
+    variants = ["fp64", "tf32", "bf16x3", "bf16x2", "fp64tc"]
+    for p in variants:
         for _ in range(2):
             plan.project(x0_t, y, prec=p)
         times = []
@@ -408,21 +415,38 @@ def main():
             torch.cuda.synchronize()
             times.append(a.elapsed_time(b) / 1e3)
         proj[p] = statistics.mean(times)
+        proj_out[p] = y.cpu().numpy()
 
-    # FP64 path solve time (the comparison arm of the metric), once
-    fp64_solve_ms = None
-    e_fp64 = None
-    if prec != "fp64":
-        plan64 = Plan(sb, prec="fp64", tol=1e-10)
-        torch.cuda.synchronize()
-        a = time.perf_counter()
-        _, info64 = plan64.solve(x0_t)
-        fp64_solve_ms = (time.perf_counter() - a) * 1e3
-        e_fp64 = info64["energy"]
-        plan64.close()
-    else:
-        fp64_solve_ms = t_step * 1e3
-        e_fp64 = infos[0]["energy"]
+    # ---- full solves in the other arithmetics (the FP64 path is the comparison arm of the
+    # metric), over the same start vectors as the first timed steps, one plan each
+    nvar = min(3, len(x0s_t))
+    solves = {}
+    for name, opts in (("fp64", dict(prec="fp64")),
+                       ("fp64tc", dict(prec="fp64tc")),
+                       ("tf32", dict(prec="tf32", anchor_prec=args.anchor)),
+                       ("bf16x3", dict(prec="bf16x3", anchor_prec=args.anchor)),
+                       ("bf16x2", dict(prec="bf16x2", anchor_prec=args.anchor))):
+        if name == prec:
+            solves[name] = {"ms": [i_ms for i_ms in step_ms[:nvar]],
+                            "iters": [i["iters"] for i in infos[:nvar]],
+                            "energy": [i["energy"] for i in infos[:nvar]]}
+        else:
+            pv = Plan(sb, tol=1e-10, **opts)
+            pv.solve(x0s_t[0])  # builds and tunes the plan's operand images
+            ms_l, it_l, e_l = [], [], []
+            for sv in range(nvar):
+                torch.cuda.synchronize()
+                a = time.perf_counter()
+                _, iv = pv.solve(x0s_t[sv])
+                torch.cuda.synchronize()
+                ms_l.append((time.perf_counter() - a) * 1e3)
+                it_l.append(iv["iters"])
+                e_l.append(iv["energy"])
+            pv.close()
+            solves[name] = {"ms": ms_l, "iters": it_l, "energy": e_l}
+        solves[name]["mean_ms"] = statistics.mean(solves[name]["ms"])
+    fp64_solve_ms = solves["fp64"]["mean_ms"]
+    e_fp64 = solves["fp64"]["energy"][0]
 
     pk, pk_kind = peaks()
     if prec == "fp64":
@@ -431,28 +455,34 @@ def main():
     elif prec == "tf32":
         bound, peak, unit = "tensor", TF32_TFLOPS, "TFLOP/s"
         peak_note = "measured cuBLAS TF32 8192^3 on this pool's GB300"
+    elif prec == "bf16x2":
+        bound, peak, unit = "tensor", pk["bf16_tflops"] / 3.0, "TFLOP/s"
+        peak_note = f"{pk_kind} bf16 burst / 3 products (algorithmic FLOPs of a BF16x2 GEMM)"
     else:
         bound, peak, unit = "tensor", pk["bf16_tflops"] / 6.0, "TFLOP/s"
         peak_note = f"{pk_kind} bf16 burst / 6 products (algorithmic FLOPs of a BF16x3 GEMM)"
     achieved = flops / proj[prec] / 1e12
-    # DRAM bytes of one BF16x3 projection (pack, two tcgen05 launches, split-K reduction)
-    # from the ncu capture in profiles/tc_gemm_bf16x3_hub_L64_m2048.md (same kernels as
-    # timed here)
-    traffic = TC_TRAFFIC if (prec == "bf16x3" and args.workload == WORKLOAD) else None
+    sched = tuple(plan.get_stats()["tc_schedule"])
+    traffic = TC_TRAFFIC.get((prec, sched)) if args.workload == WORKLOAD else None
     roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
                 "frac": achieved / peak, "traffic": traffic, "kernel": f"projection ({prec})",
-                "peak_source": peak_note,
-                "traffic_source": ("ncu dram__bytes_read.sum + dram__bytes_write.sum of pack, both "
-                                   "GEMM stages and the split-K reduction, tile schedules [6, 17] "
-                                   "(profiles/tc_gemm_bf16x3_hub_L64_m2048.md)") if traffic else None}
+                "peak_source": peak_note, "tc_schedule": list(sched),
+                "traffic_source": ("ncu dram__bytes_read.sum + dram__bytes_write.sum of the "
+                                   f"projection launches, captured with tile schedules {list(sched)}")
+                if traffic else ("no ncu capture of these kernels with the tile schedules this run "
+                                 f"picked ({list(sched)})")}
 
-    # ---- CPU oracle baseline (rank 0, N = 1 only), bounded sample
+    # ---- CPU oracle baseline (rank 0, N = 1 only), bounded sample; its output is the
+    # reference for the projection error of every GPU arithmetic
     cpu = None
+    proj_err = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        val, reps, dt = cpu_oracle_projection_sample(sb, x0)
+        val, reps, dt, y_ref = cpu_oracle_projection_sample(sb, x0)
         cpu = {"value": val, "unit": "TFLOP/s", "cores": os.cpu_count(), "kind": "oracle",
                "sample": f"{reps} FP64 oracle projections (NumPy, Eq. 11) of the same "
                          f"superblock, {dt:.2f} s each"}
+        ymax = float(np.max(np.abs(y_ref)))
+        proj_err = {p: float(np.max(np.abs(proj_out[p] - y_ref)) / ymax) for p in variants}
 
     e_ref = infos[0]["energy"]  # start vector seeds[0], as the FP64-path solve
     if rank == 0:
@@ -480,9 +510,19 @@ def main():
                       "restarts": statistics.mean(i["restarts"] for i in infos), "energy": e_ref,
                       "resnorm": max(i["resnorm"] for i in infos), "plan_ms": plan_ms,
                       "fp64_path_solve_ms": fp64_solve_ms, "fp64_path_energy": e_fp64,
+                      "fp64_path_iters": solves["fp64"]["iters"],
                       "dE_vs_fp64_path": abs(e_ref - e_fp64),
                       "dE_between_steps": max(abs(i["energy"] - e_ref) for i in infos),
-                      "speedup_vs_fp64_path": (fp64_solve_ms / (t_step * 1e3)) if fp64_solve_ms else None},
+                      "speedup_vs_fp64_path": fp64_solve_ms / statistics.mean(solves[prec]["ms"]),
+                      "speedup_note": f"FP64-path solve vs this arithmetic's solve, both over start "
+                                      f"vectors {seeds[:nvar]} (host wall clock per solve)"},
+            "variants": {p: {"projection_ms": proj[p] * 1e3,
+                             "projection_tflops": flops / proj[p] / 1e12,
+                             "projection_err_vs_oracle": proj_err[p] if proj_err else None,
+                             "solve_ms": solves[p]["mean_ms"], "solve_ms_each": solves[p]["ms"],
+                             "iters": solves[p]["iters"],
+                             "dE_vs_fp64_path": max(abs(e - e_fp64) for e in solves[p]["energy"])}
+                         for p in variants},
             "projection_ms": {p: v * 1e3 for p, v in proj.items()},
             "roofline": roofline,
             "cpu_baseline": cpu,

@@ -65,18 +65,23 @@ typedef enum {
 /* Arithmetic of the projection GEMMs.  FP64: float64 operands and accumulation on the
  * FP64 units.  TF32: operands rounded to TF32 on the tensor cores, FP32 accumulation.
  * BF16X3: every operand split into three BF16 terms x = x0 + x1 + x2, the six products
- * with i + j <= 2 accumulated in FP32 on the tensor cores.  FP64_TC: FP64-accurate
- * products on the tensor cores: every operand row chunk (256 K elements) is split into a
- * power-of-two scale and seven integer base-128 digits held exactly in BF16; digit
- * products sharing a scale are summed exactly in FP32 and the scaled sums are combined in
- * FP32-pair (about 48-bit) arithmetic, then converted to float64.  The Davidson vector
- * work (overlaps, Gram-Schmidt, Rayleigh quotient, residual, small eigenproblem) is always
- * float64. */
+ * with i + j <= 2 accumulated in FP32 on the tensor cores.  BF16X2: the shorter split
+ * x = x0 + x1 (two BF16 terms, about 17 significant bits) with the three products
+ * x0 y0 + x0 y1 + x1 y0 accumulated in FP32 on the tensor cores: half the tensor work and
+ * two thirds of the operand bytes of BF16X3, at a larger projection error (meant for the
+ * mixed Davidson iteration, whose FP64-accurate anchors decide the answer).  FP64_TC:
+ * FP64-accurate products on the tensor cores: every operand row chunk (256 K elements) is
+ * split into a power-of-two scale and seven integer base-128 digits held exactly in BF16;
+ * digit products sharing a scale are summed exactly in FP32 and the scaled sums are
+ * combined in FP32-pair (about 48-bit) arithmetic, then converted to float64.  The Davidson
+ * vector work (overlaps, Gram-Schmidt, Rayleigh quotient, residual, small eigenproblem)
+ * keeps float64 accuracy in every mode. */
 typedef enum {
   DMRG_PREC_FP64 = 0,
   DMRG_PREC_TF32 = 1,
   DMRG_PREC_BF16X3 = 2,
-  DMRG_PREC_FP64_TC = 3
+  DMRG_PREC_FP64_TC = 3,
+  DMRG_PREC_BF16X2 = 4
 } dmrg_precision;
 
 enum { DMRG_HOST_DATA = 0, DMRG_DEVICE_DATA = 1 };
@@ -123,7 +128,7 @@ typedef struct {
    DMRG_VEC_FP64          FP64 units throughout.
    DMRG_VEC_DOUBLE_FLOAT  double-float (FP32 pairs, ~48 bits) on the FP32 units; measured
                           slower than FP64 at the sizes tested, kept as an option.
-   DMRG_VEC_SPLIT         mixed modes only (TF32/BF16X3 with fp64_refine): basis column 0
+   DMRG_VEC_SPLIT         mixed modes only (TF32/BF16X3/BF16X2 with fp64_refine): column 0
                           (the FP64 anchor) in FP64, the low-precision columns in FP32
                           arithmetic, whose rounding stays far below their projection
                           error; anchor iterations and the convergence test stay FP64.
@@ -151,7 +156,7 @@ typedef struct {
   int32_t vector_arith;  /* arithmetic of the Davidson vector passes (dmrg_vector_arith);
                             vectors are float64 in memory in every mode (default
                             DMRG_VEC_SPLIT)                                              */
-  int32_t autotune;      /* 1 (default): the first TF32/BF16X3 projection of a plan times
+  int32_t autotune;      /* 1 (default): the first TF32/BF16X3/BF16X2 projection of a plan times
                             the candidate tile schedules of both tensor-core GEMM stages
                             and keeps the fastest (that call synchronizes its stream and
                             must not be captured in a CUDA graph; dmrg_plan_autotune does
@@ -180,11 +185,11 @@ typedef struct {
                                (3 s + w) 3 + o: order o of the tile list that the CTAs take
                                tiles from (0: descending estimated time; 1: stage 1 grouped
                                by vector segment, stage 2 by right sector; 2: stage 1
-                               grouped by operator block, stage 2 by left sector), BF16x3
+                               grouped by operator block, stage 2 by left sector), BF16
                                tile width w (0: 128 columns; 1: 256 columns for tiles below
                                half the mean work per SM; 2: 256 wherever possible) and
                                stage-2 K split s (0: none; 1, 2: tiles above 2/3, 2/5 of the
-                               mean time per SM split into parts); -1 before a TF32/BF16X3
+                               mean time per SM split into parts); -1 before a low-precision
                                plan exists                                                 */
   float tc_tune_us[2][DMRG_TILE_SCHEDULES]; /* autotuner: median time of each schedule per
                                stage (us), 0 if not tuned or not a candidate               */
@@ -206,18 +211,20 @@ dmrg_status dmrg_plan_create(const dmrg_superblock_desc* desc, const dmrg_option
 void dmrg_plan_destroy(dmrg_plan* plan);
 dmrg_status dmrg_plan_get_stats(const dmrg_plan* plan, dmrg_plan_stats* stats);
 
-/* Tile-schedule autotuner of the tensor-core projection (prec DMRG_PREC_TF32 or
- * DMRG_PREC_BF16X3): builds the operand images if needed, times every candidate schedule
- * of each GEMM stage on this GPU (L2 flushed before each timing) and keeps the fastest;
- * the results appear in dmrg_plan_stats.  The paper has no counterpart (its records are
- * dispatched to streams by Algorithms 6-7).  Synchronizes the stream; allocates and frees
- * 256 MB of scratch. */
+/* Tile-schedule autotuner of the tensor-core projection (prec DMRG_PREC_TF32,
+ * DMRG_PREC_BF16X3 or DMRG_PREC_BF16X2): builds the operand images if needed, times every
+ * candidate schedule of each GEMM stage on this GPU (L2 flushed before each timing) and
+ * keeps the fastest; the results appear in dmrg_plan_stats (for the plan's own precision
+ * when its tensor-core plan exists, else for the first one built).  The paper has no
+ * counterpart (its records are dispatched to streams by Algorithms 6-7).  Synchronizes the
+ * stream; allocates and frees 256 MB of scratch. */
 dmrg_status dmrg_plan_autotune(dmrg_plan* plan, dmrg_precision prec, void* stream);
 
-/* Fixes the tile schedules of the tensor-core projection in precision prec (DMRG_PREC_TF32
- * or DMRG_PREC_BF16X3) to stage1 and stage2 (indices as in dmrg_plan_stats.tc_schedule;
- * stage 1 takes no K split, TF32 only 128-column tiles) and keeps the first projection
- * from autotuning; builds the operand images if needed and synchronizes the stream.
+/* Fixes the tile schedules of the tensor-core projection in precision prec (DMRG_PREC_TF32,
+ * DMRG_PREC_BF16X3 or DMRG_PREC_BF16X2) to stage1 and stage2 (indices as in
+ * dmrg_plan_stats.tc_schedule; stage 1 takes no K split, TF32 only 128-column tiles) and
+ * keeps the first projection from autotuning; builds the operand images if needed and
+ * synchronizes the stream.
  * DMRG_ERR_INVALID_ARG for an index that is not a candidate of its stage. */
 dmrg_status dmrg_plan_set_tile_schedule(dmrg_plan* plan, dmrg_precision prec, int32_t stage1,
                                         int32_t stage2, void* stream);

@@ -17,7 +17,7 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libdmrg_gb300.so")
 
-PREC = {"fp64": 0, "tf32": 1, "bf16x3": 2, "fp64tc": 3}
+PREC = {"fp64": 0, "tf32": 1, "bf16x3": 2, "fp64tc": 3, "bf16x2": 4}
 VEC = {"fp64": 0, "df": 1, "split": 2}
 TILE_SCHEDULES = 27  # DMRG_TILE_SCHEDULES: candidate tile schedules per GEMM stage
 IDENTITY = -1

@@ -13,8 +13,8 @@
 // fall-back to the raw residual on breakdown, restart to the Ritz vector when the basis
 // holds max_subspace columns (20 in Sec. 6.1), stop on ||r||_2 <= tol.
 //
-// Low-precision projections (TF32, BF16X3) carry an error of order eps * ||H||, which
-// bounds how small the computed residual can get.  The mixed mode therefore anchors the
+// Low-precision projections (TF32, BF16X3, BF16X2) carry an error of order eps * ||H||,
+// which bounds how small the computed residual can get.  The mixed mode therefore anchors the
 // iteration with float64 projections: the basis is collapsed to the Ritz vector x, which
 // is projected in FP64, so lambda = x^T H x is an FP64 Rayleigh quotient and the residual
 // W(:,0) - lambda x is exact.  Only such an exact residual can end the iteration.  Later
@@ -313,8 +313,10 @@ dmrg_status phase_b(dmrg_davidson_state* s, cudaStream_t st, bool* need_c) {
     for (int j = 1; j < k; ++j) ytail += h.y[j] * h.y[j];
     ytail = s->anchored ? std::sqrt(ytail) : 1.0;
     // relative error of one low-precision projection, measured against FP64 at the full
-    // workload sizes (BF16x3: 5e-6 of max|y|, FP32 accumulation over K ~ 1e3; TF32: 1e-3)
-    const double eps = s->plan->opt.prec == DMRG_PREC_TF32 ? 2e-3 : 5e-6;
+    // workload sizes (BF16x3: 5e-6 of max|y|, FP32 accumulation over K ~ 1e3; BF16x2:
+    // operands to 2^-18 and the dropped x1 y1 product, 3e-5; TF32: 1e-3)
+    const dmrg_precision lp = s->plan->opt.prec;
+    const double eps = lp == DMRG_PREC_TF32 ? 2e-3 : lp == DMRG_PREC_BF16X2 ? 3e-5 : 5e-6;
     // a plain restart folds the current low-precision error of W y into W(:,0): it stays
     // in the floor until the next FP64 anchor
     const double floor_est = eps * hnorm * ytail + s->baked_err;
@@ -648,8 +650,7 @@ dmrg_status dmrg_davidson_solve_batched(dmrg_plan* const* plans, int32_t nb,
   cudaEvent_t bdone = nullptr;
   std::vector<cudaEvent_t> ready(nb, nullptr);
   const dmrg_precision p0 = nb > 0 ? plans[0]->opt.prec : DMRG_PREC_FP64;
-  bool group = err == DMRG_OK && nb >= 2 && (int)owned.size() == nb &&
-               (p0 == DMRG_PREC_TF32 || p0 == DMRG_PREC_BF16X3);
+  bool group = err == DMRG_OK && nb >= 2 && (int)owned.size() == nb && tc_lowprec(p0);
   for (int i = 0; i < nb && group; ++i) group = plans[i]->opt.prec == p0;
   if (group) {
     if (cudaStreamCreateWithFlags(&bst, cudaStreamNonBlocking) != cudaSuccess ||

@@ -4,10 +4,12 @@
 // record with two proper factors; stage 2: one GEMM per output segment whose K dimension
 // concatenates every record writing that segment), but every GEMM runs as
 //     D[128 x N] (FP32, in TMEM) += A_tile[128 x K] . B_tile[N x K]^T,  N = 128 or 256
-// with both operands K-major in shared memory.  Two arithmetics:
+// with both operands K-major in shared memory.  Three arithmetics:
 //   TF32   : operands stored as FP32 rounded to TF32, one product per K step;
 //   BF16x3 : every operand stored as three BF16 planes x = x0 + x1 + x2 (24 significant
-//            bits); the six products x_i y_j with i + j <= 2 are accumulated in FP32.
+//            bits); the six products x_i y_j with i + j <= 2 are accumulated in FP32;
+//   BF16x2 : two BF16 planes x = x0 + x1 (about 17 significant bits); the three products
+//            x0 y0 + x0 y1 + x1 y0 are accumulated in FP32.
 //
 // Operand tiles are "images": the exact shared-memory byte image of a 128-row x 32-element
 // K-major tile in a swizzled canonical layout (BF16x3: 64-byte rows, 512-byte atoms; TF32:
@@ -262,6 +264,12 @@ pack_kernel(const PackChunk* __restrict__ chunks, const PackJob* __restrict__ jo
   grid_dep_launch();
 }
 
+// products of plane pairs per K step: TF32 1, BF16x2 3, BF16x3 6
+template <int PLANES>
+__host__ __device__ constexpr int kProducts() {
+  return PLANES == 3 ? 6 : PLANES == 2 ? 3 : 1;
+}
+
 // ---------------------------------------------------------------- grouped GEMM kernel
 // WIDE: tiles may be 256 columns wide (N = 256 MMA, B operand = two 128-row image tiles,
 // each plane of B in a 2 x CHUNK slot so that its 256 rows are contiguous; TMEM holds two
@@ -445,10 +453,10 @@ tc_gemm_kernel(const TcTile* __restrict__ tiles, int ntiles, const TcJob* __rest
             const uint32_t sa = smem_u32(smem + stage * kStage);
             const uint32_t sb = sa + kStageA;
 #pragma unroll
-            for (int pr = 0; pr < (PLANES == 3 ? 6 : 1); ++pr) {
-              // (pa, pb) in (0,0) (0,1) (1,0) (0,2) (1,1) (2,0)
-              const int pa = PLANES == 3 ? (pr == 0 ? 0 : pr == 1 ? 0 : pr == 2 ? 1 : pr == 3 ? 0 : pr == 4 ? 1 : 2) : 0;
-              const int pb = PLANES == 3 ? (pr == 0 ? 0 : pr == 1 ? 1 : pr == 2 ? 0 : pr == 3 ? 2 : pr == 4 ? 1 : 0) : 0;
+            for (int pr = 0; pr < kProducts<PLANES>(); ++pr) {
+              // plane pairs (pa, pb) with pa + pb < PLANES: (0,0) (0,1) (1,0) (0,2) (1,1) (2,0)
+              const int pa = pr == 0 ? 0 : pr == 1 ? 0 : pr == 2 ? 1 : pr == 3 ? 0 : pr == 4 ? 1 : 2;
+              const int pb = pr == 0 ? 0 : pr == 1 ? 1 : pr == 2 ? 0 : pr == 3 ? 2 : pr == 4 ? 1 : 0;
 #pragma unroll
               for (int kk = 0; kk < L::ROWB / 32; ++kk) {  // one MMA per 32 bytes of K
                 const uint64_t ad = L::desc(sa + pa * L::CHUNK + kk * 32);
@@ -600,7 +608,8 @@ tc_gemm_kernel(const TcTile* __restrict__ tiles, int ntiles, const TcJob* __rest
                 const uint32_t off = L::off(row, gbase + g);
                 *reinterpret_cast<uint4*>(tb + off) = make_uint4(w0[0], w0[1], w0[2], w0[3]);
                 *reinterpret_cast<uint4*>(tb + L::CHUNK + off) = make_uint4(w1[0], w1[1], w1[2], w1[3]);
-                *reinterpret_cast<uint4*>(tb + 2 * L::CHUNK + off) = make_uint4(w2[0], w2[1], w2[2], w2[3]);
+                if constexpr (PLANES == 3)
+                  *reinterpret_cast<uint4*>(tb + 2 * L::CHUNK + off) = make_uint4(w2[0], w2[1], w2[2], w2[3]);
               }
             }
           }
@@ -788,7 +797,7 @@ dmrg_status build_tc(dmrg_plan* p, dmrg_precision prec, cudaStream_t st, TcPlan*
   TcPlan* t = new TcPlan();
   t->prec = prec;
   const bool tf32 = prec == DMRG_PREC_TF32;
-  t->planes = tf32 ? 1 : 3;
+  t->planes = tf32 ? 1 : prec == DMRG_PREC_BF16X2 ? 2 : 3;
   t->kt_elems = tf32 ? tc::Layout<true>::KT : tc::Layout<false>::KT;
   t->chunk = tf32 ? tc::Layout<true>::CHUNK : tc::Layout<false>::CHUNK;
   const int planes = t->planes, KT = t->kt_elems;
@@ -1130,6 +1139,7 @@ dmrg_status build_tc(dmrg_plan* p, dmrg_precision prec, cudaStream_t st, TcPlan*
   if ((s = upload_vec(&d_opj, op_jobs, st)) != DMRG_OK) return fail(s);
   if ((s = upload_vec(&d_opc, op_chunks, st)) != DMRG_OK) return fail(s);
   if (tf32) s = launch_pack<1, true>(op_chunks, d_opc, d_opj, p->arena, nullptr, t->buf[TB_OPS], st);
+  else if (planes == 2) s = launch_pack<2, false>(op_chunks, d_opc, d_opj, p->arena, nullptr, t->buf[TB_OPS], st);
   else s = launch_pack<3, false>(op_chunks, d_opc, d_opj, p->arena, nullptr, t->buf[TB_OPS], st);
   cudaStreamSynchronize(st);
   cudaFree(d_opj);
@@ -1353,11 +1363,11 @@ void tc_batch_destroy(TcBatch* b) {
 dmrg_status tc_batch_create(dmrg_plan* const* plans, int nb, dmrg_precision prec,
                             cudaStream_t st, TcBatch** out) {
   *out = nullptr;
-  if (prec != DMRG_PREC_TF32 && prec != DMRG_PREC_BF16X3) {
-    set_error("internal: grouped launch needs a TF32 or BF16X3 plan");
+  if (!tc_lowprec(prec)) {
+    set_error("internal: grouped launch needs a TF32, BF16X3 or BF16X2 plan");
     return DMRG_ERR_INVALID_ARG;
   }
-  const int slot = prec == DMRG_PREC_TF32 ? 0 : 1;
+  const int slot = tc_slot(prec);
   TcBatch* b = new TcBatch();
   b->prec = prec;
   auto fail = [&](dmrg_status e) { tc_batch_destroy(b); return e; };
@@ -1410,7 +1420,7 @@ dmrg_status tc_batch_create(dmrg_plan* const* plans, int nb, dmrg_precision prec
     for (const Item& it : items[g]) {
       const TcJob& j = jobs[it.job];
       const int nn = ceil_div(j.N, kRows);
-      const bool wide_tiles = prec == DMRG_PREC_BF16X3 && 4 * it.cost <= mean;
+      const bool wide_tiles = prec != DMRG_PREC_TF32 && 4 * it.cost <= mean;
       for (int mt = 0; mt < ceil_div(j.M, kRows); ++mt)
         for (int nt = 0; nt < nn;) {
           const int w = (wide_tiles && nt + 1 < nn) ? 2 : 1;
@@ -1520,7 +1530,7 @@ dmrg_status run_batch(TcBatch* b, cudaStream_t st) {
 dmrg_status tc_batch_project(TcBatch* b, const double* const* x, double* const* y,
                              const char* active, cudaStream_t st) {
   DMRG_TRY(tc_batch_error(b));
-  const int slot = b->prec == DMRG_PREC_TF32 ? 0 : 1;
+  const int slot = tc_slot(b->prec);
   const int r = b->slot;
   b->slot ^= 1;
   // the pinned slot is rewritten only after its previous copy has completed
@@ -1544,12 +1554,11 @@ dmrg_status tc_batch_project(TcBatch* b, const double* const* x, double* const* 
                                 cudaMemcpyHostToDevice, st));
   DMRG_CUDA_TRY(cudaEventRecord(b->ev[r], st));
   if (b->prec == DMRG_PREC_TF32) return run_batch<1, 6, true>(b, st);
+  if (b->prec == DMRG_PREC_BF16X2) return run_batch<2, 4, false>(b, st);
   return run_batch<3, 3, false>(b, st);
 }
 
-bool tc_available(dmrg_precision prec) {
-  return prec == DMRG_PREC_TF32 || prec == DMRG_PREC_BF16X3 || prec == DMRG_PREC_FP64_TC;
-}
+bool tc_available(dmrg_precision prec) { return tc_lowprec(prec) || prec == DMRG_PREC_FP64_TC; }
 
 void destroy_tc(dmrg_plan* p) {
   if (!p) return;
@@ -1573,7 +1582,7 @@ dmrg_status tc_error_status(dmrg_plan* p) {
 
 dmrg_status launch_project_tc(dmrg_plan* p, dmrg_precision prec, const double* x, double* y,
                               cudaStream_t st) {
-  const int slot = prec == DMRG_PREC_TF32 ? 0 : 1;
+  const int slot = tc_slot(prec);
   if (!p->tc[slot]) {
     TcPlan* t = nullptr;
     DMRG_TRY(build_tc(p, prec, st, &t));
@@ -1582,14 +1591,16 @@ dmrg_status launch_project_tc(dmrg_plan* p, dmrg_precision prec, const double* x
   TcPlan* t = p->tc[slot];
   if (p->opt.autotune && !t->tuned) {
     if (prec == DMRG_PREC_TF32) DMRG_TRY((tune_tc<1, 6, true>(p, t, x, y, st)));
+    else if (prec == DMRG_PREC_BF16X2) DMRG_TRY((tune_tc<2, 4, false>(p, t, x, y, st)));
     else DMRG_TRY((tune_tc<3, 3, false>(p, t, x, y, st)));
   }
   if (prec == DMRG_PREC_TF32) return run_tc<1, 6, true>(p, t, x, y, st);
+  if (prec == DMRG_PREC_BF16X2) return run_tc<2, 4, false>(p, t, x, y, st);
   return run_tc<3, 3, false>(p, t, x, y, st);
 }
 
 dmrg_status tune_project_tc(dmrg_plan* p, dmrg_precision prec, cudaStream_t st) {
-  const int slot = prec == DMRG_PREC_TF32 ? 0 : 1;
+  const int slot = tc_slot(prec);
   if (!p->tc[slot]) {
     TcPlan* t = nullptr;
     DMRG_TRY(build_tc(p, prec, st, &t));
@@ -1603,15 +1614,16 @@ dmrg_status tune_project_tc(dmrg_plan* p, dmrg_precision prec, cudaStream_t st) 
     set_error("autotune: scratch allocation failed");
     return DMRG_ERR_OOM;
   }
-  dmrg_status s = prec == DMRG_PREC_TF32 ? tune_tc<1, 6, true>(p, t, p->D, y, st)
-                                         : tune_tc<3, 3, false>(p, t, p->D, y, st);
+  dmrg_status s = prec == DMRG_PREC_TF32     ? tune_tc<1, 6, true>(p, t, p->D, y, st)
+                  : prec == DMRG_PREC_BF16X2 ? tune_tc<2, 4, false>(p, t, p->D, y, st)
+                                             : tune_tc<3, 3, false>(p, t, p->D, y, st);
   cudaFreeAsync(y, st);
   return s;
 }
 
 dmrg_status set_schedule_tc(dmrg_plan* p, dmrg_precision prec, int stage1, int stage2,
                             cudaStream_t st) {
-  const int slot = prec == DMRG_PREC_TF32 ? 0 : 1;
+  const int slot = tc_slot(prec);
   if (!p->tc[slot]) {
     TcPlan* t = nullptr;
     DMRG_TRY(build_tc(p, prec, st, &t));
@@ -1634,7 +1646,9 @@ dmrg_status set_schedule_tc(dmrg_plan* p, dmrg_precision prec, int stage1, int s
 
 void tc_schedule_stats(const dmrg_plan* p, int32_t sched[2], float us[2][DMRG_TILE_SCHEDULES]) {
   static_assert(DMRG_TILE_SCHEDULES == kSchedules, "schedule count of the public stats");
-  const TcPlan* t = p->tc[1] ? p->tc[1] : p->tc[0];
+  // the plan's own low-precision arithmetic if built, else the first one built
+  const TcPlan* t = tc_lowprec(p->opt.prec) ? p->tc[tc_slot(p->opt.prec)] : nullptr;
+  for (int i = 0; i < 3 && !t; ++i) t = p->tc[i];
   for (int g = 0; g < 2; ++g) {
     sched[g] = t ? t->sched[g] : -1;
     for (int c = 0; c < kSchedules; ++c) us[g][c] = t ? t->tune_us[g][c] : 0.0f;

@@ -164,7 +164,7 @@ struct dmrg_plan {
   int64_t ntiles1 = 0, ntiles2 = 0;
   size_t device_bytes = 0;
 
-  dmrg::TcPlan* tc[2] = {nullptr, nullptr};  // TF32, BF16x3; built on first use
+  dmrg::TcPlan* tc[3] = {nullptr, nullptr, nullptr};  // TF32, BF16x3, BF16x2; built on first use
   dmrg::OzPlan* oz = nullptr;                 // FP64 emulation; built on first use
 };
 
@@ -192,6 +192,13 @@ dmrg_status tc_batch_error(const TcBatch* b);
 void tc_batch_destroy(TcBatch* b);
 void destroy_tc(dmrg_plan* plan);
 bool tc_available(dmrg_precision prec);
+// slot of a low-precision tensor-core plan in dmrg_plan::tc (TF32 0, BF16X3 1, BF16X2 2)
+inline int tc_slot(dmrg_precision prec) {
+  return prec == DMRG_PREC_TF32 ? 0 : prec == DMRG_PREC_BF16X3 ? 1 : 2;
+}
+inline bool tc_lowprec(dmrg_precision prec) {
+  return prec == DMRG_PREC_TF32 || prec == DMRG_PREC_BF16X3 || prec == DMRG_PREC_BF16X2;
+}
 dmrg_status tc_error_status(dmrg_plan* plan);
 // gemm_oz.cu
 dmrg_status launch_project_oz(dmrg_plan* plan, const double* x, double* y, cudaStream_t stream);

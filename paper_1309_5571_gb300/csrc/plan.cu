@@ -425,7 +425,7 @@ dmrg_status dmrg_plan_create(const dmrg_superblock_desc* desc, const dmrg_option
   if (opt) p->opt = *opt; else dmrg_options_default(&p->opt);
   if (p->opt.max_subspace < 2 || p->opt.max_subspace > DMRG_MAX_SUBSPACE ||
       p->opt.max_iter < 1 || !(p->opt.tol >= 0.0) ||
-      (int)p->opt.prec < 0 || (int)p->opt.prec > 3 ||
+      (int)p->opt.prec < 0 || (int)p->opt.prec > 4 ||
       (p->opt.anchor_prec != DMRG_PREC_FP64 && p->opt.anchor_prec != DMRG_PREC_FP64_TC) ||
       p->opt.vector_arith < DMRG_VEC_FP64 || p->opt.vector_arith > DMRG_VEC_SPLIT ||
       (p->opt.autotune != 0 && p->opt.autotune != 1) ||
@@ -518,8 +518,8 @@ dmrg_status dmrg_plan_autotune(dmrg_plan* p, dmrg_precision prec, void* stream) 
     set_error("NULL plan");
     return DMRG_ERR_INVALID_ARG;
   }
-  if (prec != DMRG_PREC_TF32 && prec != DMRG_PREC_BF16X3) {
-    set_error("autotune: precision must be DMRG_PREC_TF32 or DMRG_PREC_BF16X3");
+  if (!tc_lowprec(prec)) {
+    set_error("autotune: precision must be DMRG_PREC_TF32, DMRG_PREC_BF16X3 or DMRG_PREC_BF16X2");
     return DMRG_ERR_INVALID_ARG;
   }
   if (p->n == 0) return DMRG_OK;
@@ -535,8 +535,8 @@ dmrg_status dmrg_plan_set_tile_schedule(dmrg_plan* p, dmrg_precision prec, int32
     set_error("NULL plan");
     return DMRG_ERR_INVALID_ARG;
   }
-  if (prec != DMRG_PREC_TF32 && prec != DMRG_PREC_BF16X3) {
-    set_error("tile schedule: precision must be DMRG_PREC_TF32 or DMRG_PREC_BF16X3");
+  if (!tc_lowprec(prec)) {
+    set_error("tile schedule: precision must be DMRG_PREC_TF32, DMRG_PREC_BF16X3 or DMRG_PREC_BF16X2");
     return DMRG_ERR_INVALID_ARG;
   }
   if (p->n == 0) return DMRG_OK;
@@ -571,7 +571,7 @@ dmrg_status dmrg_project_prec(dmrg_plan* p, dmrg_precision prec, const double* x
   cudaStream_t st = (cudaStream_t)stream;
   if (prec == DMRG_PREC_FP64) return launch_project_fp64(p, x, y, st);
   if (prec == DMRG_PREC_FP64_TC) return launch_project_oz(p, x, y, st);
-  if (prec == DMRG_PREC_TF32 || prec == DMRG_PREC_BF16X3) return launch_project_tc(p, prec, x, y, st);
+  if (tc_lowprec(prec)) return launch_project_tc(p, prec, x, y, st);
   set_error("unknown precision %d", (int)prec);
   return DMRG_ERR_INVALID_ARG;
 }

@@ -1,11 +1,20 @@
 """Tensor-core (tcgen05) projections and the mixed-precision Davidson against the FP64
 oracle, on the GPU.
 
-Tolerances, derived from the arithmetic: BF16x3 keeps 24 significant bits per operand
-(dropped products are below 2^-24 relative) and accumulates in FP32, whose rounding grows
-with the accumulation length; two chained stages with K up to ~900 give a bound of a few
-hundred units of u = 2^-24 relative to max|y|: 2e-5.  TF32 keeps 11 significant bits
-(u = 2^-11 ~ 4.9e-4 per operand) on the small problems tested: 5e-3.
+Tolerances, derived from the arithmetic (all relative to max|y|):
+
+* BF16x3 keeps 24 significant bits per operand (dropped products are below 2^-24
+  relative) and accumulates in FP32, whose rounding grows with the accumulation length;
+  two chained stages with K up to ~900 give a bound of a few hundred units of
+  u = 2^-24: 2e-5.
+* BF16x2 represents each operand as x0 + x1 to 2^-18 relative (x0 = rn(x) to 2^-9, x1 =
+  rn(x - x0) to 2^-9 of the remainder) and drops x1 y1 (below 2^-18 |x y|): at most
+  3 * 2^-18 = 1.1e-5 per product and per stage, twice (the stage-1 result is split
+  again), times the cancellation of the sums (sum |terms| / max|y|, a few on these
+  operators), plus the FP32 accumulation of BF16x3: 2e-4.
+* TF32 rounds each operand to 11 significant bits (2^-11 = 4.9e-4 relative): two
+  operands and the rounded intermediate, times the same cancellation: 5e-3.
+
 The mixed Davidson ends only on an FP64 residual, so its energy meets |dE| <= 1e-10.
 """
 import numpy as np
@@ -28,11 +37,12 @@ from paper_1309_5571_gb300 import Plan, capi  # noqa: E402
 
 from test_gpu_parity import PROBLEMS, problem, rel_err, cuda  # noqa: E402
 
-TOL = {"bf16x3": 2e-5, "tf32": 5e-3}
+TOL = {"bf16x3": 2e-5, "bf16x2": 2e-4, "tf32": 5e-3}
+LOWPREC = ["bf16x3", "bf16x2", "tf32"]
 E_TOL = 1e-10
 
 
-@pytest.mark.parametrize("prec", ["bf16x3", "tf32"])
+@pytest.mark.parametrize("prec", LOWPREC)
 @pytest.mark.parametrize("name", list(PROBLEMS))
 def test_projection_tensor_core_matches_oracle(name, prec):
     sb = problem(name)
@@ -54,7 +64,7 @@ def test_projection_tensor_core_repeatable():
 
 
 @pytest.mark.parametrize("name", ["heis_L16_m64", "hub_L8_m40", "hub_quarter_L12_m48", "ragged"])
-@pytest.mark.parametrize("prec", ["bf16x3", "tf32"])
+@pytest.mark.parametrize("prec", LOWPREC)
 def test_mixed_davidson_matches_oracle(name, prec):
     sb = problem(name)
     x0 = warmup.start_vector(sb.n, seed=0)
@@ -76,10 +86,10 @@ NSCHED = capi.TILE_SCHEDULES  # (3 s + w) 3 + o: K split s, tile width w, order 
 def candidates(prec, stage):
     """Tile schedules of a GEMM stage: stage 1 takes no K split, TF32 only 128-column tiles."""
     return [c for c in range(NSCHED)
-            if (stage == 2 or c // 9 == 0) and (prec == "bf16x3" or (c // 3) % 3 == 0)]
+            if (stage == 2 or c // 9 == 0) and (prec != "tf32" or (c // 3) % 3 == 0)]
 
 
-@pytest.mark.parametrize("prec", ["bf16x3", "tf32"])
+@pytest.mark.parametrize("prec", LOWPREC)
 def test_autotuned_schedule(prec):
     # the tuner times exactly the candidates of each stage and keeps one of them; schedules
     # without a K split compute every output element in the same CTA arithmetic, so the
@@ -106,7 +116,7 @@ def test_autotuned_schedule(prec):
     assert all(c in candidates(prec, g + 1) for g, c in enumerate(p2.get_stats()["tc_schedule"]))
 
 
-@pytest.mark.parametrize("prec", ["bf16x3", "tf32"])
+@pytest.mark.parametrize("prec", LOWPREC)
 @pytest.mark.parametrize("name", ["hub_L8_m40", "ragged", "heis_L16_m64"])
 def test_every_tile_schedule_matches_oracle(name, prec):
     # each candidate schedule of each stage (the other stage on schedule 0) against the
@@ -136,7 +146,7 @@ def test_tile_schedule_rejects_non_candidates():
             plan.set_tile_schedule(*bad)
     tf = Plan(sb, prec="tf32", autotune=False)
     with pytest.raises(capi.DmrgError):
-        tf.set_tile_schedule(0, 3, prec="tf32")   # 256-column tiles: BF16x3 only
+        tf.set_tile_schedule(0, 3, prec="tf32")   # 256-column tiles: BF16 splits only
 
 
 @pytest.mark.parametrize("name", ["heis_L16_m64", "hub_quarter_L12_m48", "ragged"])
@@ -158,7 +168,8 @@ def test_mixed_davidson_vector_arithmetic(name):
 
 @pytest.fixture(scope="module")
 def hub_L64_m2048():
-    return warmup.workload("hub_L64_m2048")
+    from _workloads import workload
+    return workload("hub_L64_m2048")
 
 
 def test_full_size_projection_hubbard_m2048_bf16x3(hub_L64_m2048):
@@ -175,6 +186,22 @@ def test_full_size_projection_hubbard_m2048_bf16x3(hub_L64_m2048):
         plan.set_tile_schedule(4, s2)
         ys = plan.project(cuda(x)).cpu().numpy()
         assert rel_err(ys, y_ref) <= TOL["bf16x3"], (s2, rel_err(ys, y_ref))
+
+
+@pytest.mark.parametrize("prec", ["bf16x2", "tf32"])
+def test_full_size_projection_hubbard_m2048_lowprec(hub_L64_m2048, prec):
+    # the other low-precision arithmetics at full size, on every schedule family the
+    # autotuner may pick for stage 2 (LPT order, K split), against the oracle
+    sb = hub_L64_m2048
+    plan = Plan(sb, prec=prec)
+    x = warmup.start_vector(sb.n, seed=5)
+    y_ref = oproj.project_blocks(sb, x)
+    y = plan.project(cuda(x)).cpu().numpy()
+    assert rel_err(y, y_ref) <= TOL[prec], (prec, rel_err(y, y_ref))
+    for s2 in (9, 18):
+        plan.set_tile_schedule(0, s2, prec=prec)
+        ys = plan.project(cuda(x)).cpu().numpy()
+        assert rel_err(ys, y_ref) <= TOL[prec], (prec, s2, rel_err(ys, y_ref))
 
 
 def test_full_size_mixed_solve_hubbard_m2048_properties(hub_L64_m2048):

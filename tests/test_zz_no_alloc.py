@@ -54,3 +54,50 @@ def test_noalloc_rejects_more_columns_than_its_scratch_holds():
     st = lib.dmrg_gemv_trans_noalloc(V.data_ptr(), 8, 8, 25, w.data_ptr(), s.data_ptr(), None)
     assert st == 1
     assert b"outside [1, 24]" in lib.dmrg_last_error()
+
+
+@pytest.mark.parametrize("n,k", [(0, 1), (1, 24), (300, 5), (1, 1)])
+def test_noalloc_edge_shapes_match_numpy(n, k):
+    # empty input (s = 0), one row, and fewer rows than the grid has threads (most blocks
+    # write zero partial sums), against NumPy and against the allocating entry point
+    lib = capi.load()
+    rng = np.random.default_rng(100 + n + k)
+    ldv = max(n, 1) + 5
+    Vh = rng.standard_normal((k, ldv))
+    wh = rng.standard_normal(max(n, 1))[:n]
+    V = torch.from_numpy(Vh).cuda()
+    w = torch.from_numpy(np.ascontiguousarray(wh)).cuda() if n else torch.zeros(1, dtype=torch.float64, device="cuda")
+    s = torch.full((k,), float("nan"), dtype=torch.float64, device="cuda")
+    st = lib.dmrg_gemv_trans_noalloc(V.data_ptr(), ldv, n, k, w.data_ptr(), s.data_ptr(),
+                                     torch.cuda.current_stream().cuda_stream)
+    assert st == 0, lib.dmrg_last_error()
+    torch.cuda.synchronize()
+    got = s.cpu().numpy()
+    exact = Vh[:, :n] @ wh
+    np.testing.assert_allclose(got, exact, rtol=1e-12, atol=1e-12 * max(n, 1))
+    if n:
+        np.testing.assert_allclose(got, _call(lib.dmrg_gemv_trans, V, k, w[:n]), rtol=1e-12,
+                                   atol=1e-12 * n)
+
+
+def test_noalloc_allocates_no_device_memory():
+    # the call's contract: no device allocation.  After a warm-up call (which loads the
+    # kernel and looks up the scratch address), repeated calls leave the free device memory
+    # exactly where it was; the output and inputs are allocated by the caller beforehand
+    lib = capi.load()
+    rng = np.random.default_rng(5)
+    n, k = 200003, 17
+    V = torch.from_numpy(rng.standard_normal((k, n))).cuda()
+    w = torch.from_numpy(rng.standard_normal(n)).cuda()
+    s = torch.empty(k, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream().cuda_stream
+    assert lib.dmrg_gemv_trans_noalloc(V.data_ptr(), n, n, k, w.data_ptr(), s.data_ptr(), stream) == 0
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(5):
+        assert lib.dmrg_gemv_trans_noalloc(V.data_ptr(), n, n, k, w.data_ptr(), s.data_ptr(), stream) == 0
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+    np.testing.assert_allclose(s.cpu().numpy(), V.cpu().numpy() @ w.cpu().numpy(), rtol=1e-12,
+                               atol=1e-12 * n)
