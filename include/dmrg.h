@@ -288,6 +288,26 @@ dmrg_status dmrg_davidson_solve(dmrg_plan* plan, const double* x0, double* x_out
 dmrg_status dmrg_davidson_solve_batched(dmrg_plan* const* plans, int32_t nb,
                                         const double* const* x0, double* const* x_out,
                                         dmrg_solve_info* infos, void* stream);
+/* Lowest nev eigenpairs by the block Davidson-Liu iteration that Sec. 6 names as the
+ * block extension of Algorithm 3: every iteration adds the corrections of the unconverged
+ * ones among the `block` lowest Ritz pairs (block >= nev), each orthonormalised (classical
+ * Gram-Schmidt twice) against the basis and the corrections added before it; when they do
+ * not fit in max_subspace columns the basis is collapsed to the current Ritz block and (with
+ * restart_keep = 2) as much of the previous one as leaves room.  Projections are
+ * FP64-accurate: the plan's precision if it is DMRG_PREC_FP64 or DMRG_PREC_FP64_TC, else its
+ * anchor_prec; the vector passes are FP64.  X0: device, column-major n x block start block
+ * (leading dimension ldx0 >= n), orthonormalised by the call (DMRG_ERR_INVALID_ARG if it is
+ * rank deficient).  X_out: device, column-major n x nev (ldx_out >= n), the Ritz vectors of
+ * the nev lowest pairs in ascending order.  energies (host, nev): their Ritz values;
+ * resnorms (host, nev, may be NULL): ||H x - theta x||_2.  info (may be NULL): iters,
+ * fp64_projections (all projections), restarts, converged; energy and resnorm of the lowest
+ * pair.  Needs 1 <= nev <= block <= 8 and 2 block <= max_subspace.  Synchronizes the stream;
+ * DMRG_ERR_NOT_CONVERGED with everything filled when max_iter is reached. */
+dmrg_status dmrg_davidson_solve_block(dmrg_plan* plan, int32_t nev, int32_t block,
+                                      const double* X0, int64_t ldx0, double* X_out,
+                                      int64_t ldx_out, double* energies, double* resnorms,
+                                      dmrg_solve_info* info, void* stream);
+
 /* Same, with x0 and x_out in host memory: the host-to-device copy of x0 and the
  * device-to-host copy of x_out are part of the call. */
 dmrg_status dmrg_davidson_solve_host(dmrg_plan* plan, const double* x0_host,

@@ -120,6 +120,9 @@ SIGNATURES = {
     "dmrg_davidson_solve_batched": (C.c_int, [C.POINTER(C.c_void_p), C.c_int32,
                                               C.POINTER(C.c_void_p), C.POINTER(C.c_void_p),
                                               C.POINTER(SolveInfo), C.c_void_p]),
+    "dmrg_davidson_solve_block": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_int64,
+                                            C.c_void_p, C.c_int64, C.POINTER(C.c_double),
+                                            C.POINTER(C.c_double), C.POINTER(SolveInfo), C.c_void_p]),
     "dmrg_precision_available": (C.c_int32, [C.c_int]),
     "dmrg_kernel_launches": (C.c_int64, []),
     "dmrg_status_string": (C.c_char_p, [C.c_int]),
@@ -326,6 +329,29 @@ class Plan:
         _check(self.lib.dmrg_davidson_solve_host(self.handle, x0.ctypes.data, x_out.ctypes.data,
                                                  C.byref(info), _stream_ptr(stream)))
         return x_out, info.as_dict()
+
+    def solve_block(self, X0, nev, X_out=None, stream=None, raise_on_nonconvergence=True):
+        """dmrg_davidson_solve_block: the nev lowest eigenpairs from a start block X0 given as a
+        contiguous CUDA float64 tensor of shape (block, n) (row c = start vector c, i.e. a
+        column-major n x block matrix).  Returns (X of shape (nev, n), energies, resnorms, info)."""
+        torch = _torch()
+        if not (isinstance(X0, torch.Tensor) and X0.is_cuda and X0.dtype == torch.float64
+                and X0.is_contiguous() and X0.dim() == 2 and X0.shape[1] == self.n):
+            raise ValueError(f"X0 must be a contiguous CUDA float64 tensor of shape (block, {self.n})")
+        block = X0.shape[0]
+        if X_out is None:
+            X_out = torch.empty((nev, self.n), dtype=torch.float64, device=X0.device)
+        if not (X_out.is_contiguous() and tuple(X_out.shape) == (nev, self.n) and X_out.dtype == torch.float64):
+            raise ValueError(f"X_out must be a contiguous float64 tensor of shape ({nev}, {self.n})")
+        e = (C.c_double * nev)()
+        r = (C.c_double * nev)()
+        info = SolveInfo()
+        st = self.lib.dmrg_davidson_solve_block(self.handle, int(nev), int(block), X0.data_ptr(), self.n,
+                                                X_out.data_ptr(), self.n, e, r, C.byref(info),
+                                                _stream_ptr(stream))
+        if not (st == 5 and not raise_on_nonconvergence):
+            _check(st)
+        return X_out, list(e), list(r), info.as_dict()
 
     def state(self, x0, stream=None) -> "DavidsonState":
         return DavidsonState(self, x0, stream)

@@ -377,7 +377,64 @@ __global__ void __launch_bounds__(kEigThreads) small_eig_kernel(DevSmall* small,
   if (tid < KMAX) small->y[tid] = tid < k ? Q64[tid][best] : 0.0;
 }
 
+// All eigenpairs of the k x k symmetric B in FP64, in ascending order (the block iteration
+// needs the b lowest pairs, not only the lowest): a cold cyclic Jacobi solve with FP64
+// rotations on B, then the eigenvalues sorted; theta[j] is the j-th smallest and column j
+// of Q (Q[r * KMAX + j]) its eigenvector.
+__global__ void __launch_bounds__(kEigThreads) all_eig_kernel(DevSmall* small, int k) {
+  __shared__ double A64[KMAX][KMAX + 1];
+  __shared__ double Q64[KMAX][KMAX + 1];
+  __shared__ double cs64[KMAX / 2], sn64[KMAX / 2];
+  __shared__ Schedule sch;
+  __shared__ int rotated;
+  __shared__ int order[KMAX];
+  __shared__ double scale64;
+  const int tid = threadIdx.x;
+  sch.build((k + 1) & ~1);
+  for (int e = tid; e < KMAX * KMAX; e += blockDim.x) {
+    const int r = e / KMAX, c = e - (e / KMAX) * KMAX;
+    A64[r][c] = (r < k && c < k) ? small->B[r * KMAX + c] : 0.0;
+    Q64[r][c] = (r == c) ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    double sc = 0.0;
+    for (int i = 0; i < k; ++i)
+      for (int j = 0; j < k; ++j) sc = fmax(sc, fabs(A64[i][j]));
+    scale64 = sc;
+  }
+  __syncthreads();
+  const double abs64 = 1e-17 * scale64;
+  const int sweeps = jacobi_sweeps<double>(A64, Q64, k, 1e-30, abs64 * abs64, 40, sch, cs64, sn64, &rotated);
+  if (tid == 0) {
+    // ascending order of the diagonal (selection sort of at most 24 values)
+    for (int i = 0; i < k; ++i) order[i] = i;
+    for (int i = 0; i < k; ++i) {
+      int m = i;
+      for (int j = i + 1; j < k; ++j)
+        if (A64[order[j]][order[j]] < A64[order[m]][order[m]]) m = j;
+      const int w = order[i];
+      order[i] = order[m];
+      order[m] = w;
+    }
+    small->jacobi_sweeps = sweeps;
+    small->qk = 0;  // not a warm start for the single-vector solver
+  }
+  __syncthreads();
+  for (int e = tid; e < KMAX * KMAX; e += blockDim.x) {
+    const int r = e / KMAX, c = e - (e / KMAX) * KMAX;
+    small->Q[e] = (r < k && c < k) ? Q64[r][order[c]] : 0.0;
+  }
+  if (tid < KMAX) small->theta[tid] = tid < k ? A64[order[tid]][order[tid]] : 0.0;
+}
+
 }  // namespace
+
+dmrg_status launch_all_eig(DevSmall* small, int k, cudaStream_t st) {
+  all_eig_kernel<<<1, kEigThreads, 0, st>>>(small, k);
+  DMRG_LAUNCH_CHECK();
+  return DMRG_OK;
+}
 
 dmrg_status launch_jacobi(DevSmall* small, int k, cudaStream_t st) {
   small_eig_kernel<<<1, kEigThreads, 0, st>>>(small, k);

@@ -246,6 +246,8 @@ dmrg_status launch_overlap(const VecWork& w, const double* V, int64_t ldv, int64
                            int k, const double* vec, double* s_out, DevSmall* small,
                            int Bcol, cudaStream_t st, const double* w0 = nullptr);
 dmrg_status launch_jacobi(DevSmall* small, int k, cudaStream_t st);
+// all eigenpairs of B (k x k) in FP64, ascending: theta[j] and column j of Q
+dmrg_status launch_all_eig(DevSmall* small, int k, cudaStream_t st);
 // r = W y - lambda V y, t = r / (lambda - D) (mode 0) or t = r (mode 1) into tcol;
 // reductions: rnorm2, s[0] = V^T t, tnorm2_before.
 dmrg_status launch_residual(const VecWork& w, const double* V, const double* W,
