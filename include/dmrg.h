@@ -161,6 +161,13 @@ typedef struct {
                             and keeps the fastest (that call synchronizes its stream and
                             must not be captured in a CUDA graph; dmrg_plan_autotune does
                             it ahead of time); 0: descending-cost schedule              */
+  int32_t graphs;        /* 1 (default): a TF32/BF16X3/BF16X2 projection is replayed from a
+                            CUDA graph of its launch sequence (pack, both GEMM stages, the
+                            split-K reduction), captured on first use for each pair of
+                            vector pointers and tile schedules on a stream owned by the
+                            plan; a call made while the caller's stream is being captured
+                            launches the kernels directly into that capture; 0: direct
+                            launches always.  The results are identical either way.       */
 } dmrg_options;
 
 typedef struct {

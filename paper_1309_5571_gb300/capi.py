@@ -66,7 +66,7 @@ class Options(C.Structure):
     _fields_ = [("prec", C.c_int32), ("tol", C.c_double), ("max_iter", C.c_int32),
                 ("max_subspace", C.c_int32), ("restart_keep", C.c_int32), ("fp64_refine", C.c_int32),
                 ("refine_ratio", C.c_double), ("anchor_prec", C.c_int32),
-                ("vector_arith", C.c_int32), ("autotune", C.c_int32)]
+                ("vector_arith", C.c_int32), ("autotune", C.c_int32), ("graphs", C.c_int32)]
 
 
 class SolveInfo(C.Structure):
@@ -223,7 +223,8 @@ def marshal(sb) -> _Marshalled:
 
 
 def options(prec="fp64", tol=1e-10, max_iter=1000, max_subspace=20, restart_keep=2, fp64_refine=True,
-            refine_ratio=0.0, anchor_prec="fp64", vector_arith="split", autotune=True) -> Options:
+            refine_ratio=0.0, anchor_prec="fp64", vector_arith="split", autotune=True,
+            graphs=True) -> Options:
     o = Options()
     load().dmrg_options_default(C.byref(o))
     o.prec = PREC[prec] if isinstance(prec, str) else int(prec)
@@ -236,6 +237,7 @@ def options(prec="fp64", tol=1e-10, max_iter=1000, max_subspace=20, restart_keep
     o.anchor_prec = PREC[anchor_prec] if isinstance(anchor_prec, str) else int(anchor_prec)
     o.vector_arith = VEC[vector_arith] if isinstance(vector_arith, str) else int(vector_arith)
     o.autotune = int(bool(autotune))
+    o.graphs = int(bool(graphs))
     return o
 
 

@@ -12,6 +12,7 @@ static thread_local char g_last_error[1024] = "";
 static std::atomic<int64_t> g_launches{0};
 
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void note_launches(int64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 void set_error(const char* fmt, ...) {
   va_list ap;
@@ -36,6 +37,7 @@ void dmrg_options_default(dmrg_options* opt) {
   opt->anchor_prec = DMRG_PREC_FP64;
   opt->vector_arith = DMRG_VEC_SPLIT;
   opt->autotune = 1;
+  opt->graphs = 1;
 }
 
 const char* dmrg_status_string(dmrg_status s) {

@@ -40,8 +40,12 @@ struct dmrg_davidson_state {
   dmrg_plan* plan = nullptr;
   int64_t n = 0, ldv = 0;
   int kmax = 20;
-  double* V = nullptr;     // (kmax + 1) columns
-  double* W = nullptr;     // kmax columns
+  double* V = nullptr;     // (kmax + 1) columns (split arithmetic: column 0 only)
+  double* W = nullptr;     // kmax columns (split arithmetic: column 0 only)
+  bool f32 = false;        // split arithmetic: columns >= 1 of V and W stored in FP32
+  float* V32 = nullptr;    // kmax + 1 FP32 columns (column 0 unused)
+  float* W32 = nullptr;    // kmax FP32 columns (column 0 unused)
+  double* tbuf = nullptr;  // split arithmetic: the new direction t while it is formed
   double* D = nullptr;     // padded diag(H_SB)
   double* xbuf = nullptr;  // Ritz vector at a restart
   double* wbuf = nullptr;  // W y at a restart
@@ -96,21 +100,27 @@ int vec_mode(const dmrg_davidson_state* s) {
   if (a == DMRG_VEC_SPLIT) return s->mixed ? DMRG_VEC_SPLIT : DMRG_VEC_FP64;
   return a;
 }
-dmrg_status ov(dmrg_davidson_state* s, int k, const double* vec, double* s_out, int Bcol,
-               cudaStream_t st, const double* w0 = nullptr) {
+// the FP64 work column of the new direction t (basis column k without split storage)
+double* tcol_of(dmrg_davidson_state* s, int k) { return s->f32 ? s->tbuf : s->V + (int64_t)k * s->ldv; }
+
+// overlap with vec64 (FP64) or, with split storage, vec32 (an FP32 basis column)
+dmrg_status ov(dmrg_davidson_state* s, int k, const double* vec64, const float* vec32,
+               double* s_out, int Bcol, cudaStream_t st, const double* w0 = nullptr) {
   switch (vec_mode(s)) {
     case DMRG_VEC_SPLIT:
-      return launch_overlap_split(s->vw, s->V, s->ldv, s->n, k, vec, s_out, s->small, Bcol, st, w0);
+      return launch_overlap_split(s->vw, s->V, s->V32, s->ldv, s->n, k, vec64, vec32, s_out, s->small,
+                                  Bcol, st, w0);
     case DMRG_VEC_DOUBLE_FLOAT:
-      return launch_overlap_df(s->vw, s->V, s->ldv, s->n, k, vec, s_out, s->small, Bcol, st, w0);
+      return launch_overlap_df(s->vw, s->V, s->ldv, s->n, k, vec64, s_out, s->small, Bcol, st, w0);
     default:
-      return launch_overlap(s->vw, s->V, s->ldv, s->n, k, vec, s_out, s->small, Bcol, st, w0);
+      return launch_overlap(s->vw, s->V, s->ldv, s->n, k, vec64, s_out, s->small, Bcol, st, w0);
   }
 }
 dmrg_status res(dmrg_davidson_state* s, int k, double* tcol, int mode, cudaStream_t st) {
   switch (vec_mode(s)) {
     case DMRG_VEC_SPLIT:
-      return launch_residual_split(s->vw, s->V, s->W, s->D, s->ldv, s->n, k, tcol, s->small, mode, st);
+      return launch_residual_split(s->vw, s->V, s->W, s->V32, s->W32, s->D, s->ldv, s->n, k, tcol,
+                                   s->small, mode, st);
     case DMRG_VEC_DOUBLE_FLOAT:
       return launch_residual_df(s->vw, s->V, s->W, s->D, s->ldv, s->n, k, tcol, s->small, mode, st);
     default:
@@ -121,7 +131,7 @@ dmrg_status cgs(dmrg_davidson_state* s, int k, double* tcol, int sin, int sout, 
                 cudaStream_t st) {
   switch (vec_mode(s)) {
     case DMRG_VEC_SPLIT:
-      return launch_cgs_split(s->vw, s->V, s->ldv, s->n, k, tcol, s->small, sin, sout, st, second);
+      return launch_cgs_split(s->vw, s->V, s->V32, s->ldv, s->n, k, tcol, s->small, sin, sout, st, second);
     case DMRG_VEC_DOUBLE_FLOAT:
       return launch_cgs_df(s->vw, s->V, s->ldv, s->n, k, tcol, s->small, sin, sout, st, second);
     default:
@@ -129,16 +139,35 @@ dmrg_status cgs(dmrg_davidson_state* s, int k, double* tcol, int sin, int sout, 
   }
 }
 
+// normalise t; with split storage it is also appended as FP32 basis column k
 dmrg_status fin(dmrg_davidson_state* s, int k, double* tcol, cudaStream_t st) {
   if (vec_mode(s) == DMRG_VEC_SPLIT)
-    return launch_finish_split(s->vw, s->V, tcol, s->n, k, s->small, st);
+    return launch_finish_split(s->vw, s->V, tcol, s->n, k, s->small, s->V32 + (int64_t)k * s->ldv, st);
   return launch_finish(tcol, s->n, s->small, st);
+}
+
+// x (and wx) = V y over the first k columns, into padded buffers
+dmrg_status ritz(dmrg_davidson_state* s, int k, double* x, double* wx, cudaStream_t st) {
+  if (s->f32)
+    return launch_ritz_split(s->vw, s->V, s->W, s->V32, s->W32, s->ldv, s->n, k, s->small, x, wx, st);
+  return launch_ritz(s->V, s->W, s->ldv, s->n, k, s->small, x, wx, st);
 }
 
 dmrg_status project_col(dmrg_davidson_state* s, int col, bool fp64, cudaStream_t st) {
   // FP64-accurate projections (FP64 mode, or an anchor of a mixed mode) use FP64 units
   // or the FP64-emulating tensor-core path, as the options say
   dmrg_precision prec = s->plan->opt.prec;
+  if (s->f32 && col > 0) {
+    // a low-precision column in FP32 storage (anchors are always column 0)
+    if (fp64) {
+      set_error("internal: FP64 projection of an FP32 basis column");
+      return DMRG_ERR_INVALID_ARG;
+    }
+    DMRG_TRY(launch_project_tc32(s->plan, prec, s->V32 + (int64_t)col * s->ldv,
+                                 s->W32 + (int64_t)col * s->ldv, st));
+    s->projections++;
+    return DMRG_OK;
+  }
   if (fp64) prec = s->plan->opt.prec == DMRG_PREC_FP64_TC ? DMRG_PREC_FP64_TC : s->plan->opt.anchor_prec;
   DMRG_TRY(dmrg_project_prec(s->plan, prec, s->V + col * s->ldv, s->W + col * s->ldv, st));
   if (prec == DMRG_PREC_FP64 || prec == DMRG_PREC_FP64_TC) s->fp64_projections++;
@@ -173,10 +202,16 @@ dmrg_status dmrg_state_create(dmrg_plan* plan, const double* x0, void* stream,
   s->kmax = plan->opt.max_subspace;
   s->mixed = plan->opt.prec != DMRG_PREC_FP64 && plan->opt.prec != DMRG_PREC_FP64_TC &&
              plan->opt.fp64_refine;
+  s->f32 = s->mixed && plan->opt.vector_arith == DMRG_VEC_SPLIT;
   auto fail = [&](dmrg_status e) { dmrg_state_destroy(s); return e; };
   const size_t col = sizeof(double) * (size_t)s->ldv;
-  if (cudaMalloc((void**)&s->V, col * (s->kmax + 1)) != cudaSuccess ||
-      cudaMalloc((void**)&s->W, col * s->kmax) != cudaSuccess ||
+  const size_t col32 = sizeof(float) * (size_t)s->ldv;
+  const int cV = s->f32 ? 1 : s->kmax + 1, cW = s->f32 ? 1 : s->kmax;
+  if (cudaMalloc((void**)&s->V, col * cV) != cudaSuccess ||
+      cudaMalloc((void**)&s->W, col * cW) != cudaSuccess ||
+      (s->f32 && (cudaMalloc((void**)&s->V32, col32 * (s->kmax + 1)) != cudaSuccess ||
+                  cudaMalloc((void**)&s->W32, col32 * s->kmax) != cudaSuccess ||
+                  cudaMalloc((void**)&s->tbuf, col) != cudaSuccess)) ||
       cudaMalloc((void**)&s->D, col) != cudaSuccess ||
       cudaMalloc((void**)&s->xbuf, col) != cudaSuccess ||
       cudaMalloc((void**)&s->wbuf, col) != cudaSuccess ||
@@ -191,8 +226,11 @@ dmrg_status dmrg_state_create(dmrg_plan* plan, const double* x0, void* stream,
   }
   dmrg_status e = vec_work_create(&s->vw);
   if (e != DMRG_OK) return fail(e);
-  if (cudaMemsetAsync(s->V, 0, col * (s->kmax + 1), st) != cudaSuccess ||
-      cudaMemsetAsync(s->W, 0, col * s->kmax, st) != cudaSuccess ||
+  if (cudaMemsetAsync(s->V, 0, col * cV, st) != cudaSuccess ||
+      cudaMemsetAsync(s->W, 0, col * cW, st) != cudaSuccess ||
+      (s->f32 && (cudaMemsetAsync(s->V32, 0, col32 * (s->kmax + 1), st) != cudaSuccess ||
+                  cudaMemsetAsync(s->W32, 0, col32 * s->kmax, st) != cudaSuccess ||
+                  cudaMemsetAsync(s->tbuf, 0, col, st) != cudaSuccess)) ||
       cudaMemsetAsync(s->D, 0, col, st) != cudaSuccess ||
       cudaMemsetAsync(s->xbuf, 0, col, st) != cudaSuccess ||
       cudaMemsetAsync(s->wbuf, 0, col, st) != cudaSuccess ||
@@ -217,6 +255,9 @@ void dmrg_state_destroy(dmrg_davidson_state* s) {
   if (!s) return;
   cudaFree(s->V);
   cudaFree(s->W);
+  cudaFree(s->V32);
+  cudaFree(s->W32);
+  cudaFree(s->tbuf);
   cudaFree(s->D);
   cudaFree(s->xbuf);
   cudaFree(s->wbuf);
@@ -261,9 +302,10 @@ dmrg_status phase_a_end(dmrg_davidson_state* s, cudaStream_t st) {
   const int k = s->k, col = k - 1;
   // after an FP64 anchor, the anchor row of B comes from the exact column W(:,0)
   const double* w0 = (s->mixed && s->anchored) ? s->W : nullptr;
-  DMRG_TRY(ov(s, k, s->W + col * ldv, nullptr, col, st, w0));
+  if (s->f32 && col > 0) DMRG_TRY(ov(s, k, nullptr, s->W32 + col * ldv, nullptr, col, st, w0));
+  else DMRG_TRY(ov(s, k, s->W + col * ldv, nullptr, nullptr, col, st, w0));
   DMRG_TRY(launch_jacobi(s->small, k, st));
-  DMRG_TRY(res(s, k, s->V + (int64_t)k * ldv, 0, st));
+  DMRG_TRY(res(s, k, tcol_of(s, k), 0, st));
   DMRG_CUDA_TRY(cudaMemcpyAsync(s->hsmall, s->small, sizeof(DevSmall), cudaMemcpyDeviceToHost, st));
   return DMRG_OK;
 }
@@ -282,7 +324,7 @@ dmrg_status phase_b(dmrg_davidson_state* s, cudaStream_t st, bool* need_c) {
   const bool anchor = s->cur_anchor;
   const bool fp64 = !s->mixed && (s->plan->opt.prec == DMRG_PREC_FP64 ||
                                    s->plan->opt.prec == DMRG_PREC_FP64_TC);
-  double* tcol = s->V + (int64_t)k * ldv;
+  double* tcol = tcol_of(s, k);
   s->iters++;
   s->sweeps += s->hsmall->jacobi_sweeps;
   s->lambda = s->hsmall->lambda;
@@ -349,7 +391,7 @@ dmrg_status phase_b(dmrg_davidson_state* s, cudaStream_t st, bool* need_c) {
   }
   if (do_anchor) {
     // collapse to the normalised Ritz vector; its projection is redone in FP64
-    DMRG_TRY(launch_ritz(s->V, s->W, ldv, n, k, s->small, s->xbuf, nullptr, st));
+    DMRG_TRY(ritz(s, k, s->xbuf, nullptr, st));
     DMRG_TRY(launch_normalize(s->vw, s->xbuf, s->V, n, s->small, st));
     s->k = 1;
     s->restarts++;
@@ -395,24 +437,36 @@ dmrg_status phase_b(dmrg_davidson_state* s, cudaStream_t st, bool* need_c) {
     for (int j = 0; j < KMAX; ++j) h.y[j] = j == 0 ? 1.0 : 0.0;
     h.qk = 0;  // the next small eigenproblem starts cold
     DMRG_CUDA_TRY(cudaMemcpyAsync(s->small, s->hsmall, sizeof(DevSmall), cudaMemcpyHostToDevice, st));
-    DMRG_TRY(launch_ritz2(s->V, s->W, ldv, n, k, s->small, s->xbuf, s->pbuf, s->wbuf, s->wpbuf, st));
     const size_t bytes = sizeof(double) * n;
-    DMRG_CUDA_TRY(cudaMemcpyAsync(s->V, s->xbuf, bytes, cudaMemcpyDeviceToDevice, st));
-    DMRG_CUDA_TRY(cudaMemcpyAsync(s->V + ldv, s->pbuf, bytes, cudaMemcpyDeviceToDevice, st));
-    DMRG_CUDA_TRY(cudaMemcpyAsync(s->W, s->wbuf, bytes, cudaMemcpyDeviceToDevice, st));
-    DMRG_CUDA_TRY(cudaMemcpyAsync(s->W + ldv, s->wpbuf, bytes, cudaMemcpyDeviceToDevice, st));
-    DMRG_TRY(launch_orth_pair(s->vw, s->V + ldv, s->W + ldv, s->V, s->W, n, s->small, st));
     const double* w0 = (s->mixed && s->anchored) ? s->W : nullptr;
-    DMRG_TRY(ov(s, 2, s->W + ldv, nullptr, 1, st, w0));
+    if (s->f32) {
+      // p orthonormalised against x in FP64 before it is rounded into FP32 column 1
+      DMRG_TRY(launch_ritz2_split(s->vw, s->V, s->W, s->V32, s->W32, ldv, n, k, s->small, s->xbuf,
+                                  s->pbuf, s->wbuf, s->wpbuf, st));
+      DMRG_TRY(launch_orth_pair(s->vw, s->pbuf, s->wpbuf, s->xbuf, s->wbuf, n, s->small, st));
+      DMRG_CUDA_TRY(cudaMemcpyAsync(s->V, s->xbuf, bytes, cudaMemcpyDeviceToDevice, st));
+      DMRG_CUDA_TRY(cudaMemcpyAsync(s->W, s->wbuf, bytes, cudaMemcpyDeviceToDevice, st));
+      DMRG_TRY(launch_convert32(s->vw, s->pbuf, s->V32 + ldv, n, st));
+      DMRG_TRY(launch_convert32(s->vw, s->wpbuf, s->W32 + ldv, n, st));
+      DMRG_TRY(ov(s, 2, nullptr, s->W32 + ldv, nullptr, 1, st, w0));
+    } else {
+      DMRG_TRY(launch_ritz2(s->V, s->W, ldv, n, k, s->small, s->xbuf, s->pbuf, s->wbuf, s->wpbuf, st));
+      DMRG_CUDA_TRY(cudaMemcpyAsync(s->V, s->xbuf, bytes, cudaMemcpyDeviceToDevice, st));
+      DMRG_CUDA_TRY(cudaMemcpyAsync(s->V + ldv, s->pbuf, bytes, cudaMemcpyDeviceToDevice, st));
+      DMRG_CUDA_TRY(cudaMemcpyAsync(s->W, s->wbuf, bytes, cudaMemcpyDeviceToDevice, st));
+      DMRG_CUDA_TRY(cudaMemcpyAsync(s->W + ldv, s->wpbuf, bytes, cudaMemcpyDeviceToDevice, st));
+      DMRG_TRY(launch_orth_pair(s->vw, s->V + ldv, s->W + ldv, s->V, s->W, n, s->small, st));
+      DMRG_TRY(ov(s, 2, s->W + ldv, nullptr, nullptr, 1, st, w0));
+    }
     knew = 2;
     s->restarts++;
     s->plain_restarts++;
     s->baked_err += s->cur_err;
     s->ritz_k = 0;
-    DMRG_TRY(ov(s, knew, tcol, s->small->s[0], -1, st));
+    DMRG_TRY(ov(s, knew, tcol, nullptr, s->small->s[0], -1, st));
   } else if (do_restart) {
     // V = [x], W = [W y], B = [lambda]; the correction t (column k) is kept
-    DMRG_TRY(launch_ritz(s->V, s->W, ldv, n, k, s->small, s->xbuf, s->wbuf, st));
+    DMRG_TRY(ritz(s, k, s->xbuf, s->wbuf, st));
     DMRG_CUDA_TRY(cudaMemcpyAsync(s->V, s->xbuf, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
     DMRG_CUDA_TRY(cudaMemcpyAsync(s->W, s->wbuf, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
     DMRG_TRY(launch_set_B00(s->small, st));
@@ -421,7 +475,7 @@ dmrg_status phase_b(dmrg_davidson_state* s, cudaStream_t st, bool* need_c) {
     s->plain_restarts++;
     s->baked_err += s->cur_err;
     s->ritz_k = 0;
-    DMRG_TRY(ov(s, knew, tcol, s->small->s[0], -1, st));
+    DMRG_TRY(ov(s, knew, tcol, nullptr, s->small->s[0], -1, st));
   }
   s->knew = knew;
   s->did_restart = do_restart;  // (after a restart y = e_1 in the new basis)
@@ -438,7 +492,7 @@ dmrg_status phase_b(dmrg_davidson_state* s, cudaStream_t st, bool* need_c) {
 dmrg_status phase_c(dmrg_davidson_state* s, cudaStream_t st) {
   const int64_t ldv = s->ldv;
   const int k = s->k, knew = s->knew;
-  double* tcol = s->V + (int64_t)k * ldv;
+  double* tcol = tcol_of(s, k);
   if (s->hsmall->flags & 1) {
     // breakdown: fall back to the raw residual r (mode 1 writes t = r); after a restart
     // the basis is [x] with W = [W y], so r = W(:,0) - lambda V(:,0)
@@ -457,7 +511,7 @@ dmrg_status phase_c(dmrg_davidson_state* s, cudaStream_t st) {
       return DMRG_ERR_NUMERIC;
     }
   }
-  if (knew != k) {
+  if (knew != k && !s->f32) {  // (split storage: the normalisation wrote column knew)
     DMRG_CUDA_TRY(cudaMemcpyAsync(s->V + (int64_t)knew * ldv, tcol, sizeof(double) * ldv,
                                   cudaMemcpyDeviceToDevice, st));
   }
@@ -512,6 +566,12 @@ dmrg_status dmrg_state_ritz(dmrg_davidson_state* s, double* x_out, void* stream)
   }
   if (s->ritz_k == 0) {  // the basis was collapsed onto the Ritz vector
     DMRG_CUDA_TRY(cudaMemcpyAsync(x_out, s->V, sizeof(double) * s->n, cudaMemcpyDeviceToDevice,
+                                  (cudaStream_t)stream));
+    return DMRG_OK;
+  }
+  if (s->f32) {  // (padded work buffer first: x_out holds exactly n elements)
+    DMRG_TRY(ritz(s, s->ritz_k, s->xbuf, nullptr, (cudaStream_t)stream));
+    DMRG_CUDA_TRY(cudaMemcpyAsync(x_out, s->xbuf, sizeof(double) * s->n, cudaMemcpyDeviceToDevice,
                                   (cudaStream_t)stream));
     return DMRG_OK;
   }
@@ -668,6 +728,8 @@ dmrg_status dmrg_davidson_solve_batched(dmrg_plan* const* plans, int32_t nb,
   }
   std::vector<const double*> bx(nb, nullptr);
   std::vector<double*> by(nb, nullptr);
+  std::vector<const float*> bx32(nb, nullptr);
+  std::vector<float*> by32(nb, nullptr);
   std::vector<char> lp(nb, 0);
   // lockstep: every phase is enqueued for all active problems before one wait for all
   for (int it = 0; err == DMRG_OK; ++it) {
@@ -685,8 +747,11 @@ dmrg_status dmrg_davidson_solve_batched(dmrg_plan* const* plans, int32_t nb,
       if (batch && is_lp) {
         lp[i] = 1;
         any_lp = true;
-        bx[i] = s->V + (int64_t)(s->k - 1) * s->ldv;
-        by[i] = s->W + (int64_t)(s->k - 1) * s->ldv;
+        const int64_t c = s->k - 1;
+        bx[i] = s->V + c * s->ldv;
+        by[i] = s->W + c * s->ldv;
+        bx32[i] = (s->f32 && c > 0) ? s->V32 + c * s->ldv : nullptr;
+        by32[i] = (s->f32 && c > 0) ? s->W32 + c * s->ldv : nullptr;
         if (cudaEventRecord(ready[i], sts[i]) != cudaSuccess ||
             cudaStreamWaitEvent(bst, ready[i], 0) != cudaSuccess) {
           set_error("dmrg_davidson_solve_batched: event record failed");
@@ -700,7 +765,7 @@ dmrg_status dmrg_davidson_solve_batched(dmrg_plan* const* plans, int32_t nb,
     }
     if (err != DMRG_OK) break;
     if (any_lp) {
-      err = tc_batch_project(batch, bx.data(), by.data(), lp.data(), bst);
+      err = tc_batch_project(batch, bx.data(), by.data(), bx32.data(), by32.data(), lp.data(), bst);
       if (err == DMRG_OK && cudaEventRecord(bdone, bst) != cudaSuccess) {
         set_error("dmrg_davidson_solve_batched: event record failed");
         err = DMRG_ERR_CUDA;

@@ -107,6 +107,8 @@ struct TcPtrs {
   const double* arena;
   const double* x;
   double* y;
+  const float* x32;     // FP32 vector in and out instead of x, y when not NULL
+  float* y32;
   const uint8_t* ops;
   uint8_t* xa;          // A-form and B-form vector images (one buffer)
   uint8_t* inter;
@@ -176,7 +178,20 @@ struct TcPlan {
   std::vector<std::pair<int64_t, int>> h_order[2];  // (cost per tile, job), descending
   std::vector<PackJob> h_xjobs;
   std::vector<PackChunk> h_xchunks;
+  // CUDA graphs of the projection's launch sequence (pack, both GEMM stages, the split-K
+  // reduction), one per (x, y, x32, y32) vector pair under the current tile schedules,
+  // captured on a plan-owned stream and replayed on the caller's stream; dropped when the
+  // schedules change
+  using GraphKey = std::tuple<const void*, const void*, const void*, const void*>;
+  std::map<GraphKey, std::pair<cudaGraphExec_t, int>> graphs;  // -> (exec, kernel launches)
+  cudaStream_t cap_st = nullptr;
 };
+
+// drops every captured projection graph of a tensor-core plan
+void drop_graphs(TcPlan* t) {
+  for (auto& g : t->graphs) cudaGraphExecDestroy(g.second.first);
+  t->graphs.clear();
+}
 
 namespace tc {
 
@@ -193,7 +208,8 @@ template <int PLANES, bool TF32>
 __global__ void __launch_bounds__(256)
 pack_kernel(const PackChunk* __restrict__ chunks, const PackJob* __restrict__ jobs,
             const double* __restrict__ arena, const double* __restrict__ x,
-            uint8_t* __restrict__ dst, const TcPtrs* __restrict__ ptrs) {
+            uint8_t* __restrict__ dst, const TcPtrs* __restrict__ ptrs,
+            const float* __restrict__ x32) {
   using L = Layout<TF32>;
   constexpr int EPG = TF32 ? 4 : 8;  // elements per 16-byte group
   constexpr int KT = L::KT;
@@ -204,10 +220,13 @@ pack_kernel(const PackChunk* __restrict__ chunks, const PackJob* __restrict__ jo
     if (!pt.active) return;
     arena = pt.arena;
     x = pt.x;
+    x32 = pt.x32;
     dst = pt.xa;
   }
   const PackJob jb = jobs[ch.job];
   const double* src = (jb.src_space ? x : arena) + jb.src_off;
+  // an FP32 vector (the low-precision basis columns of a mixed solve) is read as it is
+  const float* src32 = (jb.src_space && x32) ? x32 + jb.src_off : nullptr;
   uint8_t* base = dst + jb.dst_off + ((int64_t)ch.rt * jb.nkt + ch.kt) * PLANES * L::CHUNK;
   const bool kfast = jb.cs == 1;
   for (int idx = threadIdx.x; idx < kRows * L::GROUPS; idx += blockDim.x) {
@@ -225,9 +244,14 @@ pack_kernel(const PackChunk* __restrict__ chunks, const PackJob* __restrict__ jo
 #pragma unroll
     for (int e = 0; e < EPG; ++e) {
       const int k = k0 + e;
-      double a = 0.0;
-      if (grow < jb.R && k < jb.K) a = src[grow * jb.rs + (int64_t)k * jb.cs];
-      v[e] = scaled ? (float)(jb.scale * a) : f64_to_f32_rn(a);
+      const bool in = grow < jb.R && k < jb.K;
+      const int64_t at = grow * jb.rs + (int64_t)k * jb.cs;
+      if (src32) {
+        v[e] = in ? src32[at] : 0.0f;
+      } else {
+        const double a = in ? src[at] : 0.0;
+        v[e] = scaled ? (float)(jb.scale * a) : f64_to_f32_rn(a);
+      }
     }
     const uint32_t off = L::off(r, g);
     if constexpr (TF32) {
@@ -282,7 +306,8 @@ tc_gemm_kernel(const TcTile* __restrict__ tiles, int ntiles, const TcJob* __rest
                const uint8_t* __restrict__ b3, uint8_t* __restrict__ out_img,
                double* __restrict__ y, const double* __restrict__ x, int* __restrict__ gerr,
                const TcPtrs* __restrict__ ptrs, int gemm_stage, int* __restrict__ tile_ctr,
-               float* __restrict__ partial) {
+               float* __restrict__ partial, float* __restrict__ y32,
+               const float* __restrict__ x32) {
   using L = Layout<TF32>;
   constexpr uint32_t kStageA = PLANES * L::CHUNK;             // A operand of one stage
   constexpr uint32_t kSlotB = (WIDE ? 2 : 1) * L::CHUNK;      // one plane of B
@@ -497,11 +522,15 @@ tc_gemm_kernel(const TcTile* __restrict__ tiles, int ntiles, const TcJob* __rest
       uint8_t* o_img = out_img;
       double* o_y = y;
       const double* i_x = x;
+      float* o_y32 = y32;
+      const float* i_x32 = x32;
       if (ptrs) {
         const TcPtrs& pt = ptrs[tile.pad_];
         o_img = gemm_stage == 1 ? pt.inter : nullptr;
         o_y = pt.y;
         i_x = pt.x;
+        o_y32 = pt.y32;
+        i_x32 = pt.x32;
       }
       const TcJob job = jobs[tile.job];
       const bool has = tile.kb < tile.ke;
@@ -539,6 +568,23 @@ tc_gemm_kernel(const TcTile* __restrict__ tiles, int ntiles, const TcJob* __rest
                   // partial sums of this part: slot red + part, row-major 128 x 256
                   *reinterpret_cast<float2*>(partial + (int64_t)(tile.red + tile.part) * kSlotFloats +
                                              r * 256 + cc) = make_float2(f0, f1);
+                } else if (mr < job.M && o_y32) {
+                  // FP32 output (a low-precision basis column of a mixed solve)
+                  const int n = tile.nt * kRows + cc;
+                  float* yp = o_y32 + job.out_off + mr * job.N + n;
+                  float e0 = f0, e1 = f1;
+                  if (job.axpy != 0.0) {
+                    const float* xp = i_x32 + job.x_off + mr * job.N + n;
+                    const float a = (float)job.axpy;
+                    if (n < job.N) e0 = fmaf(a, xp[0], e0);
+                    if (n + 1 < job.N) e1 = fmaf(a, xp[1], e1);
+                  }
+                  if (n + 1 < job.N && (reinterpret_cast<uintptr_t>(yp) & 7) == 0) {
+                    *reinterpret_cast<float2*>(yp) = make_float2(e0, e1);
+                  } else {
+                    if (n < job.N) yp[0] = e0;
+                    if (n + 1 < job.N) yp[1] = e1;
+                  }
                 } else if (mr < job.M) {
                   const int n = tile.nt * kRows + cc;
                   double* yp = o_y + job.out_off + mr * job.N + n;
@@ -649,7 +695,8 @@ tc_gemm_kernel(const TcTile* __restrict__ tiles, int ntiles, const TcJob* __rest
 __global__ void __launch_bounds__(256)
 split_reduce_kernel(const TcTile* __restrict__ groups, const TcJob* __restrict__ jobs,
                     const float* __restrict__ partial, double* __restrict__ y,
-                    const double* __restrict__ x) {
+                    const double* __restrict__ x, float* __restrict__ y32,
+                    const float* __restrict__ x32) {
   grid_dep_wait();
   const TcTile g = groups[blockIdx.x >> 5];
   const TcJob job = jobs[g.job];
@@ -668,15 +715,26 @@ split_reduce_kernel(const TcTile* __restrict__ groups, const TcJob* __restrict__
     }
     const float v[4] = {s.x, s.y, s.z, s.w};
     const int n0 = g.nt * kRows + col;
-    double* yr = y + job.out_off + m * job.N;
-    const double* xr = x + job.x_off + m * job.N;
+    if (y32) {
+      float* yr = y32 + job.out_off + m * job.N;
+      const float* xr = x32 + job.x_off + m * job.N;
+      const float a = (float)job.axpy;
 #pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      const int n = n0 + e;
-      if (n < job.N) {
-        double val = f32_to_f64(v[e]);  // exact, integer ops
-        if (job.axpy != 0.0) val = fma(job.axpy, xr[n], val);
-        yr[n] = val;
+      for (int e = 0; e < 4; ++e) {
+        const int n = n0 + e;
+        if (n < job.N) yr[n] = job.axpy != 0.0 ? fmaf(a, xr[n], v[e]) : v[e];
+      }
+    } else {
+      double* yr = y + job.out_off + m * job.N;
+      const double* xr = x + job.x_off + m * job.N;
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int n = n0 + e;
+        if (n < job.N) {
+          double val = f32_to_f64(v[e]);  // exact, integer ops
+          if (job.axpy != 0.0) val = fma(job.axpy, xr[n], val);
+          yr[n] = val;
+        }
       }
     }
   }
@@ -720,6 +778,8 @@ dmrg_status upload_vec(T** dst, const std::vector<T>& v, cudaStream_t st) {
 
 void free_tc(TcPlan* t) {
   if (!t) return;
+  drop_graphs(t);
+  if (t->cap_st) cudaStreamDestroy(t->cap_st);
   for (int b = 0; b < 4; ++b)
     if (b != TB_XB) cudaFree(t->buf[b]);
   if (t->h_err) cudaFreeHost(t->h_err);
@@ -741,7 +801,7 @@ dmrg_status launch_pack(const std::vector<PackChunk>& chunks, const PackChunk* d
                         uint8_t* dst, cudaStream_t st) {
   if (chunks.empty()) return DMRG_OK;
   tc::pack_kernel<PLANES, TF32><<<(unsigned)chunks.size(), 256, 0, st>>>(d_chunks, d_jobs, arena, x, dst,
-                                                                          nullptr);
+                                                                          nullptr, nullptr);
   DMRG_LAUNCH_CHECK();
   return DMRG_OK;
 }
@@ -1196,17 +1256,27 @@ dmrg_status configure_tc() {
   return DMRG_OK;
 }
 
+// The vector of a projection: FP64 x, y, or (x32, y32 set) an FP32 one.
+struct VecIO {
+  const double* x;
+  double* y;
+  const float* x32;
+  float* y32;
+};
+
 // part 0: pack X into its operand images; part 1, 2: the GEMM stages with schedule c
 template <int PLANES, int STAGES, bool TF32>
-dmrg_status run_tc_part(dmrg_plan* p, TcPlan* t, const double* x, double* y, int part, int c,
+dmrg_status run_tc_part(dmrg_plan* p, TcPlan* t, const VecIO& io, int part, int c,
                         cudaStream_t st) {
+  const double* x = io.x;
+  double* y = io.y;
   constexpr bool WIDE = !TF32;
   constexpr size_t smem = tc::smem_bytes<PLANES, STAGES, TF32, WIDE>();
   if (part == 0) {
     if (t->n_xpack_chunks > 0) {  // X -> A-form and B-form images
       DMRG_CUDA_TRY(launch_pdl(tc::pack_kernel<PLANES, TF32>, dim3((unsigned)t->n_xpack_chunks), dim3(256),
                                0, st, (const PackChunk*)t->d_xpack_chunks, (const PackJob*)t->d_xpack_jobs,
-                               (const double*)p->arena, x, t->buf[TB_XA], (const TcPtrs*)nullptr));
+                               (const double*)p->arena, x, t->buf[TB_XA], (const TcPtrs*)nullptr, io.x32));
       DMRG_LAUNCH_CHECK();
     }
     return DMRG_OK;
@@ -1219,28 +1289,69 @@ dmrg_status run_tc_part(dmrg_plan* p, TcPlan* t, const double* x, double* y, int
       (const TcTile*)t->d_tiles[part - 1][c], (int)nt, (const TcJob*)t->d_jobs, (const TcSeg*)t->d_segs,
       (const uint8_t*)t->buf[TB_OPS], (const uint8_t*)t->buf[TB_XA], (const uint8_t*)t->buf[TB_XB],
       (const uint8_t*)(part == 1 ? nullptr : t->buf[TB_INTER]), part == 1 ? t->buf[TB_INTER] : nullptr, y, x,
-      t->d_err, (const TcPtrs*)nullptr, part, t->d_ctr + 2 * (part - 1), t->d_partial));
+      t->d_err, (const TcPtrs*)nullptr, part, t->d_ctr + 2 * (part - 1), t->d_partial, io.y32, io.x32));
   DMRG_LAUNCH_CHECK();
   if (part == 2 && t->ngroups[c] > 0) {
     DMRG_CUDA_TRY(launch_pdl(tc::split_reduce_kernel, dim3((unsigned)(t->ngroups[c] * 32)), dim3(256), 0, st,
                              (const TcTile*)t->d_groups[c], (const TcJob*)t->d_jobs,
-                             (const float*)t->d_partial, y, x));
+                             (const float*)t->d_partial, y, x, io.y32, io.x32));
     DMRG_LAUNCH_CHECK();
   }
   return DMRG_OK;
 }
 
 template <int PLANES, int STAGES, bool TF32>
-dmrg_status run_tc(dmrg_plan* p, TcPlan* t, const double* x, double* y, cudaStream_t st) {
+dmrg_status run_tc_direct(dmrg_plan* p, TcPlan* t, const VecIO& io, cudaStream_t st) {
+  DMRG_TRY((run_tc_part<PLANES, STAGES, TF32>(p, t, io, 0, 0, st)));
+  DMRG_TRY((run_tc_part<PLANES, STAGES, TF32>(p, t, io, 1, t->sched[0], st)));
+  DMRG_TRY((run_tc_part<PLANES, STAGES, TF32>(p, t, io, 2, t->sched[1], st)));
+  return DMRG_OK;
+}
+
+template <int PLANES, int STAGES, bool TF32>
+dmrg_status run_tc(dmrg_plan* p, TcPlan* t, const VecIO& io, cudaStream_t st) {
   DMRG_TRY((configure_tc<PLANES, STAGES, TF32>()));
   if (*t->h_err != 0) {
     set_error("tensor-core projection kernel reported error %d (a bounded wait timed out)",
               *t->h_err);
     return DMRG_ERR_CUDA;
   }
-  DMRG_TRY((run_tc_part<PLANES, STAGES, TF32>(p, t, x, y, 0, 0, st)));
-  DMRG_TRY((run_tc_part<PLANES, STAGES, TF32>(p, t, x, y, 1, t->sched[0], st)));
-  DMRG_TRY((run_tc_part<PLANES, STAGES, TF32>(p, t, x, y, 2, t->sched[1], st)));
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  DMRG_CUDA_TRY(cudaStreamIsCapturing(st, &cs));
+  // launched directly when graphs are off, or inside the caller's own stream capture
+  if (!p->opt.graphs || cs != cudaStreamCaptureStatusNone)
+    return run_tc_direct<PLANES, STAGES, TF32>(p, t, io, st);
+  const TcPlan::GraphKey key{io.x, io.y, io.x32, io.y32};
+  auto it = t->graphs.find(key);
+  if (it == t->graphs.end()) {
+    if (!t->cap_st) DMRG_CUDA_TRY(cudaStreamCreateWithFlags(&t->cap_st, cudaStreamNonBlocking));
+    const int64_t l0 = dmrg_kernel_launches();
+    DMRG_CUDA_TRY(cudaStreamBeginCapture(t->cap_st, cudaStreamCaptureModeThreadLocal));
+    dmrg_status s = run_tc_direct<PLANES, STAGES, TF32>(p, t, io, t->cap_st);
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(t->cap_st, &g);
+    const int nk = (int)(dmrg_kernel_launches() - l0);
+    note_launches(-nk);  // captured, not launched: replays count them
+    if (s != DMRG_OK) {
+      if (g) cudaGraphDestroy(g);
+      return s;
+    }
+    if (e != cudaSuccess) {
+      set_error("capture of the projection graph: %s", cudaGetErrorString(e));
+      return DMRG_ERR_CUDA;
+    }
+    cudaGraphExec_t ex = nullptr;
+    const cudaError_t ei = cudaGraphInstantiate(&ex, g, 0);
+    cudaGraphDestroy(g);
+    if (ei != cudaSuccess) {
+      set_error("instantiation of the projection graph: %s", cudaGetErrorString(ei));
+      return DMRG_ERR_CUDA;
+    }
+    if (t->graphs.size() >= 96) drop_graphs(t);  // bounded: a solve uses about 25 vector pairs
+    it = t->graphs.emplace(key, std::make_pair(ex, nk)).first;
+  }
+  DMRG_CUDA_TRY(cudaGraphLaunch(it->second.first, st));
+  note_launches(it->second.second);
   return DMRG_OK;
 }
 
@@ -1266,7 +1377,8 @@ dmrg_status tune_tc(dmrg_plan* p, TcPlan* t, const double* x, double* y, cudaStr
     set_error("autotune: allocation of the L2 flush buffer or events failed");
     return DMRG_ERR_OOM;
   }
-  dmrg_status s = run_tc_part<PLANES, STAGES, TF32>(p, t, x, y, 0, 0, st);
+  const VecIO io{x, y, nullptr, nullptr};
+  dmrg_status s = run_tc_part<PLANES, STAGES, TF32>(p, t, io, 0, 0, st);
   for (int part = 1; part <= 2 && s == DMRG_OK; ++part) {
     float best = 0.0f;
     int arg = 0;
@@ -1274,7 +1386,7 @@ dmrg_status tune_tc(dmrg_plan* p, TcPlan* t, const double* x, double* y, cudaStr
     for (int c = 0; c < kSchedules && s == DMRG_OK; ++c) {
       if (!t->valid[part - 1][c]) continue;
       float ms[3] = {0.0f, 0.0f, 0.0f};
-      s = run_tc_part<PLANES, STAGES, TF32>(p, t, x, y, part, c, st);
+      s = run_tc_part<PLANES, STAGES, TF32>(p, t, io, part, c, st);
       for (int r = 0; r < 3 && s == DMRG_OK; ++r) {
         if (cudaMemsetAsync(flush, r + 1, kFlush, st) != cudaSuccess ||
             cudaEventRecord(e0, st) != cudaSuccess) {
@@ -1282,7 +1394,7 @@ dmrg_status tune_tc(dmrg_plan* p, TcPlan* t, const double* x, double* y, cudaStr
           s = DMRG_ERR_CUDA;
           break;
         }
-        s = run_tc_part<PLANES, STAGES, TF32>(p, t, x, y, part, c, st);
+        s = run_tc_part<PLANES, STAGES, TF32>(p, t, io, part, c, st);
         if (s != DMRG_OK) break;
         if (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
             cudaEventElapsedTime(&ms[r], e0, e1) != cudaSuccess) {
@@ -1300,6 +1412,7 @@ dmrg_status tune_tc(dmrg_plan* p, TcPlan* t, const double* x, double* y, cudaStr
       }
     }
     t->sched[part - 1] = arg;
+    drop_graphs(t);
   }
   cleanup();
   if (s == DMRG_OK && *t->h_err != 0) {
@@ -1511,7 +1624,7 @@ dmrg_status run_batch(TcBatch* b, cudaStream_t st) {
   DMRG_TRY((configure_tc<PLANES, STAGES, TF32>()));
   if (b->nchunks > 0) {
     tc::pack_kernel<PLANES, TF32><<<(unsigned)b->nchunks, 256, 0, st>>>(
-        b->d_pchunks, b->d_pjobs, nullptr, nullptr, nullptr, b->d_ptrs);
+        b->d_pchunks, b->d_pjobs, nullptr, nullptr, nullptr, b->d_ptrs, nullptr);
     DMRG_LAUNCH_CHECK();
   }
   for (int part = 1; part <= 2; ++part) {
@@ -1520,7 +1633,8 @@ dmrg_status run_batch(TcBatch* b, cudaStream_t st) {
     const int grid = (int)std::min<int64_t>(nt, b->sms);
     tc::tc_gemm_kernel<PLANES, STAGES, TF32, WIDE><<<grid, tc::kThreads, smem, st>>>(
         b->d_tiles[part - 1], (int)nt, b->d_jobs, b->d_segs, nullptr, nullptr, nullptr, nullptr,
-        nullptr, nullptr, nullptr, b->d_err, b->d_ptrs, part, b->d_ctr + 2 * (part - 1), nullptr);
+        nullptr, nullptr, nullptr, b->d_err, b->d_ptrs, part, b->d_ctr + 2 * (part - 1), nullptr,
+        nullptr, nullptr);
     DMRG_LAUNCH_CHECK();
   }
   return DMRG_OK;
@@ -1528,7 +1642,8 @@ dmrg_status run_batch(TcBatch* b, cudaStream_t st) {
 }  // namespace
 
 dmrg_status tc_batch_project(TcBatch* b, const double* const* x, double* const* y,
-                             const char* active, cudaStream_t st) {
+                             const float* const* x32, float* const* y32, const char* active,
+                             cudaStream_t st) {
   DMRG_TRY(tc_batch_error(b));
   const int slot = tc_slot(b->prec);
   const int r = b->slot;
@@ -1540,9 +1655,12 @@ dmrg_status tc_batch_project(TcBatch* b, const double* const* x, double* const* 
   for (size_t i = 0; i < b->plans.size(); ++i) {
     const dmrg_plan* p = b->plans[i];
     const TcPlan* t = p->tc[slot];
-    h[i] = TcPtrs{p->arena, x[i], y[i], t->buf[TB_OPS], t->buf[TB_XA], t->buf[TB_INTER],
+    const bool f32 = x32 && x32[i];
+    h[i] = TcPtrs{p->arena, f32 ? nullptr : x[i], f32 ? nullptr : y[i], f32 ? x32[i] : nullptr,
+                  f32 ? y32[i] : nullptr, t->buf[TB_OPS], t->buf[TB_XA], t->buf[TB_INTER],
                   active[i] ? 1 : 0, 0};
-    if (active[i] && (!x[i] || !y[i] || !t->buf[TB_OPS] || !t->buf[TB_XA] ||
+    if (active[i] && (!(f32 ? (const void*)x32[i] : (const void*)x[i]) ||
+                      !(f32 ? (void*)y32[i] : (void*)y[i]) || !t->buf[TB_OPS] || !t->buf[TB_XA] ||
                       (t->ntiles1 > 0 && !t->buf[TB_INTER]))) {
       set_error("internal: grouped projection of problem %zu without its buffers", i);
       return DMRG_ERR_INVALID_ARG;
@@ -1580,8 +1698,8 @@ dmrg_status tc_error_status(dmrg_plan* p) {
   return DMRG_OK;
 }
 
-dmrg_status launch_project_tc(dmrg_plan* p, dmrg_precision prec, const double* x, double* y,
-                              cudaStream_t st) {
+namespace {
+dmrg_status project_tc_io(dmrg_plan* p, dmrg_precision prec, const VecIO& io, cudaStream_t st) {
   const int slot = tc_slot(prec);
   if (!p->tc[slot]) {
     TcPlan* t = nullptr;
@@ -1589,14 +1707,21 @@ dmrg_status launch_project_tc(dmrg_plan* p, dmrg_precision prec, const double* x
     p->tc[slot] = t;
   }
   TcPlan* t = p->tc[slot];
-  if (p->opt.autotune && !t->tuned) {
-    if (prec == DMRG_PREC_TF32) DMRG_TRY((tune_tc<1, 6, true>(p, t, x, y, st)));
-    else if (prec == DMRG_PREC_BF16X2) DMRG_TRY((tune_tc<2, 4, false>(p, t, x, y, st)));
-    else DMRG_TRY((tune_tc<3, 3, false>(p, t, x, y, st)));
-  }
-  if (prec == DMRG_PREC_TF32) return run_tc<1, 6, true>(p, t, x, y, st);
-  if (prec == DMRG_PREC_BF16X2) return run_tc<2, 4, false>(p, t, x, y, st);
-  return run_tc<3, 3, false>(p, t, x, y, st);
+  if (p->opt.autotune && !t->tuned) DMRG_TRY(tune_project_tc(p, prec, st));
+  if (prec == DMRG_PREC_TF32) return run_tc<1, 6, true>(p, t, io, st);
+  if (prec == DMRG_PREC_BF16X2) return run_tc<2, 4, false>(p, t, io, st);
+  return run_tc<3, 3, false>(p, t, io, st);
+}
+}  // namespace
+
+dmrg_status launch_project_tc(dmrg_plan* p, dmrg_precision prec, const double* x, double* y,
+                              cudaStream_t st) {
+  return project_tc_io(p, prec, VecIO{x, y, nullptr, nullptr}, st);
+}
+
+dmrg_status launch_project_tc32(dmrg_plan* p, dmrg_precision prec, const float* x, float* y,
+                                cudaStream_t st) {
+  return project_tc_io(p, prec, VecIO{nullptr, nullptr, x, y}, st);
 }
 
 dmrg_status tune_project_tc(dmrg_plan* p, dmrg_precision prec, cudaStream_t st) {
@@ -1638,6 +1763,7 @@ dmrg_status set_schedule_tc(dmrg_plan* p, dmrg_precision prec, int stage1, int s
       return DMRG_ERR_INVALID_ARG;
     }
   }
+  drop_graphs(t);
   t->sched[0] = stage1;
   t->sched[1] = stage2;
   t->tuned = true;  // fixed: the first projection does not autotune

@@ -33,6 +33,9 @@ void set_error(const char* fmt, ...);
 
 // Kernel launches are counted and checked with cudaGetLastError right after the launch.
 void note_launch();
+// adds n (may be negative) to the launch count: the kernels of a replayed CUDA graph count
+// as launches, the captured ones do not
+void note_launches(int64_t n);
 #define DMRG_LAUNCH_CHECK()                  \
   do {                                       \
     ::dmrg::note_launch();                   \
@@ -175,6 +178,10 @@ dmrg_status launch_project_fp64(dmrg_plan* plan, const double* x, double* y,
 // gemm_tc.cu
 dmrg_status launch_project_tc(dmrg_plan* plan, dmrg_precision prec, const double* x,
                               double* y, cudaStream_t stream);
+// the same with an FP32 vector in and out (the low-precision basis columns of a mixed
+// solve with split vector arithmetic)
+dmrg_status launch_project_tc32(dmrg_plan* plan, dmrg_precision prec, const float* x, float* y,
+                                cudaStream_t stream);
 // builds the tensor-core plan of prec if needed and times its tile schedules
 dmrg_status tune_project_tc(dmrg_plan* plan, dmrg_precision prec, cudaStream_t stream);
 dmrg_status set_schedule_tc(dmrg_plan* plan, dmrg_precision prec, int stage1, int stage2,
@@ -185,9 +192,11 @@ void tc_schedule_stats(const dmrg_plan* plan, int32_t sched[2], float us[2][DMRG
 struct TcBatch;
 dmrg_status tc_batch_create(dmrg_plan* const* plans, int nb, dmrg_precision prec,
                             cudaStream_t stream, TcBatch** out);
-// y[i] = H_i x[i] for every i with active[i]; x[i], y[i] are device vectors of plan i
+// y[i] = H_i x[i] for every i with active[i]; x[i], y[i] are device vectors of plan i, or,
+// where x32 (and y32) are given and x32[i] is not NULL, FP32 vectors x32[i], y32[i]
 dmrg_status tc_batch_project(TcBatch* b, const double* const* x, double* const* y,
-                             const char* active, cudaStream_t stream);
+                             const float* const* x32, float* const* y32, const char* active,
+                             cudaStream_t stream);
 dmrg_status tc_batch_error(const TcBatch* b);
 void tc_batch_destroy(TcBatch* b);
 void destroy_tc(dmrg_plan* plan);
@@ -284,19 +293,37 @@ dmrg_status launch_residual_df(const VecWork& w, const double* V, const double* 
 dmrg_status launch_cgs_df(const VecWork& w, const double* V, int64_t ldv, int64_t n, int k,
                           double* tcol, DevSmall* small, int sin, int sout, cudaStream_t st,
                           int second = 0);
-// vec_split.cu -- mixed modes: column 0 in FP64, low-precision columns in FP32
-dmrg_status launch_overlap_split(const VecWork& w, const double* V, int64_t ldv, int64_t n,
-                                 int k, const double* vec, double* s_out, DevSmall* small,
-                                 int Bcol, cudaStream_t st, const double* w0 = nullptr);
-dmrg_status launch_residual_split(const VecWork& w, const double* V, const double* W,
-                                  const double* D, int64_t ldv, int64_t n, int k, double* tcol,
-                                  DevSmall* small, int mode, cudaStream_t st);
-dmrg_status launch_cgs_split(const VecWork& w, const double* V, int64_t ldv, int64_t n, int k,
-                             double* tcol, DevSmall* small, int sin, int sout, cudaStream_t st,
-                             int second = 0);
-// flags breakdown, else t = (t - s[1][0] v_0) / norm unless the second pass ran (k >= 2)
-dmrg_status launch_finish_split(const VecWork& w, const double* V, double* tcol, int64_t n,
-                                int k, DevSmall* small, cudaStream_t st);
+// vec_split.cu -- mixed modes with split arithmetic: column 0 of the basis in FP64 (V0, W0),
+// the low-precision columns j >= 1 stored in FP32 (V32 + j * ldv, W32 + j * ldv); the new
+// direction t is an FP64 work vector (tcol) until it is appended
+dmrg_status launch_overlap_split(const VecWork& w, const double* V0, const float* V32, int64_t ldv,
+                                 int64_t n, int k, const double* vec64, const float* vec32,
+                                 double* s_out, DevSmall* small, int Bcol, cudaStream_t st,
+                                 const double* w0 = nullptr);
+dmrg_status launch_residual_split(const VecWork& w, const double* V0, const double* W0,
+                                  const float* V32, const float* W32, const double* D,
+                                  int64_t ldv, int64_t n, int k, double* tcol, DevSmall* small,
+                                  int mode, cudaStream_t st);
+dmrg_status launch_cgs_split(const VecWork& w, const double* V0, const float* V32, int64_t ldv,
+                             int64_t n, int k, double* tcol, DevSmall* small, int sin, int sout,
+                             cudaStream_t st, int second = 0);
+// flags breakdown, else t = (t - s[1][0] v_0) / norm unless the second pass ran (k >= 2),
+// and out32 = t rounded to FP32
+dmrg_status launch_finish_split(const VecWork& w, const double* V0, double* tcol, int64_t n,
+                                int k, DevSmall* small, float* out32, cudaStream_t st);
+// dst = src rounded to nearest FP32 (n elements rounded up to even; padded buffers)
+dmrg_status launch_convert32(const VecWork& w, const double* src, float* dst, int64_t n,
+                             cudaStream_t st);
+// x = V y (and wx = W y if wx): column 0 in FP64, the FP32 tail summed in FP32 (padded
+// outputs: n rounded up to even elements are written)
+dmrg_status launch_ritz_split(const VecWork& w, const double* V0, const double* W0,
+                              const float* V32, const float* W32, int64_t ldv, int64_t n, int k,
+                              const DevSmall* small, double* x, double* wx, cudaStream_t st);
+// two-vector restart: x = V C0, p = V C1, wx = W C0, wp = W C1 (padded outputs)
+dmrg_status launch_ritz2_split(const VecWork& w, const double* V0, const double* W0,
+                               const float* V32, const float* W32, int64_t ldv, int64_t n, int k,
+                               const DevSmall* small, double* x, double* p, double* wx,
+                               double* wp, cudaStream_t st);
 dmrg_status launch_gemv_trans_public(const double* V, int64_t ldv, int64_t n, int k,
                                      const double* w, double* s, cudaStream_t st);
 

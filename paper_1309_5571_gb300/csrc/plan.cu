@@ -429,6 +429,7 @@ dmrg_status dmrg_plan_create(const dmrg_superblock_desc* desc, const dmrg_option
       (p->opt.anchor_prec != DMRG_PREC_FP64 && p->opt.anchor_prec != DMRG_PREC_FP64_TC) ||
       p->opt.vector_arith < DMRG_VEC_FP64 || p->opt.vector_arith > DMRG_VEC_SPLIT ||
       (p->opt.autotune != 0 && p->opt.autotune != 1) ||
+      (p->opt.graphs != 0 && p->opt.graphs != 1) ||
       (p->opt.restart_keep != 1 && p->opt.restart_keep != 2)) {
     set_error("options out of range (max_subspace must be in [2, %d])", DMRG_MAX_SUBSPACE);
     delete p;

@@ -263,3 +263,59 @@ def test_full_size_projection_hubbard_m2048_fp64tc(hub_L64_m2048):
     x = warmup.start_vector(sb.n, seed=5)
     y = plan.project(cuda(x)).cpu().numpy()
     assert rel_err(y, oproj.project_blocks(sb, x)) <= 1e-12
+
+
+# ---------------------------------------------------------------- CUDA-graph replay
+@pytest.mark.parametrize("prec", LOWPREC)
+def test_graph_replay_is_bit_identical(prec):
+    # a projection replayed from its captured graph equals the direct launches bit for bit,
+    # for several vector pairs (one graph each) and after a schedule change (graphs dropped)
+    sb = problem("hub_L8_m40")
+    direct = Plan(sb, prec=prec, graphs=False)
+    graphed = Plan(sb, prec=prec, graphs=True)
+    for pl in (direct, graphed):
+        pl.set_tile_schedule(3, 12, prec=prec) if prec != "tf32" else pl.set_tile_schedule(1, 10, prec=prec)
+    xs = [cuda(np.random.default_rng(s).standard_normal(sb.n)) for s in range(3)]
+    ys = [torch.empty_like(x) for x in xs]
+    for rep in range(2):
+        for x, y in zip(xs, ys):
+            ref = direct.project(x, prec=prec).cpu().numpy()
+            out = graphed.project(x, y, prec=prec).cpu().numpy()
+            np.testing.assert_array_equal(out, ref)
+    for pl in (direct, graphed):
+        pl.set_tile_schedule(0, 9, prec=prec)
+    np.testing.assert_array_equal(graphed.project(xs[0], ys[0], prec=prec).cpu().numpy(),
+                                  direct.project(xs[0], prec=prec).cpu().numpy())
+
+
+def test_graph_projection_inside_a_caller_capture():
+    # while the caller's stream is being captured the projection launches its kernels into
+    # that capture (no nested capture); replaying the caller's graph gives the same bits
+    sb = problem("ragged")
+    plan = Plan(sb, prec="bf16x2")
+    x = cuda(np.random.default_rng(4).standard_normal(sb.n))
+    ref = plan.project(x).cpu().numpy()      # builds and tunes the plan outside the capture
+    y = torch.zeros_like(x)
+    g = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s):
+            plan.project(x, y, stream=s)
+    torch.cuda.synchronize()
+    g.replay()
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(y.cpu().numpy(), ref)
+
+
+def test_graph_solve_equals_direct_solve():
+    sb = problem("heis_L16_m64")
+    x0 = cuda(warmup.start_vector(sb.n, seed=0))
+    res = {}
+    for gflag in (False, True):
+        plan = Plan(sb, prec="bf16x2", anchor_prec="fp64tc", graphs=gflag)
+        plan.set_tile_schedule(0, 0, prec="bf16x2")
+        x, info = plan.solve(x0)
+        res[gflag] = (x.cpu().numpy(), info)
+    np.testing.assert_array_equal(res[False][0], res[True][0])
+    assert res[False][1]["energy"] == res[True][1]["energy"]
+    assert res[False][1]["iters"] == res[True][1]["iters"]
