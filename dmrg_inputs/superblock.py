@@ -148,3 +148,65 @@ def load_npz(path: str) -> Superblock:
         opsL=ops["L"], opsR=ops["R"],
         terms=[(float(c), int(a), int(b)) for c, (a, b) in zip(z["terms_coef"], z["terms_ab"])],
     )
+
+
+@dataclass
+class SuperblockL11r:
+    """One superblock problem in the l-1-1-r form of Sec. 4.2: H_SB = sum_a c_a A_a (x)
+    a_a (x) b_a (x) B_a (Eq. 12), with A_a on the block l, a_a and b_a on the two middle
+    sites and B_a on the block r.
+
+    Layout conventions:
+
+    * the site states are their own sectors (each has one quantum number ``qs[s]``), so
+      a site operator is a dense q x q matrix ``sops[o]`` with element [s_out, s_in];
+    * a segment (i, s1, s2, k) -- block-l sector i, site states s1 and s2, block-r
+      sector k -- is a row-major [dl[i], dr[k]] matrix; segments follow ``segs`` and
+      hold every combination whose quantum numbers add up to Q;
+    * a term (coef, a, s1, s2, b) contributes coef * (A_a (x) sops[s1] (x) sops[s2] (x)
+      B_b); an index of -1 names the identity of that subsystem.
+
+    The container only records the problem; nothing here applies an operator."""
+
+    ql: List[Tuple[int, ...]]
+    dl: np.ndarray
+    qs: List[Tuple[int, ...]]
+    qr: List[Tuple[int, ...]]
+    dr: np.ndarray
+    Q: Tuple[int, ...]
+    segs: List[Tuple[int, int, int, int]]
+    opsl: List[BlockOp]
+    sops: List[np.ndarray]
+    opsr: List[BlockOp]
+    terms: List[Tuple[float, int, int, int, int]]
+    meta: dict = field(default_factory=dict)
+
+    def offsets(self) -> np.ndarray:
+        sizes = np.array([int(self.dl[i]) * int(self.dr[k]) for i, _, _, k in self.segs],
+                         dtype=np.int64)
+        off = np.zeros(len(sizes) + 1, dtype=np.int64)
+        np.cumsum(sizes, out=off[1:])
+        return off
+
+    @property
+    def n(self) -> int:
+        return int(self.offsets()[-1])
+
+    @property
+    def q(self) -> int:
+        return len(self.qs)
+
+    def seg_index(self) -> Dict[Tuple[int, int, int, int], int]:
+        return {s: idx for idx, s in enumerate(self.segs)}
+
+
+def segs_for_target(ql, qs, qr, Q) -> List[Tuple[int, int, int, int]]:
+    """All (i, s1, s2, k) whose quantum numbers add up to Q, ordered by i, s1, s2, k."""
+    out = []
+    for i, a in enumerate(ql):
+        for s1, b in enumerate(qs):
+            for s2, c in enumerate(qs):
+                for k, d in enumerate(qr):
+                    if tuple(w + x + y + z for w, x, y, z in zip(a, b, c, d)) == tuple(Q):
+                        out.append((i, s1, s2, k))
+    return out

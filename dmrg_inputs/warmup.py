@@ -35,7 +35,8 @@ from typing import Dict, List, Tuple
 
 import numpy as np
 
-from .superblock import IDENTITY, BlockOp, Superblock, pairs_for_target
+from .superblock import (IDENTITY, BlockOp, Superblock, SuperblockL11r, pairs_for_target,
+                         segs_for_target)
 
 Blocks = Dict[Tuple[int, int], np.ndarray]
 
@@ -324,10 +325,9 @@ def superblock_from_blocks(Lb: SBlock, Rb: SBlock, model: str, Q, J=1.0, delta=1
     return sb
 
 
-def warmup_superblock(model: str, L: int, m: int, J=1.0, delta=1.0, t=1.0, U=4.0,
-                      filling=1.0) -> Superblock:
-    """Mid-chain LR superblock of an L-site chain (L even, L >= 4): blocks of
-    l = r = L/2 - 1 sites, enlarged to L/2 sites each, target sector of Sec. 3."""
+def _warmup_blocks(model: str, L: int, m: int, J, delta, t, U, filling):
+    """The blocks l and r of L/2 - 1 sites each that the last step of the warm-up
+    enlarges (Algorithm 1 with the LR strategy, truncated by the recipe above)."""
     if L < 4 or L % 2:
         raise ValueError("L must be even and >= 4")
     if model == "heisenberg":
@@ -342,16 +342,95 @@ def warmup_superblock(model: str, L: int, m: int, J=1.0, delta=1.0, t=1.0, U=4.0
     right = _site_block(labels, sops)
     kw = dict(J=J, delta=delta, t=t, U=U)
     nsites = 1
-    while True:
+    while 2 * (nsites + 1) < L:
         Lb = enlarge(left, model, "L", **kw)
         Rb = enlarge(right, model, "R", **kw)
         nsites += 1
-        if 2 * nsites == L:
-            break
         keepL = allocate(Lb.d, _profile_weights(Lb.q, model, nsites, m, filling), m)
         keepR = allocate(Rb.d, _profile_weights(Rb.q, model, nsites, m, filling), m)
         left, right = truncate(Lb, keepL), truncate(Rb, keepR)
+    return left, right
+
+
+def warmup_superblock(model: str, L: int, m: int, J=1.0, delta=1.0, t=1.0, U=4.0,
+                      filling=1.0) -> Superblock:
+    """Mid-chain LR superblock of an L-site chain (L even, L >= 4): blocks of
+    l = r = L/2 - 1 sites, enlarged to L/2 sites each, target sector of Sec. 3."""
+    left, right = _warmup_blocks(model, L, m, J, delta, t, U, filling)
+    kw = dict(J=J, delta=delta, t=t, U=U)
+    Lb = enlarge(left, model, "L", **kw)
+    Rb = enlarge(right, model, "R", **kw)
     sb = superblock_from_blocks(Lb, Rb, model, target(model, L, filling), J=J, delta=delta, t=t)
+    sb.meta = {"model": model, "L": L, "m": m, "J": J, "delta": delta, "t": t, "U": U,
+               "filling": filling}
+    return sb
+
+
+def superblock_l11r_from_blocks(lb: SBlock, rb: SBlock, model: str, Q, J=1.0, delta=1.0,
+                                t=1.0, U=4.0) -> SuperblockL11r:
+    """The same superblock Hamiltonian in the l-1-1-r form (Sec. 4.2, Eq. 12): the terms of
+    H_SB = H_l + bond(l, s1) + H_s1 + bond(s1, s2) + H_s2 + bond(s2, r) + H_r, each a
+    product of one factor per subsystem.  The bonds are those that the LR form builds into
+    its enlarged blocks (l, s1) and (s2, r) and across them; for fermions the hop out of a
+    subsystem X carries the parity P_X of all of X (c^dag_X P_X (x) c_Y and its transpose),
+    with the modes ordered l, s1, s2, r and, inside a site, down before up (Eqs. 5-6)."""
+    opsl, sops, opsr, terms = [], [], [], []
+
+    def al(bl, name):
+        opsl.append(_to_blockop(bl, name))
+        return len(opsl) - 1
+
+    def ar(bl, name):
+        opsr.append(_to_blockop(bl, name))
+        return len(opsr) - 1
+
+    def as_(M):
+        sops.append(np.ascontiguousarray(M, dtype=np.float64))
+        return len(sops) - 1
+
+    I = IDENTITY
+    if model == "heisenberg":
+        qs, s = _heis_site()
+        sp, sm, sz = as_(s["Sp"]), as_(s["Sp"].T), as_(s["Sz"])
+        terms += [(1.0, al(lb.ops["H"], "H_l"), I, I, I), (1.0, I, I, I, ar(rb.ops["H"], "H_r"))]
+        spl, sml, szl = al(lb.ops["Sp"], "Sp"), al(_btrans(lb.ops["Sp"]), "Sm"), al(lb.ops["Sz"], "Sz")
+        spr, smr, szr = ar(rb.ops["Sp"], "Sp"), ar(_btrans(rb.ops["Sp"]), "Sm"), ar(rb.ops["Sz"], "Sz")
+        for a1, a2, a3, a4 in ((spl, sm, I, I), (sml, sp, I, I), (I, sp, sm, I),
+                               (I, sm, sp, I), (I, I, sp, smr), (I, I, sm, spr)):
+            terms.append((0.5 * J, a1, a2, a3, a4))
+        terms += [(J * delta, szl, sz, I, I), (J * delta, I, sz, sz, I), (J * delta, I, I, sz, szr)]
+    elif model == "hubbard":
+        qs, s = _hub_site(U)
+        P = s["P"]
+        terms += [(1.0, al(lb.ops["H"], "H_l"), I, I, I), (1.0, I, as_(s["H"]), I, I),
+                  (1.0, I, I, as_(s["H"]), I), (1.0, I, I, I, ar(rb.ops["H"], "H_r"))]
+        Pl = _bdiag_sign(lb.parity(), lb.d)
+        for sig in ("up", "dn"):
+            cd = s["cdag_" + sig]
+            cdP = _bmul(lb.ops["cdag_" + sig], Pl)              # c^dag_l P_l
+            lcdP, lPc = al(cdP, "cdagP_" + sig), al(_btrans(cdP), "Pc_" + sig)
+            rc, rcd = ar(_btrans(rb.ops["cdag_" + sig]), "c_" + sig), ar(rb.ops["cdag_" + sig], "cdag_" + sig)
+            c_s, cd_s = as_(cd.T), as_(cd)
+            cdP_s, Pc_s = as_(cd @ P), as_((cd @ P).T)
+            terms += [(-t, lcdP, c_s, I, I), (-t, lPc, cd_s, I, I),      # bond (l, s1)
+                      (-t, I, cdP_s, c_s, I), (-t, I, Pc_s, cd_s, I),    # bond (s1, s2)
+                      (-t, I, I, cdP_s, rc), (-t, I, I, Pc_s, rcd)]      # bond (s2, r)
+    else:
+        raise ValueError(model)
+    segs = segs_for_target(lb.q, qs, rb.q, Q)
+    return SuperblockL11r(ql=list(lb.q), dl=np.array(lb.d, dtype=np.int64), qs=list(qs),
+                          qr=list(rb.q), dr=np.array(rb.d, dtype=np.int64), Q=tuple(Q),
+                          segs=segs, opsl=opsl, sops=sops, opsr=opsr, terms=terms)
+
+
+def warmup_superblock_l11r(model: str, L: int, m: int, J=1.0, delta=1.0, t=1.0, U=4.0,
+                           filling=1.0) -> SuperblockL11r:
+    """The mid-chain superblock of ``warmup_superblock`` with the same arguments, in the
+    l-1-1-r form: the same blocks l and r (L/2 - 1 sites each) and the two middle sites
+    kept apart instead of enlarging the blocks (Sec. 4.2)."""
+    left, right = _warmup_blocks(model, L, m, J, delta, t, U, filling)
+    sb = superblock_l11r_from_blocks(left, right, model, target(model, L, filling), J=J,
+                                     delta=delta, t=t, U=U)
     sb.meta = {"model": model, "L": L, "m": m, "J": J, "delta": delta, "t": t, "U": U,
                "filling": filling}
     return sb
