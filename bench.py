@@ -236,12 +236,16 @@ def run_project(args):
     from dmrg_inputs import warmup
     from paper_1309_5571_gb300 import Plan
     prec = "bf16x2" if args.prec == "auto" else args.prec
-    sb = warmup.workload(args.workload)
+    sb = warmup.workload_l11r(args.workload) if args.strategy == "l11r" else warmup.workload(args.workload)
     x = torch.from_numpy(warmup.start_vector(sb.n, 0)).cuda()
     y = torch.empty_like(x)
-    plan = Plan(sb, prec=prec)
+    plan = Plan(sb, prec=prec, graphs=not args.no_graphs)
     if prec in ("bf16x3", "bf16x2", "tf32"):
-        plan.autotune(prec)
+        if args.sched:   # pinned tile schedules: no autotuning launches before the timed ones
+            s1, s2 = (int(v) for v in args.sched.split(","))
+            plan.set_tile_schedule(s1, s2, prec=prec)
+        else:
+            plan.autotune(prec)
     for _ in range(args.warmup):
         plan.project(x, y, prec=prec)
     torch.cuda.synchronize()
@@ -255,8 +259,11 @@ def run_project(args):
     torch.cuda.synchronize()
     torch.cuda.profiler.stop()
     t = e0.elapsed_time(e1) / 1e3 / args.steps
-    print(json.dumps({"mode": "project", "workload": args.workload, "prec": prec, "n": sb.n,
+    print(json.dumps({"mode": "project", "workload": args.workload, "strategy": args.strategy,
+                      "prec": prec, "n": sb.n, "records": plan.stats["records"],
+                      "flops": plan.stats["flops"],
                       "ms": t * 1e3, "tflops": plan.stats["flops"] / t / 1e12,
+                      "graphs": not args.no_graphs,
                       "tc_schedule": plan.get_stats()["tc_schedule"]}), flush=True)
 
 
@@ -307,12 +314,19 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--prec", default="auto", choices=["auto", "fp64", "tf32", "bf16x3", "bf16x2", "fp64tc"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-l11r", action="store_true",
+                    help="skip the l-1-1-r form of the workload in the solve report")
     ap.add_argument("--proj-reps", type=int, default=10)
     ap.add_argument("--mode", default="solve", choices=["solve", "project", "peaks", "batched"])
     ap.add_argument("--batch", type=int, default=64)
     ap.add_argument("--anchor", default="fp64tc", choices=["fp64", "fp64tc"],
                     help="FP64-accurate projections of the mixed modes")
     ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--sched", default="", help="--mode project: pin the tile schedules 'S1,S2'")
+    ap.add_argument("--strategy", default="lr", choices=["lr", "l11r"],
+                    help="--mode project: the LR form (Eq. 11) or the l-1-1-r form (Eq. 13)")
+    ap.add_argument("--no-graphs", action="store_true",
+                    help="--mode project: launch the projection kernels directly")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -452,6 +466,42 @@ def main():
     fp64_solve_ms = solves["fp64"]["mean_ms"]
     e_fp64 = solves["fp64"]["energy"][0]
 
+    # ---- the same superblock in the l-1-1-r form (Sec. 4.2): projection and solves with the
+    # run's arithmetic, over the same start vectors (the same Hamiltonian, so the same energy)
+    l11r = None
+    if not args.no_l11r:
+        sb4 = warmup.workload_l11r(args.workload)
+        p4 = Plan(sb4, prec=prec, tol=1e-10, anchor_prec=args.anchor)
+        for _ in range(2):
+            p4.project(x0_t, y, prec=prec)
+        t4 = []
+        for _ in range(args.proj_reps):
+            flush.zero_()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            p4.project(x0_t, y, prec=prec)
+            b.record(stream)
+            torch.cuda.synchronize()
+            t4.append(a.elapsed_time(b) / 1e3)
+        p4.solve(x0s_t[0])
+        ms4, it4, e4 = [], [], []
+        for sv in range(nvar):
+            torch.cuda.synchronize()
+            a = time.perf_counter()
+            _, iv = p4.solve(x0s_t[sv])
+            torch.cuda.synchronize()
+            ms4.append((time.perf_counter() - a) * 1e3)
+            it4.append(iv["iters"])
+            e4.append(iv["energy"])
+        l11r = {"records": p4.stats["records"], "flops_per_projection": p4.stats["flops"],
+                "projection_ms": statistics.mean(t4) * 1e3,
+                "projection_tflops": p4.stats["flops"] / statistics.mean(t4) / 1e12,
+                "solve_ms": statistics.mean(ms4), "solve_ms_each": ms4, "iters": it4,
+                "dE_vs_fp64_path": max(abs(e - e_fp64) for e in e4),
+                "start_vector_seeds": seeds[:nvar], "prec": prec}
+        p4.close()
+
     pk, pk_kind = peaks()
     if prec == "fp64":
         bound, peak, unit = "alu", FP64_DGEMM_TFLOPS, "TFLOP/s"
@@ -528,6 +578,7 @@ def main():
                              "dE_vs_fp64_path": max(abs(e - e_fp64) for e in solves[p]["energy"])}
                          for p in variants},
             "projection_ms": {p: v * 1e3 for p, v in proj.items()},
+            "l11r": l11r,
             "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_val, "unit": "TFLOP/s", "h2d_bytes_per_step": 8 * sb.n,

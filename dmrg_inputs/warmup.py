@@ -455,6 +455,11 @@ def workload(name: str) -> Superblock:
     return warmup_superblock(**WORKLOADS[name])
 
 
+def workload_l11r(name: str) -> SuperblockL11r:
+    """The named workload's superblock in the l-1-1-r form (same Hamiltonian)."""
+    return warmup_superblock_l11r(**WORKLOADS[name])
+
+
 def batched_workload(count: int = 64, ms=(256, 512, 1024, 2048), L: int = 100, seed: int = 1234,
                      model: str = "heisenberg"):
     """Independent superblocks of uneven size: m_i drawn uniformly from ``ms`` (NumPy

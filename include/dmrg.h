@@ -122,6 +122,43 @@ typedef struct {
   int32_t data_location;          /* DMRG_HOST_DATA or DMRG_DEVICE_DATA               */
 } dmrg_superblock_desc;
 
+/* A superblock in the l-1-1-r form of Sec. 4.2:
+ *
+ *     H_SB = sum_a coef_a  A_a^(l) (x) a_a (x) b_a (x) B_a^(r)              (Eq. 12)
+ *
+ * with A on block l, a and b on the two middle sites, B on block r, and the projection of
+ * Eq. 13 (Algorithm 2 per term).  Every site state is a sector of its own (its quantum
+ * numbers differ from the others'), so a site operator is a dense q x q matrix.  A vector
+ * is the concatenation, in the order of the segment list, of the row-major segments
+ * (i, s1, s2, k) of shape [diml[i], dimr[k]]: element psi(a, b) of segment g sits at
+ * x[offset_g + a * dimr[k] + b]. */
+typedef struct {
+  double coef;
+  int32_t l_op, s1_op, s2_op, r_op; /* DMRG_IDENTITY_OP: the identity on that subsystem */
+} dmrg_term4;
+
+typedef struct {
+  int32_t nl, nr;                   /* sectors of block l and of block r               */
+  const int64_t* diml;              /* host arrays of their dimensions                 */
+  const int64_t* dimr;
+  int32_t q;                        /* states of one site (at most 64)                 */
+  int32_t nsegs;                    /* valid (i, s1, s2, k), storage order             */
+  const int32_t* seg_l;             /* host arrays of length nsegs                     */
+  const int32_t* seg_s1;
+  const int32_t* seg_s2;
+  const int32_t* seg_r;
+  int32_t nopsl, nopsr;
+  const dmrg_operator* opsl;        /* block operators of l and r (blocks host or
+                                       device per data_location)                       */
+  const dmrg_operator* opsr;
+  int32_t nsops;
+  const double* sops;               /* host: nsops site matrices, each q x q row-major
+                                       with element [s_out * q + s_in]                 */
+  int32_t nterms;
+  const dmrg_term4* terms;          /* host array                                      */
+  int32_t data_location;            /* DMRG_HOST_DATA or DMRG_DEVICE_DATA              */
+} dmrg_l11r_desc;
+
 /* Arithmetic of the Davidson vector passes (overlap, residual, Gram-Schmidt; the paper
    runs them in FP64, Sec. 6.1).  GB300 executes about 0.55 T FP64 FMA/s against 6.8 TB/s
    of HBM, so the FP64 passes are bound by the FP64 units.
@@ -215,6 +252,17 @@ void dmrg_options_default(dmrg_options* opt);
  * dmrg_plan_destroy. */
 dmrg_status dmrg_plan_create(const dmrg_superblock_desc* desc, const dmrg_options* opt,
                              void* stream, dmrg_plan** out);
+/* Plan of a superblock in the l-1-1-r form (Sec. 4.2, Eqs. 12-13; the paper describes the
+ * form and leaves its implementation open).  Every call that takes a plan (projections in
+ * every precision, the Davidson solves, autotuning, batched solves) works on it as on an
+ * LR plan; the vector layout is that of dmrg_l11r_desc.  The site factors are single
+ * elements of their matrices (each site state is a sector), so stages 2 and 3 of
+ * Algorithm 2 become coefficients of the records, and each record is the product of a
+ * block of l, a segment and a block of r: the largest matrices are those of the blocks,
+ * O(m^2), instead of the O((mq)^2) enlarged blocks of the LR form.  Same ownership and
+ * error rules as dmrg_plan_create. */
+dmrg_status dmrg_plan_create_l11r(const dmrg_l11r_desc* desc, const dmrg_options* opt,
+                                  void* stream, dmrg_plan** out);
 void dmrg_plan_destroy(dmrg_plan* plan);
 dmrg_status dmrg_plan_get_stats(const dmrg_plan* plan, dmrg_plan_stats* stats);
 

@@ -62,6 +62,24 @@ class SuperblockDesc(C.Structure):
                 ("data_location", C.c_int32)]
 
 
+class Term4(C.Structure):
+    _fields_ = [("coef", C.c_double), ("l_op", C.c_int32), ("s1_op", C.c_int32),
+                ("s2_op", C.c_int32), ("r_op", C.c_int32)]
+
+
+class L11rDesc(C.Structure):
+    _fields_ = [("nl", C.c_int32), ("nr", C.c_int32),
+                ("diml", C.POINTER(C.c_int64)), ("dimr", C.POINTER(C.c_int64)),
+                ("q", C.c_int32), ("nsegs", C.c_int32),
+                ("seg_l", C.POINTER(C.c_int32)), ("seg_s1", C.POINTER(C.c_int32)),
+                ("seg_s2", C.POINTER(C.c_int32)), ("seg_r", C.POINTER(C.c_int32)),
+                ("nopsl", C.c_int32), ("nopsr", C.c_int32),
+                ("opsl", C.POINTER(Operator)), ("opsr", C.POINTER(Operator)),
+                ("nsops", C.c_int32), ("sops", C.POINTER(C.c_double)),
+                ("nterms", C.c_int32), ("terms", C.POINTER(Term4)),
+                ("data_location", C.c_int32)]
+
+
 class Options(C.Structure):
     _fields_ = [("prec", C.c_int32), ("tol", C.c_double), ("max_iter", C.c_int32),
                 ("max_subspace", C.c_int32), ("restart_keep", C.c_int32), ("fp64_refine", C.c_int32),
@@ -97,6 +115,8 @@ SIGNATURES = {
     "dmrg_options_default": (None, [C.POINTER(Options)]),
     "dmrg_plan_create": (C.c_int, [C.POINTER(SuperblockDesc), C.POINTER(Options), C.c_void_p,
                                    C.POINTER(C.c_void_p)]),
+    "dmrg_plan_create_l11r": (C.c_int, [C.POINTER(L11rDesc), C.POINTER(Options), C.c_void_p,
+                                        C.POINTER(C.c_void_p)]),
     "dmrg_plan_destroy": (None, [C.c_void_p]),
     "dmrg_plan_get_stats": (C.c_int, [C.c_void_p, C.POINTER(PlanStats)]),
     "dmrg_plan_autotune": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
@@ -181,8 +201,48 @@ def _check_vec(t, n, name):
 
 @dataclass
 class _Marshalled:
-    desc: SuperblockDesc
+    desc: object
     keep: list
+
+
+def _ops_array(ops, keep):
+    arr = (Operator * max(1, len(ops)))()
+    for o, op in enumerate(ops):
+        items = sorted(op.blocks.items())
+        blocks = (Block * max(1, len(items)))()
+        for b, ((i, j), M) in enumerate(items):
+            M = np.ascontiguousarray(M, dtype=np.float64)
+            keep.append(M)
+            blocks[b] = Block(i, j, M.shape[0], M.shape[1], M.shape[1], M.ctypes.data)
+        keep.append(blocks)
+        arr[o] = Operator(len(items), blocks)
+    keep.append(arr)
+    return arr
+
+
+def marshal_l11r(sb) -> _Marshalled:
+    """l-1-1-r superblock container -> C descriptor (host data); keeps the arrays alive."""
+    keep = []
+    diml = np.ascontiguousarray(sb.dl, dtype=np.int64)
+    dimr = np.ascontiguousarray(sb.dr, dtype=np.int64)
+    segs = np.asarray(sb.segs, dtype=np.int32).reshape(-1, 4)
+    cols = [np.ascontiguousarray(segs[:, c]) for c in range(4)]
+    q = len(sb.qs)
+    sops = np.ascontiguousarray(np.stack(sb.sops).reshape(-1) if sb.sops else np.zeros(1), dtype=np.float64)
+    keep += [diml, dimr, sops, *cols]
+    opsl, opsr = _ops_array(sb.opsl, keep), _ops_array(sb.opsr, keep)
+    terms = (Term4 * max(1, len(sb.terms)))()
+    for t, (coef, a, s1, s2, b) in enumerate(sb.terms):
+        terms[t] = Term4(float(coef), int(a), int(s1), int(s2), int(b))
+    keep.append(terms)
+    i32 = C.POINTER(C.c_int32)
+    desc = L11rDesc(len(diml), len(dimr), diml.ctypes.data_as(C.POINTER(C.c_int64)),
+                    dimr.ctypes.data_as(C.POINTER(C.c_int64)), q, len(segs),
+                    cols[0].ctypes.data_as(i32), cols[1].ctypes.data_as(i32),
+                    cols[2].ctypes.data_as(i32), cols[3].ctypes.data_as(i32),
+                    len(sb.opsl), len(sb.opsr), opsl, opsr, len(sb.sops),
+                    sops.ctypes.data_as(C.POINTER(C.c_double)), len(sb.terms), terms, 0)
+    return _Marshalled(desc, keep)
 
 
 def marshal(sb) -> _Marshalled:
@@ -242,16 +302,23 @@ def options(prec="fp64", tol=1e-10, max_iter=1000, max_subspace=20, restart_keep
 
 
 class Plan:
-    """A planned superblock problem on the current CUDA device (dmrg_plan_create)."""
+    """A planned superblock problem on the current CUDA device: dmrg_plan_create for an LR
+    superblock, dmrg_plan_create_l11r for one in the l-1-1-r form (a container with
+    ``segs`` and ``sops``)."""
 
     def __init__(self, sb, stream=None, **opts):
         torch = _torch()
         self.lib = load()
-        m = marshal(sb)
         self.opt = options(**opts)
         h = C.c_void_p()
-        _check(self.lib.dmrg_plan_create(C.byref(m.desc), C.byref(self.opt), _stream_ptr(stream),
-                                         C.byref(h)))
+        if hasattr(sb, "segs"):
+            m = marshal_l11r(sb)
+            _check(self.lib.dmrg_plan_create_l11r(C.byref(m.desc), C.byref(self.opt),
+                                                  _stream_ptr(stream), C.byref(h)))
+        else:
+            m = marshal(sb)
+            _check(self.lib.dmrg_plan_create(C.byref(m.desc), C.byref(self.opt), _stream_ptr(stream),
+                                             C.byref(h)))
         self.handle = h
         st = PlanStats()
         _check(self.lib.dmrg_plan_get_stats(self.handle, C.byref(st)))

@@ -115,7 +115,7 @@ dmrg_status launch_project_fp64(dmrg_plan* p, const double* x, double* y, cudaSt
                                                              p->d_segs, b, p->T, y);
     DMRG_LAUNCH_CHECK();
   }
-  return DMRG_OK;
+  return launch_seg_axpy(p, x, y, nullptr, nullptr, st);
 }
 
 }  // namespace dmrg

@@ -574,7 +574,7 @@ dmrg_status build_oz(dmrg_plan* p, cudaStream_t st, OzPlan** out) {
       } else if (r.b_blk >= 0) {
         if (r.dk > 0) segs.push_back(seg(1, xa[r.pin], 0, op_image(1, b_op, r.b_blk, r.coef), cdiv(r.dk, 64)));
       } else {
-        job.axpy += r.coef;
+        if (r.pin == r.pout) job.axpy += r.coef;  // (other segments: seg_axpy pass)
       }
     }
     job.seg_end = (int32_t)segs.size();
@@ -716,7 +716,7 @@ dmrg_status launch_project_oz(dmrg_plan* p, const double* x, double* y, cudaStre
         o->exps[0], o->exps[1], o->exps[2], p->T, y, x, o->d_err);
     DMRG_LAUNCH_CHECK();
   }
-  return DMRG_OK;
+  return launch_seg_axpy(p, x, y, nullptr, nullptr, st);
 }
 
 }  // namespace dmrg

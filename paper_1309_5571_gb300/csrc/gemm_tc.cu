@@ -1004,7 +1004,7 @@ dmrg_status build_tc(dmrg_plan* p, dmrg_precision prec, cudaStream_t st, TcPlan*
         if (r.dk > 0)
           segs.push_back(seg(TB_XA, xa[r.pin], TB_OPS, op_image(1, b_op, r.b_blk, r.coef), ceil_div(r.dk, KT)));
       } else {
-        job.axpy += r.coef;
+        if (r.pin == r.pout) job.axpy += r.coef;  // (other segments: seg_axpy pass)
       }
     }
     job.seg_end = (int32_t)segs.size();
@@ -1305,7 +1305,7 @@ dmrg_status run_tc_direct(dmrg_plan* p, TcPlan* t, const VecIO& io, cudaStream_t
   DMRG_TRY((run_tc_part<PLANES, STAGES, TF32>(p, t, io, 0, 0, st)));
   DMRG_TRY((run_tc_part<PLANES, STAGES, TF32>(p, t, io, 1, t->sched[0], st)));
   DMRG_TRY((run_tc_part<PLANES, STAGES, TF32>(p, t, io, 2, t->sched[1], st)));
-  return DMRG_OK;
+  return launch_seg_axpy(p, io.x, io.y, io.x32, io.y32, st);
 }
 
 template <int PLANES, int STAGES, bool TF32>
@@ -1618,7 +1618,7 @@ dmrg_status tc_batch_error(const TcBatch* b) {
 
 namespace {
 template <int PLANES, int STAGES, bool TF32>
-dmrg_status run_batch(TcBatch* b, cudaStream_t st) {
+dmrg_status run_batch(TcBatch* b, const TcPtrs* h, cudaStream_t st) {
   constexpr bool WIDE = !TF32;
   constexpr size_t smem = tc::smem_bytes<PLANES, STAGES, TF32, WIDE>();
   DMRG_TRY((configure_tc<PLANES, STAGES, TF32>()));
@@ -1637,6 +1637,9 @@ dmrg_status run_batch(TcBatch* b, cudaStream_t st) {
         nullptr, nullptr);
     DMRG_LAUNCH_CHECK();
   }
+  for (size_t i = 0; i < b->plans.size(); ++i)  // cross-segment identity terms, per problem
+    if (h[i].active)
+      DMRG_TRY(launch_seg_axpy(b->plans[i], h[i].x, h[i].y, h[i].x32, h[i].y32, st));
   return DMRG_OK;
 }
 }  // namespace
@@ -1671,9 +1674,9 @@ dmrg_status tc_batch_project(TcBatch* b, const double* const* x, double* const* 
   DMRG_CUDA_TRY(cudaMemcpyAsync(b->d_ptrs, h, sizeof(TcPtrs) * b->plans.size(),
                                 cudaMemcpyHostToDevice, st));
   DMRG_CUDA_TRY(cudaEventRecord(b->ev[r], st));
-  if (b->prec == DMRG_PREC_TF32) return run_batch<1, 6, true>(b, st);
-  if (b->prec == DMRG_PREC_BF16X2) return run_batch<2, 4, false>(b, st);
-  return run_batch<3, 3, false>(b, st);
+  if (b->prec == DMRG_PREC_TF32) return run_batch<1, 6, true>(b, h, st);
+  if (b->prec == DMRG_PREC_BF16X2) return run_batch<2, 4, false>(b, h, st);
+  return run_batch<3, 3, false>(b, h, st);
 }
 
 bool tc_available(dmrg_precision prec) { return tc_lowprec(prec) || prec == DMRG_PREC_FP64_TC; }

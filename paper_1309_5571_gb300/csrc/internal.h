@@ -136,6 +136,20 @@ struct HostBlock {
   int64_t arena_off;     // row-major, ld = cols
 };
 
+// Records whose block factors are both identities add coef * X(pin) to Y(pout).  In the
+// LR form pin == pout, and the GEMM epilogues add the term in place; in the l-1-1-r form
+// the site factors can move the state to another segment of the same dimensions, and a
+// pass after the last GEMM stage adds those terms (one group per output segment, entries
+// in record order).
+struct SegAxpyGroup {
+  int64_t dst_off, size;
+  int32_t beg, end;
+};
+struct SegAxpyEntry {
+  int64_t src_off;
+  double coef;
+};
+
 struct TcPlan;           // tensor-core (low precision) part, see gemm_tc.cu
 struct OzPlan;           // FP64-accurate tensor-core part, see gemm_oz.cu
 
@@ -166,6 +180,11 @@ struct dmrg_plan {
   dmrg::Tile64* d_tiles2 = nullptr;
   int64_t ntiles1 = 0, ntiles2 = 0;
   size_t device_bytes = 0;
+
+  dmrg::SegAxpyGroup* d_sax_groups = nullptr;  // cross-segment identity terms (l-1-1-r form)
+  dmrg::SegAxpyEntry* d_sax_entries = nullptr;
+  int32_t n_sax_groups = 0;
+  int64_t sax_max_size = 0;
 
   dmrg::TcPlan* tc[3] = {nullptr, nullptr, nullptr};  // TF32, BF16x3, BF16x2; built on first use
   dmrg::OzPlan* oz = nullptr;                 // FP64 emulation; built on first use
@@ -329,6 +348,10 @@ dmrg_status launch_gemv_trans_public(const double* V, int64_t ldv, int64_t n, in
 
 // plan.cu
 dmrg_status compute_diagonal(dmrg_plan* plan, double* d, cudaStream_t st);
+// y(pout) += coef x(pin) for the cross-segment identity terms (no-op without any); FP64
+// vectors, or FP32 ones when x32 is given
+dmrg_status launch_seg_axpy(const dmrg_plan* plan, const double* x, double* y, const float* x32,
+                            float* y32, cudaStream_t st);
 
 inline int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
 

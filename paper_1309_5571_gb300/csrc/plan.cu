@@ -19,6 +19,88 @@ using namespace dmrg;
 
 namespace {
 
+// Operators of one side (left or right), validated against that side's sector dimensions
+// and laid out in the host arena (row-major, ld = cols, 256-byte aligned blocks); the data
+// is copied by copy_ops once the arena exists.
+dmrg_status layout_ops(int nops, const dmrg_operator* ops, const std::vector<int64_t>& dim,
+                       std::vector<std::vector<HostBlock>>& dst, size_t* total) {
+  const int nsec = (int)dim.size();
+  dst.assign(nops, {});
+  for (int o = 0; o < nops; ++o) {
+    if (ops[o].nblocks < 0 || (ops[o].nblocks && !ops[o].blocks)) {
+      set_error("operator %d has a bad block list", o);
+      return DMRG_ERR_INVALID_ARG;
+    }
+    std::map<std::pair<int, int>, int> keys;
+    for (int b = 0; b < ops[o].nblocks; ++b) {
+      const dmrg_block& blk = ops[o].blocks[b];
+      if (blk.idx_in < 0 || blk.idx_in >= nsec || blk.idx_out < 0 || blk.idx_out >= nsec) {
+        set_error("operator %d block %d: sector index out of range", o, b);
+        return DMRG_ERR_INVALID_ARG;
+      }
+      if (blk.rows != dim[blk.idx_out] || blk.cols != dim[blk.idx_in] || blk.ld < blk.cols ||
+          (blk.rows * blk.cols > 0 && !blk.data)) {
+        set_error("operator %d block %d (%d->%d): shape %lldx%lld (ld %lld) does not match "
+                  "sectors %lldx%lld",
+                  o, b, blk.idx_in, blk.idx_out, (long long)blk.rows, (long long)blk.cols,
+                  (long long)blk.ld, (long long)dim[blk.idx_out], (long long)dim[blk.idx_in]);
+        return DMRG_ERR_SHAPE;
+      }
+      if (!keys.emplace(std::make_pair(blk.idx_in, blk.idx_out), b).second) {
+        set_error("operator %d has two blocks %d->%d", o, blk.idx_in, blk.idx_out);
+        return DMRG_ERR_SHAPE;
+      }
+      HostBlock hb{blk.idx_in, blk.idx_out, blk.rows, blk.cols, (int64_t)*total};
+      dst[o].push_back(hb);
+      *total += (size_t)round_up(blk.rows * blk.cols, 32);  // 256-byte aligned blocks
+    }
+  }
+  return DMRG_OK;
+}
+
+dmrg_status copy_ops(int nops, const dmrg_operator* ops, const std::vector<std::vector<HostBlock>>& lay,
+                     int location, dmrg_plan* p) {
+  for (int o = 0; o < nops; ++o) {
+    for (int b = 0; b < ops[o].nblocks; ++b) {
+      const dmrg_block& blk = ops[o].blocks[b];
+      double* out = p->arena_host.data() + lay[o][b].arena_off;
+      if (blk.rows * blk.cols == 0) continue;
+      if (location == DMRG_HOST_DATA) {
+        for (int64_t r = 0; r < blk.rows; ++r)
+          std::memcpy(out + r * blk.cols, blk.data + r * blk.ld, sizeof(double) * blk.cols);
+      } else {
+        DMRG_CUDA_TRY(cudaMemcpy2D(out, sizeof(double) * blk.cols, blk.data,
+                                   sizeof(double) * blk.ld, sizeof(double) * blk.cols,
+                                   blk.rows, cudaMemcpyDeviceToHost));
+      }
+    }
+  }
+  return DMRG_OK;
+}
+
+// pair list (i, k) into sectors of p->dimL x p->dimR; segment offsets and n
+dmrg_status set_pairs(dmrg_plan* p, int npairs, const int32_t* pi, const int32_t* pk) {
+  const int nL = (int)p->dimL.size(), nR = (int)p->dimR.size();
+  p->pair_i.assign(pi, pi + npairs);
+  p->pair_k.assign(pk, pk + npairs);
+  p->pair_off.assign(npairs + 1, 0);
+  std::map<std::pair<int, int>, int> seen;
+  for (int q = 0; q < npairs; ++q) {
+    int i = p->pair_i[q], k = p->pair_k[q];
+    if (i < 0 || i >= nL || k < 0 || k >= nR) {
+      set_error("pair %d = (%d,%d) out of range", q, i, k);
+      return DMRG_ERR_INVALID_ARG;
+    }
+    if (!seen.emplace(std::make_pair(i, k), q).second) {
+      set_error("pair (%d,%d) listed twice", i, k);
+      return DMRG_ERR_SHAPE;
+    }
+    p->pair_off[q + 1] = p->pair_off[q] + p->dimL[i] * p->dimR[k];
+  }
+  p->n = p->pair_off[npairs];
+  return DMRG_OK;
+}
+
 dmrg_status validate_and_copy(const dmrg_superblock_desc* d, dmrg_plan* p) {
   if (!d) {
     set_error("desc is NULL");
@@ -44,23 +126,7 @@ dmrg_status validate_and_copy(const dmrg_superblock_desc* d, dmrg_plan* p) {
     if (v < 0) { set_error("negative left sector dimension"); return DMRG_ERR_INVALID_ARG; }
   for (auto v : p->dimR)
     if (v < 0) { set_error("negative right sector dimension"); return DMRG_ERR_INVALID_ARG; }
-  p->pair_i.assign(d->pair_i, d->pair_i + d->npairs);
-  p->pair_k.assign(d->pair_k, d->pair_k + d->npairs);
-  p->pair_off.assign(d->npairs + 1, 0);
-  std::map<std::pair<int, int>, int> seen;
-  for (int q = 0; q < d->npairs; ++q) {
-    int i = p->pair_i[q], k = p->pair_k[q];
-    if (i < 0 || i >= d->nL || k < 0 || k >= d->nR) {
-      set_error("pair %d = (%d,%d) out of range", q, i, k);
-      return DMRG_ERR_INVALID_ARG;
-    }
-    if (!seen.emplace(std::make_pair(i, k), q).second) {
-      set_error("pair (%d,%d) listed twice", i, k);
-      return DMRG_ERR_SHAPE;
-    }
-    p->pair_off[q + 1] = p->pair_off[q] + p->dimL[i] * p->dimR[k];
-  }
-  p->n = p->pair_off[d->npairs];
+  DMRG_TRY(set_pairs(p, d->npairs, d->pair_i, d->pair_k));
   p->terms.assign(d->terms, d->terms + d->nterms);
   for (auto& t : p->terms) {
     if ((t.a_op != DMRG_IDENTITY_OP && (t.a_op < 0 || t.a_op >= d->nopsL)) ||
@@ -69,67 +135,84 @@ dmrg_status validate_and_copy(const dmrg_superblock_desc* d, dmrg_plan* p) {
       return DMRG_ERR_INVALID_ARG;
     }
   }
-  // stage all blocks into one host arena (row-major, ld = cols)
   size_t total = 0;
-  for (int side = 0; side < 2; ++side) {
-    int nops = side ? d->nopsR : d->nopsL;
-    const dmrg_operator* ops = side ? d->opsR : d->opsL;
-    const std::vector<int64_t>& dim = side ? p->dimR : p->dimL;
-    int nsec = side ? d->nR : d->nL;
-    auto& dst = side ? p->opsR : p->opsL;
-    dst.assign(nops, {});
-    for (int o = 0; o < nops; ++o) {
-      if (ops[o].nblocks < 0 || (ops[o].nblocks && !ops[o].blocks)) {
-        set_error("operator %d has a bad block list", o);
-        return DMRG_ERR_INVALID_ARG;
-      }
-      std::map<std::pair<int, int>, int> keys;
-      for (int b = 0; b < ops[o].nblocks; ++b) {
-        const dmrg_block& blk = ops[o].blocks[b];
-        if (blk.idx_in < 0 || blk.idx_in >= nsec || blk.idx_out < 0 || blk.idx_out >= nsec) {
-          set_error("operator %d block %d: sector index out of range", o, b);
-          return DMRG_ERR_INVALID_ARG;
-        }
-        if (blk.rows != dim[blk.idx_out] || blk.cols != dim[blk.idx_in] || blk.ld < blk.cols ||
-            (blk.rows * blk.cols > 0 && !blk.data)) {
-          set_error("operator %d block %d (%d->%d): shape %lldx%lld (ld %lld) does not match "
-                    "sectors %lldx%lld",
-                    o, b, blk.idx_in, blk.idx_out, (long long)blk.rows, (long long)blk.cols,
-                    (long long)blk.ld, (long long)dim[blk.idx_out], (long long)dim[blk.idx_in]);
-          return DMRG_ERR_SHAPE;
-        }
-        if (!keys.emplace(std::make_pair(blk.idx_in, blk.idx_out), b).second) {
-          set_error("operator %d has two blocks %d->%d", o, blk.idx_in, blk.idx_out);
-          return DMRG_ERR_SHAPE;
-        }
-        HostBlock hb{blk.idx_in, blk.idx_out, blk.rows, blk.cols, (int64_t)total};
-        dst[o].push_back(hb);
-        total += (size_t)round_up(blk.rows * blk.cols, 32);  // 256-byte aligned blocks
-      }
-    }
-  }
+  DMRG_TRY(layout_ops(d->nopsL, d->opsL, p->dimL, p->opsL, &total));
+  DMRG_TRY(layout_ops(d->nopsR, d->opsR, p->dimR, p->opsR, &total));
   p->arena_elems = total;
   p->arena_host.assign(total, 0.0);
-  for (int side = 0; side < 2; ++side) {
-    int nops = side ? d->nopsR : d->nopsL;
-    const dmrg_operator* ops = side ? d->opsR : d->opsL;
-    auto& dst = side ? p->opsR : p->opsL;
-    for (int o = 0; o < nops; ++o) {
-      for (int b = 0; b < ops[o].nblocks; ++b) {
-        const dmrg_block& blk = ops[o].blocks[b];
-        double* out = p->arena_host.data() + dst[o][b].arena_off;
-        if (blk.rows * blk.cols == 0) continue;
-        if (d->data_location == DMRG_HOST_DATA) {
-          for (int64_t r = 0; r < blk.rows; ++r)
-            std::memcpy(out + r * blk.cols, blk.data + r * blk.ld, sizeof(double) * blk.cols);
-        } else {
-          DMRG_CUDA_TRY(cudaMemcpy2D(out, sizeof(double) * blk.cols, blk.data,
-                                     sizeof(double) * blk.ld, sizeof(double) * blk.cols,
-                                     blk.rows, cudaMemcpyDeviceToHost));
-        }
-      }
-    }
+  DMRG_TRY(copy_ops(d->nopsL, d->opsL, p->opsL, d->data_location, p));
+  DMRG_TRY(copy_ops(d->nopsR, d->opsR, p->opsR, d->data_location, p));
+  return DMRG_OK;
+}
+
+// The l-1-1-r form (Sec. 4.2, Eq. 12) presented to the record engine: the block-l sector i
+// and the two site states form one "left" sector (i, s1, s2) of dimension dim_l(i); the
+// factors of block l and r keep their own blocks, and the site factors -- single elements,
+// every site state being a sector of its own -- become coefficients of the records
+// (stages 2 and 3 of Algorithm 2 are scalar multiplications).  p->opsL holds the block-l
+// operators with block-l sector indices; p->terms one entry per term of Eq. 12 (its block-l
+// and block-r factors).
+dmrg_status validate_and_copy_l11r(const dmrg_l11r_desc* d, dmrg_plan* p,
+                                   std::vector<int64_t>* diml) {
+  if (!d) {
+    set_error("desc is NULL");
+    return DMRG_ERR_INVALID_ARG;
   }
+  if (d->nl <= 0 || d->nr <= 0 || d->q <= 0 || d->q > 64 || d->nsegs < 0 || d->nterms < 0 ||
+      d->nopsl < 0 || d->nopsr < 0 || d->nsops < 0) {
+    set_error("bad sector, site, segment, term or operator counts");
+    return DMRG_ERR_INVALID_ARG;
+  }
+  if (!d->diml || !d->dimr || (d->nsegs && (!d->seg_l || !d->seg_s1 || !d->seg_s2 || !d->seg_r)) ||
+      (d->nterms && !d->terms) || (d->nopsl && !d->opsl) || (d->nopsr && !d->opsr) ||
+      (d->nsops && !d->sops)) {
+    set_error("NULL array in desc");
+    return DMRG_ERR_INVALID_ARG;
+  }
+  if (d->data_location != DMRG_HOST_DATA && d->data_location != DMRG_DEVICE_DATA) {
+    set_error("data_location must be DMRG_HOST_DATA or DMRG_DEVICE_DATA");
+    return DMRG_ERR_INVALID_ARG;
+  }
+  const int q = d->q;
+  diml->assign(d->diml, d->diml + d->nl);
+  p->dimR.assign(d->dimr, d->dimr + d->nr);
+  for (auto v : *diml)
+    if (v < 0) { set_error("negative block-l sector dimension"); return DMRG_ERR_INVALID_ARG; }
+  for (auto v : p->dimR)
+    if (v < 0) { set_error("negative block-r sector dimension"); return DMRG_ERR_INVALID_ARG; }
+  p->dimL.assign((size_t)d->nl * q * q, 0);
+  for (int i = 0; i < d->nl; ++i)
+    for (int t = 0; t < q * q; ++t) p->dimL[(size_t)i * q * q + t] = (*diml)[i];
+  std::vector<int32_t> pi(d->nsegs), pk(d->nsegs);
+  for (int g = 0; g < d->nsegs; ++g) {
+    const int i = d->seg_l[g], s1 = d->seg_s1[g], s2 = d->seg_s2[g];
+    if (i < 0 || i >= d->nl || s1 < 0 || s1 >= q || s2 < 0 || s2 >= q) {
+      set_error("segment %d = (%d,%d,%d,%d) out of range", g, i, s1, s2, d->seg_r[g]);
+      return DMRG_ERR_INVALID_ARG;
+    }
+    pi[g] = (i * q + s1) * q + s2;
+    pk[g] = d->seg_r[g];
+  }
+  DMRG_TRY(set_pairs(p, d->nsegs, pi.data(), pk.data()));
+  p->terms.clear();
+  for (int t = 0; t < d->nterms; ++t) {
+    const dmrg_term4& tm = d->terms[t];
+    if ((tm.l_op != DMRG_IDENTITY_OP && (tm.l_op < 0 || tm.l_op >= d->nopsl)) ||
+        (tm.r_op != DMRG_IDENTITY_OP && (tm.r_op < 0 || tm.r_op >= d->nopsr)) ||
+        (tm.s1_op != DMRG_IDENTITY_OP && (tm.s1_op < 0 || tm.s1_op >= d->nsops)) ||
+        (tm.s2_op != DMRG_IDENTITY_OP && (tm.s2_op < 0 || tm.s2_op >= d->nsops))) {
+      set_error("term %d names a missing operator", t);
+      return DMRG_ERR_INVALID_ARG;
+    }
+    p->terms.push_back(dmrg_term{tm.coef, tm.l_op, tm.r_op});
+  }
+  size_t total = 0;
+  DMRG_TRY(layout_ops(d->nopsl, d->opsl, *diml, p->opsL, &total));
+  DMRG_TRY(layout_ops(d->nopsr, d->opsr, p->dimR, p->opsR, &total));
+  p->arena_elems = total;
+  p->arena_host.assign(total, 0.0);
+  DMRG_TRY(copy_ops(d->nopsl, d->opsl, p->opsL, d->data_location, p));
+  DMRG_TRY(copy_ops(d->nopsr, d->opsr, p->opsR, d->data_location, p));
   return DMRG_OK;
 }
 
@@ -155,7 +238,28 @@ void add_tiles(std::vector<Tile64>& tiles, int job, int64_t M, int64_t N) {
       tiles.push_back(Tile64{job, (int32_t)m0, (int32_t)n0, 0});
 }
 
-dmrg_status build_records_and_jobs(dmrg_plan* p, Builder* bld) {
+// A record's multiplication order, FLOPs and intermediate buffer slot (Sec. 7: the
+// workload of each record is known once the plan exists).
+void finish_record(dmrg_plan* p, Record& r, int64_t* inter) {
+  r.inter_off = -1;
+  if (r.a_blk >= 0 && r.b_blk >= 0) {
+    int64_t cA = 2 * r.dj * r.di * r.dk + 2 * r.dj * r.dk * r.dl;
+    int64_t cB = 2 * r.di * r.dk * r.dl + 2 * r.dj * r.di * r.dl;
+    r.a_first = cA <= cB ? 1 : 0;
+    p->flops += std::min(cA, cB);
+    r.inter_off = *inter;
+    *inter += round_up(r.a_first ? r.dj * r.dk : r.di * r.dl, 32);
+  } else if (r.a_blk >= 0) {
+    p->flops += 2 * r.dj * r.di * r.dk;
+  } else if (r.b_blk >= 0) {
+    p->flops += 2 * r.di * r.dk * r.dl;
+  }
+  p->records.push_back(r);
+}
+
+// LR form (Eq. 11): one record per term and pair of blocks whose input (i, k) and output
+// (j, l) segments are in the sector
+void build_records_lr(dmrg_plan* p) {
   const int npairs = (int)p->pair_i.size();
   std::map<std::pair<int, int>, int> pidx;
   for (int q = 0; q < npairs; ++q) pidx[{p->pair_i[q], p->pair_k[q]}] = q;
@@ -163,7 +267,6 @@ dmrg_status build_records_and_jobs(dmrg_plan* p, Builder* bld) {
   std::vector<HostBlock> idL(nL), idR(nR);
   for (int i = 0; i < nL; ++i) idL[i] = HostBlock{i, i, p->dimL[i], p->dimL[i], -1};
   for (int k = 0; k < nR; ++k) idR[k] = HostBlock{k, k, p->dimR[k], p->dimR[k], -1};
-
   p->records.clear();
   p->flops = 0;
   int64_t inter = 0;
@@ -187,25 +290,82 @@ dmrg_status build_records_and_jobs(dmrg_plan* p, Builder* bld) {
         r.i = A.idx_in; r.j = A.idx_out; r.k = B.idx_in; r.l = B.idx_out;
         r.di = p->dimL[r.i]; r.dj = p->dimL[r.j]; r.dk = p->dimR[r.k]; r.dl = p->dimR[r.l];
         r.coef = term.coef;
-        r.inter_off = -1;
-        if (r.a_blk >= 0 && r.b_blk >= 0) {
-          int64_t cA = 2 * r.dj * r.di * r.dk + 2 * r.dj * r.dk * r.dl;
-          int64_t cB = 2 * r.di * r.dk * r.dl + 2 * r.dj * r.di * r.dl;
-          r.a_first = cA <= cB ? 1 : 0;
-          p->flops += std::min(cA, cB);
-          r.inter_off = inter;
-          inter += round_up(r.a_first ? r.dj * r.dk : r.di * r.dl, 32);
-        } else if (r.a_blk >= 0) {
-          p->flops += 2 * r.dj * r.di * r.dk;
-        } else if (r.b_blk >= 0) {
-          p->flops += 2 * r.di * r.dk * r.dl;
-        }
-        p->records.push_back(r);
+        finish_record(p, r, &inter);
       }
     }
   }
   p->T_elems = (size_t)inter;
+}
 
+// l-1-1-r form (Eq. 13 with the blocks of the paragraph after it): one record per term,
+// block of l, site elements a[s1' <- s1], b[s2' <- s2] and block of r whose input
+// (i, s1, s2, k) and output (j, s1', s2', l) segments are in the sector, with coefficient
+// coef * a * b.  Left sectors are the tuples (i * q + s1) * q + s2.
+dmrg_status build_records_l11r(dmrg_plan* p, const dmrg_l11r_desc* d,
+                               const std::vector<int64_t>& diml) {
+  const int q = d->q;
+  const int npairs = (int)p->pair_i.size();
+  std::map<std::pair<int, int>, int> pidx;
+  for (int g = 0; g < npairs; ++g) pidx[{p->pair_i[g], p->pair_k[g]}] = g;
+  const int nl = d->nl, nR = (int)p->dimR.size();
+  std::vector<HostBlock> idl(nl), idR(nR);
+  for (int i = 0; i < nl; ++i) idl[i] = HostBlock{i, i, diml[i], diml[i], -1};
+  for (int k = 0; k < nR; ++k) idR[k] = HostBlock{k, k, p->dimR[k], p->dimR[k], -1};
+  struct Elem { int in, out; double v; };
+  auto site_elems = [&](int o) {
+    std::vector<Elem> e;
+    if (o == DMRG_IDENTITY_OP) {
+      for (int s = 0; s < q; ++s) e.push_back(Elem{s, s, 1.0});
+    } else {
+      const double* M = d->sops + (size_t)o * q * q;  // row-major [out][in]
+      for (int sin = 0; sin < q; ++sin)
+        for (int sout = 0; sout < q; ++sout)
+          if (M[(size_t)sout * q + sin] != 0.0) e.push_back(Elem{sin, sout, M[(size_t)sout * q + sin]});
+    }
+    return e;
+  };
+  p->records.clear();
+  p->flops = 0;
+  int64_t inter = 0;
+  for (int t = 0; t < d->nterms; ++t) {
+    const dmrg_term4& tm = d->terms[t];
+    const std::vector<HostBlock>& As = tm.l_op == DMRG_IDENTITY_OP ? idl : p->opsL[tm.l_op];
+    const std::vector<HostBlock>& Bs = tm.r_op == DMRG_IDENTITY_OP ? idR : p->opsR[tm.r_op];
+    const std::vector<Elem> e1 = site_elems(tm.s1_op), e2 = site_elems(tm.s2_op);
+    for (int ai = 0; ai < (int)As.size(); ++ai) {
+      for (int bi = 0; bi < (int)Bs.size(); ++bi) {
+        const HostBlock& A = As[ai];
+        const HostBlock& B = Bs[bi];
+        for (const Elem& u : e1) {
+          for (const Elem& v : e2) {
+            const int Iin = (A.idx_in * q + u.in) * q + v.in;
+            const int Iout = (A.idx_out * q + u.out) * q + v.out;
+            auto in = pidx.find({Iin, B.idx_in});
+            auto out = pidx.find({Iout, B.idx_out});
+            if (in == pidx.end() || out == pidx.end()) continue;
+            Record r{};
+            r.term = t;
+            r.a_blk = tm.l_op == DMRG_IDENTITY_OP ? -1 : ai;
+            r.b_blk = tm.r_op == DMRG_IDENTITY_OP ? -1 : bi;
+            r.pin = in->second;
+            r.pout = out->second;
+            r.i = Iin; r.j = Iout; r.k = B.idx_in; r.l = B.idx_out;
+            r.di = diml[A.idx_in]; r.dj = diml[A.idx_out];
+            r.dk = p->dimR[r.k]; r.dl = p->dimR[r.l];
+            r.coef = tm.coef * u.v * v.v;
+            finish_record(p, r, &inter);
+          }
+        }
+      }
+    }
+  }
+  p->T_elems = (size_t)inter;
+  return DMRG_OK;
+}
+
+// FP64 GEMM work lists from the records: stage-1 intermediates and stage-2 output jobs
+dmrg_status build_jobs(dmrg_plan* p, Builder* bld) {
+  const int npairs = (int)p->pair_i.size();
   auto A_of = [&](const Record& r) -> const HostBlock& {
     return p->opsL[p->terms[r.term].a_op][r.a_blk];
   };
@@ -287,7 +447,7 @@ dmrg_status build_records_and_jobs(dmrg_plan* p, Builder* bld) {
         s.Q = opnd(SP_ARENA, B.arena_off, 1, B.cols);
         s.K = (int32_t)r.dk;
       } else {                    // (1 (x) 1): Y += coef X
-        job.axpy += r.coef;
+        if (r.pin == r.pout) job.axpy += r.coef;  // (other segments: seg_axpy pass)
         continue;
       }
       if (s.K == 0) continue;
@@ -326,26 +486,28 @@ dmrg_status upload(T** dst, const std::vector<T>& src, size_t* bytes, cudaStream
 }
 
 // ---------------------------------------------------------------- diagonal of H_SB
-// D[off_p + a * dk + b] = sum_t coef_t diag(A_t,ii)[a] * diag(B_t,kk)[b] over the terms
-// whose factors have a diagonal-sector block (identity factors contribute 1).
+// D[off_p + a * dk + b] = sum over the records that map segment p to itself of
+// coef * diag(A)[a] * diag(B)[b] (such a record's blocks are diagonal-sector blocks;
+// identity factors contribute 1).  In the LR form these are the terms' diagonal blocks; in
+// the l-1-1-r form the coefficients carry the diagonal site elements.
 struct DiagEntry {
-  int64_t a_off, b_off;   // arena offsets of the diagonal blocks, -1 identity, -2 absent
+  int64_t a_off, b_off;   // arena offsets of the diagonal blocks, -1 identity
   int64_t a_ld, b_ld;
   double coef;
 };
 
 __global__ void diag_kernel(const double* __restrict__ arena, const DiagEntry* __restrict__ ent,
-                            int nterms, const int64_t* __restrict__ pair_off,
+                            const int32_t* __restrict__ ent_beg, const int64_t* __restrict__ pair_off,
                             const int64_t* __restrict__ pair_dk, double* __restrict__ D) {
   const int p = blockIdx.y;
   const int64_t off = pair_off[p], size = pair_off[p + 1] - off, dk = pair_dk[p];
+  const int e0 = ent_beg[p], e1 = ent_beg[p + 1];
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < size;
        e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t a = e / dk, b = e - a * dk;
     double acc = 0.0;
-    for (int t = 0; t < nterms; ++t) {
-      const DiagEntry& d = ent[(int64_t)p * nterms + t];
-      if (d.a_off == -2 || d.b_off == -2) continue;
+    for (int t = e0; t < e1; ++t) {
+      const DiagEntry& d = ent[t];
       const double da = d.a_off == -1 ? 1.0 : arena[d.a_off + a * (d.a_ld + 1)];
       const double db = d.b_off == -1 ? 1.0 : arena[d.b_off + b * (d.b_ld + 1)];
       acc = fma(d.coef * da, db, acc);
@@ -360,43 +522,47 @@ namespace dmrg {
 
 dmrg_status compute_diagonal(dmrg_plan* p, double* d, cudaStream_t st) {
   const int npairs = (int)p->pair_i.size();
-  const int nterms = (int)p->terms.size();
   if (npairs == 0 || p->n == 0) return DMRG_OK;
-  std::vector<DiagEntry> ent((size_t)npairs * std::max(nterms, 1));
-  for (int q = 0; q < npairs; ++q) {
-    int i = p->pair_i[q], k = p->pair_k[q];
-    for (int t = 0; t < nterms; ++t) {
-      DiagEntry e{-2, -2, 0, 0, p->terms[t].coef};
-      const dmrg_term& term = p->terms[t];
-      if (term.a_op == DMRG_IDENTITY_OP) {
-        e.a_off = -1;
-      } else {
-        for (auto& hb : p->opsL[term.a_op])
-          if (hb.idx_in == i && hb.idx_out == i) { e.a_off = hb.arena_off; e.a_ld = hb.cols; }
-      }
-      if (term.b_op == DMRG_IDENTITY_OP) {
-        e.b_off = -1;
-      } else {
-        for (auto& hb : p->opsR[term.b_op])
-          if (hb.idx_in == k && hb.idx_out == k) { e.b_off = hb.arena_off; e.b_ld = hb.cols; }
-      }
-      ent[(size_t)q * nterms + t] = e;
+  std::vector<std::vector<DiagEntry>> per(npairs);
+  for (const Record& r : p->records) {
+    if (r.pin != r.pout) continue;
+    DiagEntry e{-1, -1, 0, 0, r.coef};
+    if (r.a_blk >= 0) {
+      const HostBlock& hb = p->opsL[p->terms[r.term].a_op][r.a_blk];
+      e.a_off = hb.arena_off;
+      e.a_ld = hb.cols;
     }
+    if (r.b_blk >= 0) {
+      const HostBlock& hb = p->opsR[p->terms[r.term].b_op][r.b_blk];
+      e.b_off = hb.arena_off;
+      e.b_ld = hb.cols;
+    }
+    per[r.pin].push_back(e);
   }
+  std::vector<DiagEntry> ent;
+  std::vector<int32_t> beg(npairs + 1, 0);
+  for (int q = 0; q < npairs; ++q) {
+    ent.insert(ent.end(), per[q].begin(), per[q].end());
+    beg[q + 1] = (int32_t)ent.size();
+  }
+  if (ent.empty()) ent.push_back(DiagEntry{-1, -1, 0, 0, 0.0});  // (no record: D = 0)
   std::vector<int64_t> dk(npairs);
   for (int q = 0; q < npairs; ++q) dk[q] = p->dimR[p->pair_k[q]];
   DiagEntry* d_ent = nullptr;
+  int32_t* d_beg = nullptr;
   int64_t *d_off = nullptr, *d_dk = nullptr;
   size_t dummy = 0;
   DMRG_TRY(upload(&d_ent, ent, &dummy, st));
+  DMRG_TRY(upload(&d_beg, beg, &dummy, st));
   DMRG_TRY(upload(&d_off, p->pair_off, &dummy, st));
   DMRG_TRY(upload(&d_dk, dk, &dummy, st));
   dim3 grid(64, npairs);
-  diag_kernel<<<grid, 256, 0, st>>>(p->arena, d_ent, nterms, d_off, d_dk, d);
+  diag_kernel<<<grid, 256, 0, st>>>(p->arena, d_ent, d_beg, d_off, d_dk, d);
   note_launch();
   cudaError_t e = cudaGetLastError();
   cudaStreamSynchronize(st);
   cudaFree(d_ent);
+  cudaFree(d_beg);
   cudaFree(d_off);
   cudaFree(d_dk);
   if (e != cudaSuccess) {
@@ -406,17 +572,39 @@ dmrg_status compute_diagonal(dmrg_plan* p, double* d, cudaStream_t st) {
   return DMRG_OK;
 }
 
+template <typename T>
+__global__ void seg_axpy_kernel(const SegAxpyGroup* __restrict__ groups,
+                                const SegAxpyEntry* __restrict__ ent, const T* __restrict__ x,
+                                T* __restrict__ y) {
+  const SegAxpyGroup g = groups[blockIdx.y];
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < g.size;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    T acc = y[g.dst_off + e];
+    for (int t = g.beg; t < g.end; ++t) {
+      const SegAxpyEntry en = ent[t];
+      if constexpr (sizeof(T) == 8) acc = fma(en.coef, x[en.src_off + e], acc);
+      else acc = fmaf((float)en.coef, x[en.src_off + e], acc);
+    }
+    y[g.dst_off + e] = acc;
+  }
+}
+
+dmrg_status launch_seg_axpy(const dmrg_plan* p, const double* x, double* y, const float* x32,
+                            float* y32, cudaStream_t st) {
+  if (p->n_sax_groups == 0) return DMRG_OK;
+  const dim3 grid((unsigned)std::min<int64_t>(64, (p->sax_max_size + 255) / 256), (unsigned)p->n_sax_groups);
+  if (x32) seg_axpy_kernel<float><<<grid, 256, 0, st>>>(p->d_sax_groups, p->d_sax_entries, x32, y32);
+  else seg_axpy_kernel<double><<<grid, 256, 0, st>>>(p->d_sax_groups, p->d_sax_entries, x, y);
+  DMRG_LAUNCH_CHECK();
+  return DMRG_OK;
+}
+
 }  // namespace dmrg
 
-extern "C" {
+namespace {
 
-dmrg_status dmrg_plan_create(const dmrg_superblock_desc* desc, const dmrg_options* opt,
-                             void* stream, dmrg_plan** out) {
-  if (!out) {
-    set_error("out is NULL");
-    return DMRG_ERR_INVALID_ARG;
-  }
-  *out = nullptr;
+// a plan with validated options (defaults if opt is NULL)
+dmrg_status new_plan(const dmrg_options* opt, dmrg_plan** out) {
   dmrg_plan* p = new (std::nothrow) dmrg_plan();
   if (!p) {
     set_error("host allocation failed");
@@ -435,12 +623,16 @@ dmrg_status dmrg_plan_create(const dmrg_superblock_desc* desc, const dmrg_option
     delete p;
     return DMRG_ERR_INVALID_ARG;
   }
-  cudaStream_t st = (cudaStream_t)stream;
-  dmrg_status s = validate_and_copy(desc, p);
-  if (s != DMRG_OK) { delete p; return s; }
+  *out = p;
+  return DMRG_OK;
+}
+
+// FP64 work lists, device arena, intermediates and the diagonal of a plan whose records
+// exist; on failure the plan is destroyed
+dmrg_status finish_plan(dmrg_plan* p, cudaStream_t st, dmrg_plan** out) {
   cudaGetDevice(&p->device);
   Builder bld;
-  s = build_records_and_jobs(p, &bld);
+  dmrg_status s = build_jobs(p, &bld);
   if (s != DMRG_OK) { delete p; return s; }
   auto fail = [&](dmrg_status st_) { dmrg_plan_destroy(p); return st_; };
   if (p->arena_elems) {
@@ -469,6 +661,25 @@ dmrg_status dmrg_plan_create(const dmrg_superblock_desc* desc, const dmrg_option
   if ((s = upload(&p->d_tiles2, bld.tiles2, &p->device_bytes, st)) != DMRG_OK) return fail(s);
   p->ntiles1 = (int64_t)bld.tiles1.size();
   p->ntiles2 = (int64_t)bld.tiles2.size();
+  {
+    // cross-segment identity terms, grouped by output segment in record order
+    std::map<int, std::vector<SegAxpyEntry>> by_dst;
+    for (const Record& r : p->records)
+      if (r.a_blk < 0 && r.b_blk < 0 && r.pin != r.pout && r.coef != 0.0)
+        by_dst[r.pout].push_back(SegAxpyEntry{p->pair_off[r.pin], r.coef});
+    std::vector<SegAxpyGroup> groups;
+    std::vector<SegAxpyEntry> ent;
+    for (auto& kv : by_dst) {
+      const int64_t size = p->pair_off[kv.first + 1] - p->pair_off[kv.first];
+      groups.push_back(SegAxpyGroup{p->pair_off[kv.first], size, (int32_t)ent.size(),
+                                    (int32_t)(ent.size() + kv.second.size())});
+      ent.insert(ent.end(), kv.second.begin(), kv.second.end());
+      p->sax_max_size = std::max(p->sax_max_size, size);
+    }
+    if ((s = upload(&p->d_sax_groups, groups, &p->device_bytes, st)) != DMRG_OK) return fail(s);
+    if ((s = upload(&p->d_sax_entries, ent, &p->device_bytes, st)) != DMRG_OK) return fail(s);
+    p->n_sax_groups = (int32_t)groups.size();
+  }
   if (p->n > 0) {
     if (cudaMalloc((void**)&p->D, sizeof(double) * p->n) != cudaSuccess) {
       set_error("cudaMalloc for the diagonal failed");
@@ -485,6 +696,43 @@ dmrg_status dmrg_plan_create(const dmrg_superblock_desc* desc, const dmrg_option
   return DMRG_OK;
 }
 
+}  // namespace
+
+extern "C" {
+
+dmrg_status dmrg_plan_create(const dmrg_superblock_desc* desc, const dmrg_options* opt,
+                             void* stream, dmrg_plan** out) {
+  if (!out) {
+    set_error("out is NULL");
+    return DMRG_ERR_INVALID_ARG;
+  }
+  *out = nullptr;
+  dmrg_plan* p = nullptr;
+  DMRG_TRY(new_plan(opt, &p));
+  cudaStream_t st = (cudaStream_t)stream;
+  dmrg_status s = validate_and_copy(desc, p);
+  if (s != DMRG_OK) { delete p; return s; }
+  build_records_lr(p);
+  return finish_plan(p, st, out);
+}
+
+dmrg_status dmrg_plan_create_l11r(const dmrg_l11r_desc* desc, const dmrg_options* opt,
+                                  void* stream, dmrg_plan** out) {
+  if (!out) {
+    set_error("out is NULL");
+    return DMRG_ERR_INVALID_ARG;
+  }
+  *out = nullptr;
+  dmrg_plan* p = nullptr;
+  DMRG_TRY(new_plan(opt, &p));
+  cudaStream_t st = (cudaStream_t)stream;
+  std::vector<int64_t> diml;
+  dmrg_status s = validate_and_copy_l11r(desc, p, &diml);
+  if (s == DMRG_OK) s = build_records_l11r(p, desc, diml);
+  if (s != DMRG_OK) { delete p; return s; }
+  return finish_plan(p, st, out);
+}
+
 void dmrg_plan_destroy(dmrg_plan* p) {
   if (!p) return;
   destroy_tc(p);
@@ -496,6 +744,8 @@ void dmrg_plan_destroy(dmrg_plan* p) {
   cudaFree(p->d_segs);
   cudaFree(p->d_tiles1);
   cudaFree(p->d_tiles2);
+  cudaFree(p->d_sax_groups);
+  cudaFree(p->d_sax_entries);
   delete p;
 }
 

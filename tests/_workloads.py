@@ -16,6 +16,11 @@ def workload(name):
 
 
 @functools.lru_cache(maxsize=None)
+def workload_l11r(name):
+    return warmup.workload_l11r(name)
+
+
+@functools.lru_cache(maxsize=None)
 def superblock(model, L, m, **kw):
     return warmup.warmup_superblock(model, L, m, **kw)
 

@@ -133,7 +133,8 @@ def test_binding_structs_match_the_header(tmp_path):
     pairs = [(capi.Block, "dmrg_block"), (capi.Operator, "dmrg_operator"),
              (capi.Term, "dmrg_term"), (capi.SuperblockDesc, "dmrg_superblock_desc"),
              (capi.Options, "dmrg_options"), (capi.SolveInfo, "dmrg_solve_info"),
-             (capi.PlanStats, "dmrg_plan_stats")]
+             (capi.PlanStats, "dmrg_plan_stats"), (capi.Term4, "dmrg_term4"),
+             (capi.L11rDesc, "dmrg_l11r_desc")]
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "dmrg.h"', "int main(void) {",
              '  printf("%d\\n", (int)DMRG_TILE_SCHEDULES);']
     expect = [str(capi.TILE_SCHEDULES)]
