@@ -65,7 +65,17 @@ TF32_TFLOPS = 1006.0
 # stages, the split-K reduction when stage 2 splits), keyed by arithmetic and by the tile
 # schedules of the two GEMM stages the capture ran with; the traffic of a run whose
 # autotuner picked other schedules is not known and is reported as null
-TC_TRAFFIC = {("bf16x3", (6, 17)): 535.3e6}
+TC_TRAFFIC = {
+    ("bf16x3", (6, 17)): 535.3e6,
+    # BF16x2, captured with `bench.py --mode traffic --prec bf16x2 --scheds ...` under
+    # `ncu --metrics gpu__time_duration.sum,dram__bytes_read.sum,dram__bytes_write.sum`
+    ("bf16x2", (6, 6)): 306.6e6, ("bf16x2", (6, 7)): 305.8e6, ("bf16x2", (6, 8)): 305.8e6,
+    ("bf16x2", (6, 15)): 412.2e6, ("bf16x2", (6, 16)): 361.5e6, ("bf16x2", (6, 17)): 360.7e6,
+    ("bf16x2", (7, 6)): 303.8e6, ("bf16x2", (7, 7)): 302.9e6, ("bf16x2", (7, 8)): 303.4e6,
+    ("bf16x2", (7, 15)): 408.5e6, ("bf16x2", (7, 16)): 358.9e6, ("bf16x2", (7, 17)): 358.6e6,
+    ("bf16x2", (8, 6)): 304.2e6, ("bf16x2", (8, 7)): 303.6e6, ("bf16x2", (8, 8)): 304.3e6,
+    ("bf16x2", (8, 15)): 409.0e6, ("bf16x2", (8, 16)): 360.4e6, ("bf16x2", (8, 17)): 359.7e6,
+}
 
 
 class ClockSampler:
@@ -267,6 +277,40 @@ def run_project(args):
                       "tc_schedule": plan.get_stats()["tc_schedule"]}), flush=True)
 
 
+def run_traffic(args):
+    """One projection per listed tile schedule, each alone inside the CUDA profiler range,
+    for `ncu --profile-from-start off --metrics dram__bytes_read.sum,dram__bytes_write.sum`:
+    the DRAM traffic of the projection's launches under each schedule (the source of the
+    TC_TRAFFIC table).  Prints the schedules in capture order."""
+    import torch
+    torch.cuda.set_device(0)
+    import __graft_entry__
+    __graft_entry__.build()
+    from dmrg_inputs import warmup
+    from paper_1309_5571_gb300 import Plan
+    prec = "bf16x2" if args.prec == "auto" else args.prec
+    sb = warmup.workload(args.workload)
+    x = torch.from_numpy(warmup.start_vector(sb.n, 0)).cuda()
+    y = torch.empty_like(x)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    plan = Plan(sb, prec=prec, graphs=False)
+    order = []
+    for spec in args.scheds.split(":"):
+        s1, s2 = (int(v) for v in spec.split(","))
+        plan.set_tile_schedule(s1, s2, prec=prec)
+        for _ in range(2):
+            plan.project(x, y, prec=prec)
+        flush.zero_()
+        torch.cuda.synchronize()
+        torch.cuda.profiler.start()
+        plan.project(x, y, prec=prec)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
+        order.append([s1, s2])
+    print(json.dumps({"mode": "traffic", "workload": args.workload, "prec": prec,
+                      "schedules_in_capture_order": order}), flush=True)
+
+
 def run_batched(args):
     """Uneven batch of independent Heisenberg superblocks (L = 100, m drawn from
     {256, 512, 1024, 2048} with seed 1234): one batched solve versus the same solves one
@@ -317,7 +361,9 @@ def main():
     ap.add_argument("--no-l11r", action="store_true",
                     help="skip the l-1-1-r form of the workload in the solve report")
     ap.add_argument("--proj-reps", type=int, default=10)
-    ap.add_argument("--mode", default="solve", choices=["solve", "project", "peaks", "batched"])
+    ap.add_argument("--mode", default="solve", choices=["solve", "project", "peaks", "batched", "traffic"])
+    ap.add_argument("--scheds", default="6,7:6,16:8,7:8,16:7,6:6,8:6,6:7,7:8,8",
+                    help="--mode traffic: tile schedules 'S1,S2:S1,S2:...'")
     ap.add_argument("--batch", type=int, default=64)
     ap.add_argument("--anchor", default="fp64tc", choices=["fp64", "fp64tc"],
                     help="FP64-accurate projections of the mixed modes")
@@ -336,6 +382,8 @@ def main():
         return run_project(args)
     if args.mode == "batched":
         return run_batched(args)
+    if args.mode == "traffic":
+        return run_traffic(args)
 
     import numpy as np
     import torch
@@ -406,12 +454,23 @@ def main():
     proj_per_step = statistics.mean(i["projections"] + i["fp64_projections"] for i in infos)
     value = job_throughput(proj_per_step * flops, ws, t_step) / 1e12
 
-    # ---- end to end through the host-buffer entry point (copies inside the timing)
-    torch.cuda.synchronize()
+    # ---- end to end through the host-buffer entry point: every step copies its start
+    # vector from pinned host memory to the device and the result back inside the timing
+    # (the same K steps and start vectors as above; one untimed call first)
+    xh_in = [torch.empty(sb.n, dtype=torch.float64).pin_memory() for _ in x0s_t]
+    for h, d in zip(xh_in, x0s_t):
+        h.copy_(d.cpu())
+    xh_out = torch.empty(sb.n, dtype=torch.float64).pin_memory()
+    plan.solve_host(xh_in[0].numpy(), xh_out.numpy())
+    barrier()
     te = time.perf_counter()
-    xh, infoh = plan.solve_host(x0)
-    t_e2e = time.perf_counter() - te
-    e2e_val = (infoh["projections"] + infoh["fp64_projections"]) * flops / t_e2e / 1e12
+    e2e_proj = 0
+    for s in range(args.steps):
+        _, infoh = plan.solve_host(xh_in[s % len(xh_in)].numpy(), xh_out.numpy())
+        e2e_proj += infoh["projections"] + infoh["fp64_projections"]
+    barrier()
+    t_e2e = max_over_ranks((time.perf_counter() - te) / args.steps, device="cuda")
+    e2e_val = job_throughput(e2e_proj / args.steps * flops, ws, t_e2e) / 1e12
 
     # ---- the dominant kernel: the projection (all its launches), timed alone in every
     # arithmetic, L2 flushed before each
@@ -582,7 +641,8 @@ def main():
             "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_val, "unit": "TFLOP/s", "h2d_bytes_per_step": 8 * sb.n,
-                    "d2h_bytes_per_step": 8 * sb.n, "ms": t_e2e * 1e3},
+                    "d2h_bytes_per_step": 8 * sb.n, "ms": t_e2e * 1e3,
+                    "host_buffers": "pinned", "steps": args.steps},
             "clocks": clk.summary(),
             "gpu_launches": launches,
         }

@@ -263,7 +263,17 @@ dmrg_status dmrg_plan_create(const dmrg_superblock_desc* desc, const dmrg_option
  * error rules as dmrg_plan_create. */
 dmrg_status dmrg_plan_create_l11r(const dmrg_l11r_desc* desc, const dmrg_options* opt,
                                   void* stream, dmrg_plan** out);
+/* Frees the plan and everything it owns (the buffers kept by dmrg_plan_trim included). */
 void dmrg_plan_destroy(dmrg_plan* plan);
+/* A finished Davidson state (dmrg_state_destroy, and so the end of every solve) leaves its
+ * device and pinned buffers with its plan, and the next state of the same shape takes them
+ * over; dmrg_davidson_solve_host keeps its two device vectors the same way.  Repeated
+ * solves on one plan therefore allocate nothing after the first.  The kept workspace is
+ * (2 max_subspace + 6) n doubles for FP64 solves and about half of that for mixed solves
+ * with split vector arithmetic.  This call frees all of it now (the plan stays usable;
+ * the next solve allocates again); a state that is running holds its own buffers and is
+ * not affected.  DMRG_ERR_INVALID_ARG for a NULL plan. */
+dmrg_status dmrg_plan_trim(dmrg_plan* plan);
 dmrg_status dmrg_plan_get_stats(const dmrg_plan* plan, dmrg_plan_stats* stats);
 
 /* Tile-schedule autotuner of the tensor-core projection (prec DMRG_PREC_TF32,
@@ -319,6 +329,8 @@ dmrg_status dmrg_gemv_trans_noalloc(const double* V, int64_t ldv, int64_t n, int
  * from x0 (device, n float64, normalised by the call). */
 dmrg_status dmrg_state_create(dmrg_plan* plan, const double* x0, void* stream,
                               dmrg_davidson_state** out);
+/* Waits for the device to finish (as a cudaFree would) and hands the state's buffers to
+ * its plan for the next state (dmrg_plan_trim frees them). */
 void dmrg_state_destroy(dmrg_davidson_state* st);
 /* One iteration of Algorithm 3.  Synchronises the stream; *converged is set to 1 when
  * the residual of the current Ritz pair is below tol. */

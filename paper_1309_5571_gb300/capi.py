@@ -118,6 +118,7 @@ SIGNATURES = {
     "dmrg_plan_create_l11r": (C.c_int, [C.POINTER(L11rDesc), C.POINTER(Options), C.c_void_p,
                                         C.POINTER(C.c_void_p)]),
     "dmrg_plan_destroy": (None, [C.c_void_p]),
+    "dmrg_plan_trim": (C.c_int, [C.c_void_p]),
     "dmrg_plan_get_stats": (C.c_int, [C.c_void_p, C.POINTER(PlanStats)]),
     "dmrg_plan_autotune": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
     "dmrg_plan_set_tile_schedule": (C.c_int, [C.c_void_p, C.c_int, C.c_int32, C.c_int32, C.c_void_p]),
@@ -336,6 +337,11 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+    def trim(self):
+        """dmrg_plan_trim: free the Davidson workspace and host-solve vectors kept between
+        solves."""
+        _check(self.lib.dmrg_plan_trim(self.handle))
 
     def get_stats(self):
         st = PlanStats()

@@ -73,6 +73,7 @@ struct dmrg_davidson_state {
   int knew = 1;             // basis size after a restart decided in phase_b
   bool did_restart = false;
   bool proj_fp64 = false;   // this iteration's projection is FP64-accurate
+  bool ws_complete = false; // every workspace buffer was allocated (it may go to the plan)
 };
 
 namespace {
@@ -177,6 +178,28 @@ dmrg_status project_col(dmrg_davidson_state* s, int col, bool fp64, cudaStream_t
 
 }  // namespace
 
+namespace dmrg {
+
+void workspace_free(SolveWorkspace* w) {
+  if (!w) return;
+  cudaFree(w->V);
+  cudaFree(w->W);
+  cudaFree(w->V32);
+  cudaFree(w->W32);
+  cudaFree(w->tbuf);
+  cudaFree(w->D);
+  cudaFree(w->xbuf);
+  cudaFree(w->wbuf);
+  cudaFree(w->pbuf);
+  cudaFree(w->wpbuf);
+  cudaFree(w->small);
+  cudaFreeHost(w->hsmall);
+  vec_work_destroy(&w->vw);
+  delete w;
+}
+
+}  // namespace dmrg
+
 extern "C" {
 
 dmrg_status dmrg_state_create(dmrg_plan* plan, const double* x0, void* stream,
@@ -207,25 +230,54 @@ dmrg_status dmrg_state_create(dmrg_plan* plan, const double* x0, void* stream,
   const size_t col = sizeof(double) * (size_t)s->ldv;
   const size_t col32 = sizeof(float) * (size_t)s->ldv;
   const int cV = s->f32 ? 1 : s->kmax + 1, cW = s->f32 ? 1 : s->kmax;
-  if (cudaMalloc((void**)&s->V, col * cV) != cudaSuccess ||
-      cudaMalloc((void**)&s->W, col * cW) != cudaSuccess ||
-      (s->f32 && (cudaMalloc((void**)&s->V32, col32 * (s->kmax + 1)) != cudaSuccess ||
-                  cudaMalloc((void**)&s->W32, col32 * s->kmax) != cudaSuccess ||
-                  cudaMalloc((void**)&s->tbuf, col) != cudaSuccess)) ||
-      cudaMalloc((void**)&s->D, col) != cudaSuccess ||
-      cudaMalloc((void**)&s->xbuf, col) != cudaSuccess ||
-      cudaMalloc((void**)&s->wbuf, col) != cudaSuccess ||
-      (plan->opt.restart_keep == 2 && (cudaMalloc((void**)&s->pbuf, col) != cudaSuccess ||
-                                       cudaMalloc((void**)&s->wpbuf, col) != cudaSuccess)) ||
-      cudaMalloc((void**)&s->small, sizeof(DevSmall)) != cudaSuccess ||
-      cudaMallocHost((void**)&s->hsmall, sizeof(DevSmall)) != cudaSuccess) {
-    cudaGetLastError();
-    set_error("allocation of the Davidson workspace (%zu bytes) failed",
-              col * (2 * s->kmax + 6));
-    return fail(DMRG_ERR_OOM);
+  const bool keep2 = plan->opt.restart_keep == 2;
+  dmrg::SolveWorkspace* cached = nullptr;
+  {
+    std::lock_guard<std::mutex> g(plan->ws_mu);
+    cached = plan->ws_cache;
+    plan->ws_cache = nullptr;
   }
-  dmrg_status e = vec_work_create(&s->vw);
-  if (e != DMRG_OK) return fail(e);
+  if (cached && cached->ldv == s->ldv && cached->kmax == s->kmax && cached->f32 == s->f32 &&
+      cached->keep2 == keep2) {
+    // the previous state's buffers, same shape: no allocation
+    s->V = cached->V;
+    s->W = cached->W;
+    s->V32 = cached->V32;
+    s->W32 = cached->W32;
+    s->tbuf = cached->tbuf;
+    s->D = cached->D;
+    s->xbuf = cached->xbuf;
+    s->wbuf = cached->wbuf;
+    s->pbuf = cached->pbuf;
+    s->wpbuf = cached->wpbuf;
+    s->small = cached->small;
+    s->hsmall = cached->hsmall;
+    s->vw = cached->vw;
+    delete cached;
+  } else {
+    dmrg::workspace_free(cached);
+    if (cudaMalloc((void**)&s->V, col * cV) != cudaSuccess ||
+        cudaMalloc((void**)&s->W, col * cW) != cudaSuccess ||
+        (s->f32 && (cudaMalloc((void**)&s->V32, col32 * (s->kmax + 1)) != cudaSuccess ||
+                    cudaMalloc((void**)&s->W32, col32 * s->kmax) != cudaSuccess ||
+                    cudaMalloc((void**)&s->tbuf, col) != cudaSuccess)) ||
+        cudaMalloc((void**)&s->D, col) != cudaSuccess ||
+        cudaMalloc((void**)&s->xbuf, col) != cudaSuccess ||
+        cudaMalloc((void**)&s->wbuf, col) != cudaSuccess ||
+        (keep2 && (cudaMalloc((void**)&s->pbuf, col) != cudaSuccess ||
+                   cudaMalloc((void**)&s->wpbuf, col) != cudaSuccess)) ||
+        cudaMalloc((void**)&s->small, sizeof(DevSmall)) != cudaSuccess ||
+        cudaMallocHost((void**)&s->hsmall, sizeof(DevSmall)) != cudaSuccess) {
+      cudaGetLastError();
+      set_error("allocation of the Davidson workspace (%zu bytes) failed",
+                col * (2 * s->kmax + 6));
+      return fail(DMRG_ERR_OOM);
+    }
+    const dmrg_status ev = vec_work_create(&s->vw);
+    if (ev != DMRG_OK) return fail(ev);
+  }
+  s->ws_complete = true;
+  dmrg_status e = DMRG_OK;
   if (cudaMemsetAsync(s->V, 0, col * cV, st) != cudaSuccess ||
       cudaMemsetAsync(s->W, 0, col * cW, st) != cudaSuccess ||
       (s->f32 && (cudaMemsetAsync(s->V32, 0, col32 * (s->kmax + 1), st) != cudaSuccess ||
@@ -253,6 +305,39 @@ dmrg_status dmrg_state_create(dmrg_plan* plan, const double* x0, void* stream,
 
 void dmrg_state_destroy(dmrg_davidson_state* s) {
   if (!s) return;
+  if (s->ws_complete && s->plan) {
+    // hand the buffers to the plan for the next state, once no kernel uses them (the
+    // device-wide wait is the one a cudaFree would make)
+    auto* w = new (std::nothrow) dmrg::SolveWorkspace();
+    if (w && cudaDeviceSynchronize() == cudaSuccess) {
+      w->ldv = s->ldv;
+      w->kmax = s->kmax;
+      w->f32 = s->f32;
+      w->keep2 = s->plan->opt.restart_keep == 2;
+      w->V = s->V;
+      w->W = s->W;
+      w->V32 = s->V32;
+      w->W32 = s->W32;
+      w->tbuf = s->tbuf;
+      w->D = s->D;
+      w->xbuf = s->xbuf;
+      w->wbuf = s->wbuf;
+      w->pbuf = s->pbuf;
+      w->wpbuf = s->wpbuf;
+      w->small = s->small;
+      w->hsmall = s->hsmall;
+      w->vw = s->vw;
+      {
+        std::lock_guard<std::mutex> g(s->plan->ws_mu);
+        std::swap(w, s->plan->ws_cache);
+      }
+      dmrg::workspace_free(w);  // the workspace this one displaced, if any
+      delete s;
+      return;
+    }
+    cudaGetLastError();
+    delete w;
+  }
   cudaFree(s->V);
   cudaFree(s->W);
   cudaFree(s->V32);
@@ -615,9 +700,18 @@ dmrg_status dmrg_davidson_solve_host(dmrg_plan* plan, const double* x0_host,
   }
   cudaStream_t st = (cudaStream_t)stream;
   double *dx0 = nullptr, *dx = nullptr;
+  {
+    // the device vectors of the previous call, if no other call holds them
+    std::lock_guard<std::mutex> g(plan->ws_mu);
+    std::swap(dx0, plan->io_x0);
+    std::swap(dx, plan->io_x);
+  }
   const size_t bytes = sizeof(double) * (size_t)plan->n;
-  if (cudaMalloc((void**)&dx0, bytes) != cudaSuccess || cudaMalloc((void**)&dx, bytes) != cudaSuccess) {
+  if ((!dx0 && cudaMalloc((void**)&dx0, bytes) != cudaSuccess) ||
+      (!dx && cudaMalloc((void**)&dx, bytes) != cudaSuccess)) {
+    cudaGetLastError();
     cudaFree(dx0);
+    cudaFree(dx);
     set_error("allocation of the solve vectors failed");
     return DMRG_ERR_OOM;
   }
@@ -627,16 +721,47 @@ dmrg_status dmrg_davidson_solve_host(dmrg_plan* plan, const double* x0_host,
     e = DMRG_ERR_CUDA;
   }
   if (e == DMRG_OK) e = dmrg_davidson_solve(plan, dx0, dx, info, stream);
+  bool idle = false;
   if (e == DMRG_OK || e == DMRG_ERR_NOT_CONVERGED) {
     if (cudaMemcpyAsync(x_out_host, dx, bytes, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess) {
       set_error("device-to-host copy of x failed");
       e = DMRG_ERR_CUDA;
+    } else {
+      idle = true;
+    }
+  }
+  if (idle) {
+    // nothing of this call is in flight: the vectors go back to the plan
+    std::lock_guard<std::mutex> g(plan->ws_mu);
+    if (!plan->io_x0 && !plan->io_x) {
+      plan->io_x0 = dx0;
+      plan->io_x = dx;
+      dx0 = dx = nullptr;
     }
   }
   cudaFree(dx0);
   cudaFree(dx);
   return e;
+}
+
+dmrg_status dmrg_plan_trim(dmrg_plan* plan) {
+  if (!plan) {
+    set_error("NULL plan");
+    return DMRG_ERR_INVALID_ARG;
+  }
+  dmrg::SolveWorkspace* w = nullptr;
+  double *a = nullptr, *b = nullptr;
+  {
+    std::lock_guard<std::mutex> g(plan->ws_mu);
+    std::swap(w, plan->ws_cache);
+    std::swap(a, plan->io_x0);
+    std::swap(b, plan->io_x);
+  }
+  dmrg::workspace_free(w);
+  cudaFree(a);
+  cudaFree(b);
+  return DMRG_OK;
 }
 
 dmrg_status dmrg_gemv_trans(const double* V, int64_t ldv, int64_t n, int32_t k,

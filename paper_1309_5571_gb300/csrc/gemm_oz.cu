@@ -18,11 +18,12 @@
 // FP64, re-split for stage 2), operand tiles pre-swizzled into the 128-byte K-major
 // layout and moved by single bulk copies.
 //
-// Tile: 128 output rows (M of the MMA) x 64 columns (N), one shared-memory stage of one
-// K tile (7 digit planes of A: 112 KB; of B: 56 KB), 7 accumulators x 64 TMEM columns.
-// Warp roles: warp 0 copies, warp 1 issues tcgen05.mma, warps 2-9 drain and accumulate
-// (warp w reads TMEM lanes 32 (w % 4) .. + 31, columns 32 ((w - 2) / 4) .. + 31).  All
-// waits are bounded (2 s).
+// Tile: 128 output rows (M of the MMA) x 64 columns (N); K tiles of 32 elements in the
+// 64-byte swizzled K-major layout, two shared-memory stages of one K tile each (7 digit
+// planes of A: 56 KB; of B: 28 KB), so that the copies of one K tile overlap the 56 MMAs of
+// the previous one; 7 accumulators x 64 TMEM columns.  Warp roles: warp 0 copies, warp 1
+// issues tcgen05.mma, warps 2-9 drain and accumulate (warp w reads TMEM lanes
+// 32 (w % 4) .. + 31, columns 32 ((w - 2) / 4) .. + 31).  All waits are bounded (2 s).
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -89,14 +90,19 @@ struct OzPlan {
 namespace tc {
 #include "tc_ptx.cuh"
 
+using OzL = Layout<false>;                 // 32-element K tiles, 64-byte rows and swizzle
 constexpr int S = 7;                       // digits per operand element
 constexpr int kN = 64;                     // output columns per tile
-constexpr int kChunkKT = 4;                // K tiles (of 64) per exponent chunk
-constexpr int kOzThreads = 320;              // 2 + 8 warps
+constexpr int kKT = OzL::KT;               // elements per K tile
+constexpr int kPlane = OzL::CHUNK;         // bytes of one digit plane of one image tile
+constexpr int kChunkKT = 256 / kKT;        // K tiles per exponent chunk (256 elements)
+constexpr int kOzStages = 2;
+constexpr int kOzThreads = 320;            // 2 + 8 warps
 constexpr int kOzTmemCols = 512;           // S accumulators x 64 columns (448) -> 512
-constexpr uint32_t kStageA = S * kChunk;   // 7 planes x 128 rows x 128 bytes
-constexpr uint32_t kStageB = S * kChunk / 2;  // 7 planes x 64 rows x 128 bytes
-constexpr size_t kOzSmem = kStageA + kStageB + 1024;
+constexpr uint32_t kStageA = S * kPlane;   // 7 planes x 128 rows x 64 bytes
+constexpr uint32_t kStageB = S * kPlane / 2;  // 7 planes x 64 rows x 64 bytes
+constexpr uint32_t kStage = kStageA + kStageB;
+constexpr size_t kOzSmem = kOzStages * kStage + 1024;
 
 // ---------------------------------------------------------------- digit split
 // |x| = M 2^(be - 1075); with E = be_max - 1021 (so |x| 2^-E < 1/2),
@@ -140,7 +146,7 @@ oz_slice_kernel(const OzSliceItem* __restrict__ items, const OzSlice* __restrict
   const double* src = (jb.src_space == 0 ? arena : jb.src_space == 1 ? x : inter) + jb.src_off;
   const int kt0 = it.ch * kChunkKT;
   const int kt1 = min(kt0 + kChunkKT, jb.nkt);
-  const int k0 = kt0 * 64, k1 = min(kt1 * 64, jb.K);
+  const int k0 = kt0 * kKT, k1 = min(kt1 * kKT, jb.K);
   const bool scaled = jb.scale != 1.0;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   // pass 1: largest binary exponent of each row over the chunk
@@ -164,18 +170,19 @@ oz_slice_kernel(const OzSliceItem* __restrict__ items, const OzSlice* __restrict
   }
   __syncthreads();
   // pass 2: digit planes, one 16-byte group (8 elements) of one row per item
+  constexpr int G = OzL::GROUPS;
   const bool kfast = jb.cs == 1;
-  const int ngroups = (kt1 - kt0) * 8;
+  const int ngroups = (kt1 - kt0) * G;
   for (int idx = threadIdx.x; idx < kRows * ngroups; idx += blockDim.x) {
     int r, gg;
     if (kfast) { gg = idx % ngroups; r = idx / ngroups; }
     else { r = idx % kRows; gg = idx / kRows; }
-    const int kt = kt0 + gg / 8, g = gg % 8;
+    const int kt = kt0 + gg / G, g = gg % G;
     const int64_t grow = (int64_t)it.rt * kRows + r;
     int dig[8][S];
 #pragma unroll
     for (int e = 0; e < 8; ++e) {
-      const int k = kt * 64 + g * 8 + e;
+      const int k = kt * kKT + g * 8 + e;
       double v = 0.0;
       if (grow < jb.R && k < jb.K) {
         v = src[grow * jb.rs + (int64_t)k * jb.cs];
@@ -183,7 +190,7 @@ oz_slice_kernel(const OzSliceItem* __restrict__ items, const OzSlice* __restrict
       }
       split_digits(v, bemax[r], dig[e]);
     }
-    uint8_t* base = img + jb.dst_off + ((int64_t)it.rt * jb.nkt + kt) * S * kChunk + swz(r, g);
+    uint8_t* base = img + jb.dst_off + ((int64_t)it.rt * jb.nkt + kt) * S * kPlane + OzL::off(r, g);
 #pragma unroll
     for (int s = 0; s < S; ++s) {
       uint4 q;
@@ -191,7 +198,7 @@ oz_slice_kernel(const OzSliceItem* __restrict__ items, const OzSlice* __restrict
       q.y = pack2_bf16(__float2bfloat16_rn((float)dig[2][s]), __float2bfloat16_rn((float)dig[3][s]));
       q.z = pack2_bf16(__float2bfloat16_rn((float)dig[4][s]), __float2bfloat16_rn((float)dig[5][s]));
       q.w = pack2_bf16(__float2bfloat16_rn((float)dig[6][s]), __float2bfloat16_rn((float)dig[7][s]));
-      *reinterpret_cast<uint4*>(base + s * kChunk) = q;
+      *reinterpret_cast<uint4*>(base + s * kPlane) = q;
     }
   }
 }
@@ -204,6 +211,31 @@ __device__ __forceinline__ float pow2f(int e) {
 }
 
 // ---------------------------------------------------------------- grouped GEMM
+// The MMAs of one K tile: the 28 digit pairs (s, u) with s + u <= S - 1, each into the
+// accumulator of its scale group g = s + u, for both 16-element K steps.  The K step is
+// the outermost loop and u the innermost, so consecutive MMAs write different
+// accumulators; the descriptors are the stage's base descriptors plus constant offsets
+// (in 16-byte units; every address stays below 256 KB, so the 14-bit address field does
+// not carry).  FIRST: the first K tile of an exponent chunk, in which the first MMA of each
+// group (s = 0, first K step) overwrites its accumulator.
+template <bool FIRST>
+__device__ __forceinline__ void issue_ktile(uint32_t tmem_base, uint64_t ad0, uint64_t bd0) {
+  constexpr uint32_t idesc = instr_desc<false, kN>();
+#pragma unroll
+  for (int kk = 0; kk < OzL::ROWB / 32; ++kk) {
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+#pragma unroll
+      for (int u = 0; u < S - s; ++u) {
+        const uint64_t ad = ad0 + (uint64_t)((s * kPlane + kk * 32) >> 4);
+        const uint64_t bd = bd0 + (uint64_t)((u * (kPlane / 2) + kk * 32) >> 4);
+        mma<false>(tmem_base + (uint32_t)((s + u) * kN), ad, bd, idesc,
+                   (FIRST && kk == 0 && s == 0) ? 0u : 1u);
+      }
+    }
+  }
+}
+
 __global__ void __launch_bounds__(kOzThreads, 1)
 oz_gemm_kernel(const OzTile* __restrict__ tiles, int ntiles, const OzJob* __restrict__ jobs,
                const OzSeg* __restrict__ segs, const uint8_t* __restrict__ b0,
@@ -214,13 +246,16 @@ oz_gemm_kernel(const OzTile* __restrict__ tiles, int ntiles, const OzJob* __rest
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
-  __shared__ __align__(8) uint64_t full_bar, empty_bar, tfull_bar, tempty_bar, drain_bar;
+  __shared__ __align__(8) uint64_t full_bar[kOzStages], empty_bar[kOzStages];
+  __shared__ __align__(8) uint64_t tfull_bar, tempty_bar, drain_bar;
   __shared__ uint32_t tmem_slot;
   __shared__ volatile int abort_flag;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
-    mbar_init(smem_u32(&full_bar), 1);
-    mbar_init(smem_u32(&empty_bar), 1);
+    for (int i = 0; i < kOzStages; ++i) {
+      mbar_init(smem_u32(&full_bar[i]), 1);
+      mbar_init(smem_u32(&empty_bar[i]), 1);
+    }
     mbar_init(smem_u32(&tfull_bar), 1);
     mbar_init(smem_u32(&tempty_bar), 256);
     mbar_init(smem_u32(&drain_bar), 1);
@@ -242,10 +277,11 @@ oz_gemm_kernel(const OzTile* __restrict__ tiles, int ntiles, const OzJob* __rest
   const int32_t* exs[3] = {e0, e1, e2};
 
   if (warp == 0) {
-    // ------------------------------------------------ producer (one stage)
+    // ------------------------------------------------ producer (kOzStages-deep ring)
     if (lane == 0) {
+      int stage = 0;
       uint32_t phase = 0;
-      bool pending = false;
+      int issued = 0;
       for (int t = blockIdx.x; t < ntiles && !abort_flag; t += gridDim.x) {
         const OzTile tile = tiles[t];
         const OzJob job = jobs[tile.job];
@@ -253,35 +289,39 @@ oz_gemm_kernel(const OzTile* __restrict__ tiles, int ntiles, const OzJob* __rest
           const OzSeg sg = segs[si];
           const uint8_t* P = imgs[sg.p_buf] + sg.p_off + (int64_t)tile.mt * sg.p_nkt * kStageA;
           const uint8_t* Q = imgs[sg.q_buf] + sg.q_off + (int64_t)(tile.nt >> 1) * sg.q_nkt * kStageA +
-                             (tile.nt & 1) * (kChunk / 2);
+                             (tile.nt & 1) * (kPlane / 2);
           for (int kt = 0; kt < sg.nkt; ++kt) {
-            if (!mbar_wait(smem_u32(&empty_bar), phase ^ 1, &abort_flag, gerr, 11)) break;
-            const uint32_t sa = smem_u32(smem);
-            const uint32_t fb = smem_u32(&full_bar);
-            mbar_expect_tx(fb, kStageA + kStageB);
+            if (!mbar_wait(smem_u32(&empty_bar[stage]), phase ^ 1, &abort_flag, gerr, 11)) break;
+            const uint32_t sa = smem_u32(smem + stage * kStage);
+            const uint32_t fb = smem_u32(&full_bar[stage]);
+            mbar_expect_tx(fb, kStage);
             bulk_g2s(sa, P + (int64_t)kt * kStageA, kStageA, fb);
             const uint8_t* qk = Q + (int64_t)kt * kStageA;
 #pragma unroll
             for (int pl = 0; pl < S; ++pl)
-              bulk_g2s(sa + kStageA + pl * (kChunk / 2), qk + pl * kChunk, kChunk / 2, fb);
-            pending = true;
-            phase ^= 1;
+              bulk_g2s(sa + kStageA + pl * (kPlane / 2), qk + pl * kPlane, kPlane / 2, fb);
+            ++issued;
+            if (++stage == kOzStages) { stage = 0; phase ^= 1; }
           }
         }
       }
-      if (abort_flag && pending) {
-        const uint64_t t0 = gtime();
-        while (!mbar_try_wait(smem_u32(&full_bar), phase ^ 1) && gtime() - t0 < kWaitNs) {}
+      if (abort_flag) {
+        // the copies still in flight complete before the CTA exits (bounded)
+        int st = stage;
+        uint32_t ph = phase;
+        for (int i = 0; i < kOzStages && i < issued; ++i) {
+          if (--st < 0) { st = kOzStages - 1; ph ^= 1; }
+          const uint64_t t0 = gtime();
+          while (!mbar_try_wait(smem_u32(&full_bar[st]), ph) && gtime() - t0 < kWaitNs) {}
+        }
       }
     }
   } else if (warp == 1) {
     // ------------------------------------------------ MMA issuer
     if (lane == 0) {
+      int stage = 0;
       uint32_t phase = 0, acc_phase = 0;
       bool any = false;
-      constexpr uint32_t idesc = instr_desc<false, kN>();
-      const uint32_t sa = smem_u32(smem);
-      const uint32_t sb = sa + kStageA;
       for (int t = blockIdx.x; t < ntiles && !abort_flag; t += gridDim.x) {
         const OzJob job = jobs[tiles[t].job];
         for (int si = job.seg_begin; si < job.seg_end && !abort_flag; ++si) {
@@ -289,30 +329,17 @@ oz_gemm_kernel(const OzTile* __restrict__ tiles, int ntiles, const OzJob* __rest
           for (int c0 = 0; c0 < nkt && !abort_flag; c0 += kChunkKT) {
             if (!mbar_wait(smem_u32(&tempty_bar), acc_phase ^ 1, &abort_flag, gerr, 12)) break;
             tc_fence_after();
-            uint32_t started = 0;
             const int c1 = min(c0 + kChunkKT, nkt);
             for (int kt = c0; kt < c1; ++kt) {
-              if (!mbar_wait(smem_u32(&full_bar), phase, &abort_flag, gerr, 13)) break;
+              if (!mbar_wait(smem_u32(&full_bar[stage]), phase, &abort_flag, gerr, 13)) break;
               tc_fence_after();
-#pragma unroll
-              for (int s = 0; s < S; ++s) {
-#pragma unroll
-                for (int u = 0; u < S; ++u) {
-                  if (s + u > S - 1) continue;          // keep digit pairs with s+t <= S+1
-                  const int g = s + u;                  // scale group
-                  const uint32_t d_tmem = tmem_base + (uint32_t)(g * kN);
-#pragma unroll
-                  for (int kk = 0; kk < 4; ++kk) {
-                    const uint64_t ad = smem_desc(sa + s * kChunk + kk * 32);
-                    const uint64_t bd = smem_desc(sb + u * (kChunk / 2) + kk * 32);
-                    mma<false>(d_tmem, ad, bd, idesc, (started >> g) & 1u);
-                    started |= 1u << g;
-                  }
-                }
-              }
-              tc_commit(smem_u32(&empty_bar));
+              const uint32_t sa = smem_u32(smem + stage * kStage);
+              const uint64_t ad0 = OzL::desc(sa), bd0 = OzL::desc(sa + kStageA);
+              if (kt == c0) issue_ktile<true>(tmem_base, ad0, bd0);
+              else issue_ktile<false>(tmem_base, ad0, bd0);
+              tc_commit(smem_u32(&empty_bar[stage]));
               any = true;
-              phase ^= 1;
+              if (++stage == kOzStages) { stage = 0; phase ^= 1; }
             }
             tc_commit(smem_u32(&tfull_bar));
             acc_phase ^= 1;
@@ -404,7 +431,6 @@ oz_gemm_kernel(const OzTile* __restrict__ tiles, int ntiles, const OzJob* __rest
 // ======================================================================== host side
 namespace {
 
-using tc::kChunk;
 using tc::kRows;
 
 int cdiv(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
@@ -413,9 +439,9 @@ struct OzAlloc {
   int64_t bytes = 0, exps = 0;
   // image of rows x K: returns (byte offset, exponent offset, nkt)
   std::tuple<int64_t, int64_t, int> add(int64_t rows, int64_t K) {
-    const int nrt = cdiv(rows, kRows), nkt = cdiv(K, 64), nch = cdiv(nkt, tc::kChunkKT);
+    const int nrt = cdiv(rows, kRows), nkt = cdiv(K, tc::kKT), nch = cdiv(nkt, tc::kChunkKT);
     const int64_t off = bytes, eoff = exps;
-    bytes += (int64_t)nrt * nkt * tc::S * kChunk;
+    bytes += (int64_t)nrt * nkt * tc::S * tc::kPlane;
     exps += (int64_t)nrt * kRows * nch;
     return {off, eoff, nkt};
   }
@@ -534,13 +560,13 @@ dmrg_status build_oz(dmrg_plan* p, cudaStream_t st, OzPlan** out) {
     if (r.a_first) {  // T [dj x dk] = A X
       job.M = (int32_t)r.dj;
       job.N = (int32_t)r.dk;
-      if (r.di > 0) segs.push_back(seg(0, op_image(0, a_op, r.a_blk, 1.0), 1, xb[r.pin], cdiv(r.di, 64)));
+      if (r.di > 0) segs.push_back(seg(0, op_image(0, a_op, r.a_blk, 1.0), 1, xb[r.pin], cdiv(r.di, tc::kKT)));
       timg[ri] = ts.add(r.dj, r.dk);
       t_jobs.push_back(mk(r.inter_off, r.dk, 1, timg[ri], r.dj, r.dk, 2, 1.0));
     } else {          // U^T [dl x di] = (coef B) X^T
       job.M = (int32_t)r.dl;
       job.N = (int32_t)r.di;
-      if (r.dk > 0) segs.push_back(seg(0, op_image(1, b_op, r.b_blk, r.coef), 1, xa[r.pin], cdiv(r.dk, 64)));
+      if (r.dk > 0) segs.push_back(seg(0, op_image(1, b_op, r.b_blk, r.coef), 1, xa[r.pin], cdiv(r.dk, tc::kKT)));
       timg[ri] = ts.add(r.dl, r.di);
       t_jobs.push_back(mk(r.inter_off, r.di, 1, timg[ri], r.dl, r.di, 2, 1.0));
     }
@@ -565,14 +591,14 @@ dmrg_status build_oz(dmrg_plan* p, cudaStream_t st, OzPlan** out) {
       const int a_op = p->terms[r.term].a_op, b_op = p->terms[r.term].b_op;
       if (r.a_blk >= 0 && r.b_blk >= 0) {
         if (r.a_first) {
-          if (r.dk > 0) segs.push_back(seg(2, timg[ri], 0, op_image(1, b_op, r.b_blk, r.coef), cdiv(r.dk, 64)));
+          if (r.dk > 0) segs.push_back(seg(2, timg[ri], 0, op_image(1, b_op, r.b_blk, r.coef), cdiv(r.dk, tc::kKT)));
         } else {
-          if (r.di > 0) segs.push_back(seg(0, op_image(0, a_op, r.a_blk, 1.0), 2, timg[ri], cdiv(r.di, 64)));
+          if (r.di > 0) segs.push_back(seg(0, op_image(0, a_op, r.a_blk, 1.0), 2, timg[ri], cdiv(r.di, tc::kKT)));
         }
       } else if (r.a_blk >= 0) {
-        if (r.di > 0) segs.push_back(seg(0, op_image(0, a_op, r.a_blk, r.coef), 1, xb[r.pin], cdiv(r.di, 64)));
+        if (r.di > 0) segs.push_back(seg(0, op_image(0, a_op, r.a_blk, r.coef), 1, xb[r.pin], cdiv(r.di, tc::kKT)));
       } else if (r.b_blk >= 0) {
-        if (r.dk > 0) segs.push_back(seg(1, xa[r.pin], 0, op_image(1, b_op, r.b_blk, r.coef), cdiv(r.dk, 64)));
+        if (r.dk > 0) segs.push_back(seg(1, xa[r.pin], 0, op_image(1, b_op, r.b_blk, r.coef), cdiv(r.dk, tc::kKT)));
       } else {
         if (r.pin == r.pout) job.axpy += r.coef;  // (other segments: seg_axpy pass)
       }

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
 #include <string>
 #include <utility>
 #include <vector>
@@ -152,6 +153,7 @@ struct SegAxpyEntry {
 
 struct TcPlan;           // tensor-core (low precision) part, see gemm_tc.cu
 struct OzPlan;           // FP64-accurate tensor-core part, see gemm_oz.cu
+struct SolveWorkspace;   // buffers of one Davidson state, see davidson.cu
 
 }  // namespace dmrg
 
@@ -188,6 +190,14 @@ struct dmrg_plan {
 
   dmrg::TcPlan* tc[3] = {nullptr, nullptr, nullptr};  // TF32, BF16x3, BF16x2; built on first use
   dmrg::OzPlan* oz = nullptr;                 // FP64 emulation; built on first use
+
+  // buffers kept between solves (released by dmrg_plan_trim and dmrg_plan_destroy): the
+  // workspace of the last finished Davidson state, and the two device vectors of
+  // dmrg_davidson_solve_host; ws_mu guards the three pointers
+  std::mutex ws_mu;
+  dmrg::SolveWorkspace* ws_cache = nullptr;
+  double* io_x0 = nullptr;
+  double* io_x = nullptr;
 };
 
 namespace dmrg {
@@ -267,6 +277,24 @@ struct VecWork {
 
 dmrg_status vec_work_create(VecWork* w);
 void vec_work_destroy(VecWork* w);
+
+// The device and pinned buffers of one Davidson state (davidson.cu).  A finished state
+// hands them to its plan, and the next state of the same shape takes them over, so that
+// repeated solves allocate nothing and replay the projection graphs captured for the same
+// column pointers.
+struct SolveWorkspace {
+  int64_t ldv = 0;
+  int kmax = 0;
+  bool f32 = false, keep2 = false;
+  double *V = nullptr, *W = nullptr;
+  float *V32 = nullptr, *W32 = nullptr;
+  double *tbuf = nullptr, *D = nullptr, *xbuf = nullptr, *wbuf = nullptr;
+  double *pbuf = nullptr, *wpbuf = nullptr;
+  DevSmall* small = nullptr;
+  DevSmall* hsmall = nullptr;
+  VecWork vw;
+};
+void workspace_free(SolveWorkspace* w);
 
 // s_out[j] = V_j . w for j < k (V column-major, ldv); if Bcol >= 0 also fills row and
 // column Bcol of small->B.

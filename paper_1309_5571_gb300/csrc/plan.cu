@@ -735,6 +735,7 @@ dmrg_status dmrg_plan_create_l11r(const dmrg_l11r_desc* desc, const dmrg_options
 
 void dmrg_plan_destroy(dmrg_plan* p) {
   if (!p) return;
+  dmrg_plan_trim(p);
   destroy_tc(p);
   destroy_oz(p);
   cudaFree(p->arena);

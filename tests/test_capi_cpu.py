@@ -116,6 +116,10 @@ def test_gemv_trans_argument_checks(lib):
     assert lib.dmrg_gemv_trans(buf, 4, 4, 25, buf, buf, None) == 1    # k > 24
 
 
+def test_trim_rejects_a_null_plan(lib):
+    assert lib.dmrg_plan_trim(None) == 1
+
+
 def test_schedule_calls_check_arguments(lib):
     # NULL plan and precisions without tile schedules are rejected on the host
     assert lib.dmrg_plan_set_tile_schedule(None, 2, 0, 0, None) == 1

@@ -1,5 +1,6 @@
 """The allocation-free overlap entry point (dmrg_gemv_trans_noalloc) against the allocating
-one (dmrg_gemv_trans), through the C ABI.
+one (dmrg_gemv_trans), through the C ABI; and repeated solves on one plan, which reuse the
+workspace their plan keeps (dmrg_plan_trim releases it).
 
 Some callers cannot let the library allocate device memory (their allocator owns all of
 it, or cudaMalloc's synchronisation is not acceptable in their loop); for them the library
@@ -101,3 +102,39 @@ def test_noalloc_allocates_no_device_memory():
     assert free1 == free0
     np.testing.assert_allclose(s.cpu().numpy(), V.cpu().numpy() @ w.cpu().numpy(), rtol=1e-12,
                                atol=1e-12 * n)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "bf16x2"])
+def test_repeated_solves_allocate_nothing(prec):
+    from dmrg_inputs import warmup
+    from paper_1309_5571_gb300 import Plan
+    sb = warmup.warmup_superblock("heisenberg", 40, m=300)
+    plan = Plan(sb, prec=prec)
+    x0 = torch.from_numpy(warmup.start_vector(sb.n, seed=0)).cuda()
+    x1, x2 = torch.empty_like(x0), torch.empty_like(x0)
+    _, i1 = plan.solve(x0, x1)
+    torch.cuda.synchronize()
+    free1 = torch.cuda.mem_get_info()[0]
+    _, i2 = plan.solve(x0, x2)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free1
+    # the same workspace and tile schedule: the same iterations, bit for bit
+    assert torch.equal(x1, x2)
+    assert (i1["iters"], i1["energy"]) == (i2["iters"], i2["energy"])
+    # host-buffer solves keep their two device vectors as well
+    xh0 = x0.cpu().numpy()
+    plan.solve_host(xh0)
+    torch.cuda.synchronize()
+    free3 = torch.cuda.mem_get_info()[0]
+    xh, _ = plan.solve_host(xh0)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free3
+    np.testing.assert_array_equal(xh, x1.cpu().numpy())
+    plan.trim()
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] > free3
+    # and the plan still solves after the trim
+    x3 = torch.empty_like(x0)
+    _, i3 = plan.solve(x0, x3)
+    assert torch.equal(x3, x1)
+    plan.close()
