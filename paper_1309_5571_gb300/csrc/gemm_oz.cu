@@ -15,7 +15,7 @@
 // scales the S exact group sums by powers of two and adds them into a double-float
 // (FP32 hi + FP32 lo, ~48 bits) accumulator per output element; the result is converted
 // to FP64 once.  The rest mirrors the low-precision path: two stages (intermediates in
-// FP64, re-split for stage 2), operand tiles pre-swizzled into the 128-byte K-major
+// FP64, re-split for stage 2), operand tiles pre-swizzled into the 64-byte K-major
 // layout and moved by single bulk copies.
 //
 // Tile: 128 output rows (M of the MMA) x 64 columns (N); K tiles of 32 elements in the
@@ -217,9 +217,11 @@ __device__ __forceinline__ float pow2f(int e) {
 // accumulators; the descriptors are the stage's base descriptors plus constant offsets
 // (in 16-byte units; every address stays below 256 KB, so the 14-bit address field does
 // not carry).  FIRST: the first K tile of an exponent chunk, in which the first MMA of each
-// group (s = 0, first K step) overwrites its accumulator.
+// group (s = 0, first K step) overwrites its accumulator.  Called by the whole MMA warp;
+// leader (one lane) issues.
 template <bool FIRST>
-__device__ __forceinline__ void issue_ktile(uint32_t tmem_base, uint64_t ad0, uint64_t bd0) {
+__device__ __forceinline__ void issue_ktile(uint32_t tmem_base, uint64_t ad0, uint64_t bd0,
+                                            bool leader) {
   constexpr uint32_t idesc = instr_desc<false, kN>();
 #pragma unroll
   for (int kk = 0; kk < OzL::ROWB / 32; ++kk) {
@@ -229,8 +231,9 @@ __device__ __forceinline__ void issue_ktile(uint32_t tmem_base, uint64_t ad0, ui
       for (int u = 0; u < S - s; ++u) {
         const uint64_t ad = ad0 + (uint64_t)((s * kPlane + kk * 32) >> 4);
         const uint64_t bd = bd0 + (uint64_t)((u * (kPlane / 2) + kk * 32) >> 4);
-        mma<false>(tmem_base + (uint32_t)((s + u) * kN), ad, bd, idesc,
-                   (FIRST && kk == 0 && s == 0) ? 0u : 1u);
+        if (leader)
+          mma<false>(tmem_base + (uint32_t)((s + u) * kN), ad, bd, idesc,
+                     (FIRST && kk == 0 && s == 0) ? 0u : 1u);
       }
     }
   }
@@ -318,40 +321,44 @@ oz_gemm_kernel(const OzTile* __restrict__ tiles, int ntiles, const OzJob* __rest
     }
   } else if (warp == 1) {
     // ------------------------------------------------ MMA issuer
-    if (lane == 0) {
-      int stage = 0;
-      uint32_t phase = 0, acc_phase = 0;
-      bool any = false;
-      for (int t = blockIdx.x; t < ntiles && !abort_flag; t += gridDim.x) {
-        const OzJob job = jobs[tiles[t].job];
-        for (int si = job.seg_begin; si < job.seg_end && !abort_flag; ++si) {
-          const int nkt = segs[si].nkt;
-          for (int c0 = 0; c0 < nkt && !abort_flag; c0 += kChunkKT) {
-            if (!mbar_wait(smem_u32(&tempty_bar), acc_phase ^ 1, &abort_flag, gerr, 12)) break;
+    // The whole warp runs the loop in step (its control flow and the descriptors stay
+    // warp-uniform); lane 0 alone issues the MMAs and the commits that track them.
+    const bool leader = lane == 0;
+    int stage = 0;
+    uint32_t phase = 0, acc_phase = 0;
+    bool any = false;
+    for (int t = blockIdx.x; t < ntiles && !abort_flag; t += gridDim.x) {
+      const OzJob job = jobs[tiles[t].job];
+      for (int si = job.seg_begin; si < job.seg_end && !abort_flag; ++si) {
+        const int nkt = segs[si].nkt;
+        for (int c0 = 0; c0 < nkt && !abort_flag; c0 += kChunkKT) {
+          if (!mbar_wait_warp(smem_u32(&tempty_bar), acc_phase ^ 1, &abort_flag, gerr, 12)) break;
+          tc_fence_after();
+          const int c1 = min(c0 + kChunkKT, nkt);
+          for (int kt = c0; kt < c1; ++kt) {
+            if (!mbar_wait_warp(smem_u32(&full_bar[stage]), phase, &abort_flag, gerr, 13)) break;
             tc_fence_after();
-            const int c1 = min(c0 + kChunkKT, nkt);
-            for (int kt = c0; kt < c1; ++kt) {
-              if (!mbar_wait(smem_u32(&full_bar[stage]), phase, &abort_flag, gerr, 13)) break;
-              tc_fence_after();
-              const uint32_t sa = smem_u32(smem + stage * kStage);
-              const uint64_t ad0 = OzL::desc(sa), bd0 = OzL::desc(sa + kStageA);
-              if (kt == c0) issue_ktile<true>(tmem_base, ad0, bd0);
-              else issue_ktile<false>(tmem_base, ad0, bd0);
-              tc_commit(smem_u32(&empty_bar[stage]));
-              any = true;
-              if (++stage == kOzStages) { stage = 0; phase ^= 1; }
-            }
-            tc_commit(smem_u32(&tfull_bar));
-            acc_phase ^= 1;
+            const uint32_t sa = smem_u32(smem + stage * kStage);
+            const uint64_t ad0 = OzL::desc(sa), bd0 = OzL::desc(sa + kStageA);
+            if (kt == c0) issue_ktile<true>(tmem_base, ad0, bd0, leader);
+            else issue_ktile<false>(tmem_base, ad0, bd0, leader);
+            if (leader) tc_commit(smem_u32(&empty_bar[stage]));
+            __syncwarp();
+            any = true;
+            if (++stage == kOzStages) { stage = 0; phase ^= 1; }
           }
+          if (leader) tc_commit(smem_u32(&tfull_bar));
+          __syncwarp();
+          acc_phase ^= 1;
         }
       }
-      if (any) {
-        tc_commit(smem_u32(&drain_bar));
-        const uint64_t t0 = gtime();
-        while (!mbar_try_wait(smem_u32(&drain_bar), 0) && gtime() - t0 < kWaitNs) {}
-      }
     }
+    if (any && leader) {
+      tc_commit(smem_u32(&drain_bar));
+      const uint64_t t0 = gtime();
+      while (!mbar_try_wait(smem_u32(&drain_bar), 0) && gtime() - t0 < kWaitNs) {}
+    }
+    __syncwarp();
   } else {
     // ------------------------------------------------ epilogue (warps 2..9)
     const int quarter = warp & 3;

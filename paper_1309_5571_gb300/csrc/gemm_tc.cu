@@ -338,7 +338,7 @@ tc_gemm_kernel(const TcTile* __restrict__ tiles, int ntiles, const TcJob* __rest
     mbar_init(smem_u32(&drain_bar), 1);
     for (int r = 0; r < kRing; ++r) {
       mbar_init(smem_u32(&tq_full[r]), 1);
-      mbar_init(smem_u32(&tq_empty[r]), 5);  // the MMA lane and one lane per epilogue warp
+      mbar_init(smem_u32(&tq_empty[r]), 5);  // one lane of the MMA warp and of each epilogue warp
     }
     abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -359,9 +359,11 @@ tc_gemm_kernel(const TcTile* __restrict__ tiles, int ntiles, const TcJob* __rest
   // of its problem (tile.pad_), and tiles of inactive problems are skipped by all roles
   auto active = [&](const TcTile& tile) { return !ptrs || ptrs[tile.pad_].active != 0; };
   // consumer side of the tile ring: the next tile index, -1 at the end (or on abort);
-  // called by the MMA lane alone or by a whole epilogue warp (one arrival per warp)
+  // called by a whole warp (the MMA warp, each epilogue warp: one arrival per warp)
   auto next_tile = [&](int& slot, uint32_t& phase, bool whole_warp, int code) -> int {
-    if (!mbar_wait(smem_u32(&tq_full[slot]), phase, &abort_flag, gerr, code)) return -1;
+    const bool ok = whole_warp ? mbar_wait_warp(smem_u32(&tq_full[slot]), phase, &abort_flag, gerr, code)
+                               : mbar_wait(smem_u32(&tq_full[slot]), phase, &abort_flag, gerr, code);
+    if (!ok) return -1;
     const int t = tile_ring[slot];
     if (whole_warp) __syncwarp();
     if ((threadIdx.x & 31) == 0) mbar_arrive(smem_u32(&tq_empty[slot]));
@@ -446,66 +448,70 @@ tc_gemm_kernel(const TcTile* __restrict__ tiles, int ntiles, const TcJob* __rest
     }
   } else if (warp == 1) {
     // ------------------------------------------------ MMA issuer
-    if (lane == 0) {
-      int stage = 0;
-      uint32_t phase = 0;
-      int acc = 0;
-      uint32_t acc_phase = 0;
-      bool any = false;
-      constexpr uint32_t idesc128 = instr_desc<TF32, 128>();
-      constexpr uint32_t idesc256 = instr_desc<TF32, 256>();
-      int rslot = 0;
-      uint32_t rphase = 0;
-      while (!abort_flag) {
-        const int t = next_tile(rslot, rphase, false, 6);
-        if (t < 0) break;
-        const TcTile tile = tiles[t];
-        if (!active(tile) || tile.kb >= tile.ke) continue;
-        const TcJob job = jobs[tile.job];
-        const uint32_t idesc = (WIDE && tile.wide) ? idesc256 : idesc128;
-        if (!mbar_wait(smem_u32(&tempty_bar[acc]), acc_phase ^ 1, &abort_flag, gerr, 2)) break;
-        tc_fence_after();
-        const uint32_t d_tmem = tmem_base + (uint32_t)(acc * kAccCols);
-        uint32_t accumulate = 0;
-        int kbase = 0;
-        for (int si = job.seg_begin; si < job.seg_end && !abort_flag; ++si) {
-          const int nkt = segs[si].nkt;
-          const int k_lo = max(tile.kb - kbase, 0), k_hi = min(tile.ke - kbase, nkt);
-          kbase += nkt;
-          for (int kt = k_lo; kt < k_hi; ++kt) {
-            if (!mbar_wait(smem_u32(&full_bar[stage]), phase, &abort_flag, gerr, 3)) break;
-            tc_fence_after();
-            const uint32_t sa = smem_u32(smem + stage * kStage);
-            const uint32_t sb = sa + kStageA;
+    // The whole warp runs the loop in step (its control flow and the descriptors stay
+    // warp-uniform); lane 0 alone issues the MMAs and the commits that track them.
+    const bool leader = lane == 0;
+    int stage = 0;
+    uint32_t phase = 0;
+    int acc = 0;
+    uint32_t acc_phase = 0;
+    bool any = false;
+    constexpr uint32_t idesc128 = instr_desc<TF32, 128>();
+    constexpr uint32_t idesc256 = instr_desc<TF32, 256>();
+    int rslot = 0;
+    uint32_t rphase = 0;
+    while (!abort_flag) {
+      const int t = next_tile(rslot, rphase, true, 6);
+      if (t < 0) break;
+      const TcTile tile = tiles[t];
+      if (!active(tile) || tile.kb >= tile.ke) continue;
+      const TcJob job = jobs[tile.job];
+      const uint32_t idesc = (WIDE && tile.wide) ? idesc256 : idesc128;
+      if (!mbar_wait_warp(smem_u32(&tempty_bar[acc]), acc_phase ^ 1, &abort_flag, gerr, 2)) break;
+      tc_fence_after();
+      const uint32_t d_tmem = tmem_base + (uint32_t)(acc * kAccCols);
+      uint32_t accumulate = 0;
+      int kbase = 0;
+      for (int si = job.seg_begin; si < job.seg_end && !abort_flag; ++si) {
+        const int nkt = segs[si].nkt;
+        const int k_lo = max(tile.kb - kbase, 0), k_hi = min(tile.ke - kbase, nkt);
+        kbase += nkt;
+        for (int kt = k_lo; kt < k_hi; ++kt) {
+          if (!mbar_wait_warp(smem_u32(&full_bar[stage]), phase, &abort_flag, gerr, 3)) break;
+          tc_fence_after();
+          const uint32_t sa = smem_u32(smem + stage * kStage);
+          const uint32_t sb = sa + kStageA;
 #pragma unroll
-            for (int pr = 0; pr < kProducts<PLANES>(); ++pr) {
-              // plane pairs (pa, pb) with pa + pb < PLANES: (0,0) (0,1) (1,0) (0,2) (1,1) (2,0)
-              const int pa = pr == 0 ? 0 : pr == 1 ? 0 : pr == 2 ? 1 : pr == 3 ? 0 : pr == 4 ? 1 : 2;
-              const int pb = pr == 0 ? 0 : pr == 1 ? 1 : pr == 2 ? 0 : pr == 3 ? 2 : pr == 4 ? 1 : 0;
+          for (int pr = 0; pr < kProducts<PLANES>(); ++pr) {
+            // plane pairs (pa, pb) with pa + pb < PLANES: (0,0) (0,1) (1,0) (0,2) (1,1) (2,0)
+            const int pa = pr == 0 ? 0 : pr == 1 ? 0 : pr == 2 ? 1 : pr == 3 ? 0 : pr == 4 ? 1 : 2;
+            const int pb = pr == 0 ? 0 : pr == 1 ? 1 : pr == 2 ? 0 : pr == 3 ? 2 : pr == 4 ? 1 : 0;
 #pragma unroll
-              for (int kk = 0; kk < L::ROWB / 32; ++kk) {  // one MMA per 32 bytes of K
-                const uint64_t ad = L::desc(sa + pa * L::CHUNK + kk * 32);
-                const uint64_t bd = L::desc(sb + pb * kSlotB + kk * 32);
-                mma<TF32>(d_tmem, ad, bd, idesc, accumulate);
-                accumulate = 1;
-              }
+            for (int kk = 0; kk < L::ROWB / 32; ++kk) {  // one MMA per 32 bytes of K
+              const uint64_t ad = L::desc(sa + pa * L::CHUNK + kk * 32);
+              const uint64_t bd = L::desc(sb + pb * kSlotB + kk * 32);
+              if (leader) mma<TF32>(d_tmem, ad, bd, idesc, accumulate);
+              accumulate = 1;
             }
-            tc_commit(smem_u32(&empty_bar[stage]));
-            any = true;
-            if (++stage == STAGES) { stage = 0; phase ^= 1; }
           }
+          if (leader) tc_commit(smem_u32(&empty_bar[stage]));
+          __syncwarp();
+          any = true;
+          if (++stage == STAGES) { stage = 0; phase ^= 1; }
         }
-        tc_commit(smem_u32(&tfull_bar[acc]));
-        acc ^= 1;
-        if (acc == 0) acc_phase ^= 1;
       }
-      if (any) {
-        // all MMAs issued by this thread complete before TMEM is released
-        tc_commit(smem_u32(&drain_bar));
-        const uint64_t t0 = gtime();
-        while (!mbar_try_wait(smem_u32(&drain_bar), 0) && gtime() - t0 < kWaitNs) {}
-      }
+      if (leader) tc_commit(smem_u32(&tfull_bar[acc]));
+      __syncwarp();
+      acc ^= 1;
+      if (acc == 0) acc_phase ^= 1;
     }
+    if (any && leader) {
+      // all MMAs issued by this thread complete before TMEM is released
+      tc_commit(smem_u32(&drain_bar));
+      const uint64_t t0 = gtime();
+      while (!mbar_try_wait(smem_u32(&drain_bar), 0) && gtime() - t0 < kWaitNs) {}
+    }
+    __syncwarp();
   } else {
     // ------------------------------------------------ epilogue (warps 2..5)
     const int quarter = warp & 3;

@@ -55,6 +55,14 @@ static __device__ __noinline__ bool mbar_wait(uint32_t bar, uint32_t parity, vol
     }
   }
 }
+// The same wait made by every lane of a warp, with one outcome for all lanes (false if any
+// lane saw an abort or a timeout), so that the warp leaves it converged.
+static __device__ __forceinline__ bool mbar_wait_warp(uint32_t bar, uint32_t parity,
+                                                      volatile int* abort_flag, int* gerr,
+                                                      int code) {
+  const bool ok = mbar_wait(bar, parity, abort_flag, gerr, code);
+  return __all_sync(0xffffffffu, ok);
+}
 __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes,
                                          uint32_t bar) {
   asm volatile(
