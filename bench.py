@@ -620,6 +620,7 @@ def main():
                       "iters_per_step": [i["iters"] for i in infos],
                       "projections": statistics.mean(i["projections"] for i in infos),
                       "fp64_projections": statistics.mean(i["fp64_projections"] for i in infos),
+                      "anchor_updates": statistics.mean(i["anchor_updates"] for i in infos),
                       "restarts": statistics.mean(i["restarts"] for i in infos), "energy": e_ref,
                       "resnorm": max(i["resnorm"] for i in infos), "plan_ms": plan_ms,
                       "fp64_path_solve_ms": fp64_solve_ms, "fp64_path_energy": e_fp64,

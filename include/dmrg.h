@@ -189,7 +189,8 @@ typedef struct {
                             fallen by this factor below the last FP64 residual (0: only
                             the adaptive floor test and the subspace limit re-anchor)     */
   dmrg_precision anchor_prec; /* FP64-accurate projections of the mixed modes: DMRG_PREC_FP64
-                            (FP64 units, default) or DMRG_PREC_FP64_TC (tensor cores)     */
+                            (FP64 units, default) or DMRG_PREC_FP64_TC (tensor cores,
+                            FP64-accurate digit products; about 17x faster)              */
   int32_t vector_arith;  /* arithmetic of the Davidson vector passes (dmrg_vector_arith);
                             vectors are float64 in memory in every mode (default
                             DMRG_VEC_SPLIT)                                              */
@@ -205,6 +206,13 @@ typedef struct {
                             plan; a call made while the caller's stream is being captured
                             launches the kernels directly into that capture; 0: direct
                             launches always.  The results are identical either way.       */
+  int32_t anchor_update; /* 1 (default): with anchor_prec = DMRG_PREC_FP64_TC, an anchor taken
+                            while column 0 of the basis is still the previous anchor (no
+                            plain restart since) is formed as H x = y_0 W(:,0) + H d,
+                            d = x - y_0 v_0, with H d computed from the leading digits of
+                            the FP64_TC split that its norm needs (error held below 2^-46
+                            ||H||, as for a full FP64_TC projection); 0: every anchor
+                            projects x in full.                                          */
 } dmrg_options;
 
 typedef struct {
@@ -216,6 +224,8 @@ typedef struct {
   int32_t restarts;         /* basis collapses (subspace limit or re-anchoring)           */
   int32_t small_eig_sweeps; /* Jacobi sweeps of the projected eigenproblem, all iterations */
   int32_t converged;        /* 1 if ||r|| <= tol was reached                               */
+  int32_t anchor_updates;   /* anchors formed by the anchor update (included in
+                               fp64_projections)                                          */
 } dmrg_solve_info;
 
 typedef struct {
@@ -299,6 +309,15 @@ dmrg_status dmrg_plan_set_tile_schedule(dmrg_plan* plan, dmrg_precision prec, in
 dmrg_status dmrg_project(dmrg_plan* plan, const double* x, double* y, void* stream);
 dmrg_status dmrg_project_prec(dmrg_plan* plan, dmrg_precision prec, const double* x,
                               double* y, void* stream);
+/* y = H_SB x on the FP64_TC path with the leading `digits` (2..7) base-128 digits of every
+ * operand and stage-1 result (7: the FP64-accurate DMRG_PREC_FP64_TC projection; d digits
+ * cost d (d + 1) / 2 digit-pair products instead of 28 and give a relative accuracy of about
+ * 2^(1 - 7 d) of the row-chunk scales).  The paper has no counterpart: the Davidson anchor
+ * update uses it for the projection of a small correction (dmrg_options.anchor_update).
+ * Same layout, stream and overlap rules as dmrg_project; DMRG_ERR_INVALID_ARG for digits
+ * outside [2, 7]. */
+dmrg_status dmrg_project_digits(dmrg_plan* plan, int32_t digits, const double* x, double* y,
+                                void* stream);
 
 /* d = diag(H_SB) (device array of n float64), the Davidson preconditioner input. */
 dmrg_status dmrg_diagonal(dmrg_plan* plan, double* d, void* stream);

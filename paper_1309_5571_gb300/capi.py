@@ -84,14 +84,15 @@ class Options(C.Structure):
     _fields_ = [("prec", C.c_int32), ("tol", C.c_double), ("max_iter", C.c_int32),
                 ("max_subspace", C.c_int32), ("restart_keep", C.c_int32), ("fp64_refine", C.c_int32),
                 ("refine_ratio", C.c_double), ("anchor_prec", C.c_int32),
-                ("vector_arith", C.c_int32), ("autotune", C.c_int32), ("graphs", C.c_int32)]
+                ("vector_arith", C.c_int32), ("autotune", C.c_int32), ("graphs", C.c_int32),
+                ("anchor_update", C.c_int32)]
 
 
 class SolveInfo(C.Structure):
     _fields_ = [("energy", C.c_double), ("resnorm", C.c_double), ("iters", C.c_int32),
                 ("projections", C.c_int32), ("fp64_projections", C.c_int32),
                 ("restarts", C.c_int32), ("small_eig_sweeps", C.c_int32),
-                ("converged", C.c_int32)]
+                ("converged", C.c_int32), ("anchor_updates", C.c_int32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -124,6 +125,7 @@ SIGNATURES = {
     "dmrg_plan_set_tile_schedule": (C.c_int, [C.c_void_p, C.c_int, C.c_int32, C.c_int32, C.c_void_p]),
     "dmrg_project": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "dmrg_project_prec": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "dmrg_project_digits": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p]),
     "dmrg_diagonal": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "dmrg_gemv_trans": (C.c_int, [C.c_void_p, C.c_int64, C.c_int64, C.c_int32, C.c_void_p,
                                   C.c_void_p, C.c_void_p]),
@@ -285,7 +287,7 @@ def marshal(sb) -> _Marshalled:
 
 def options(prec="fp64", tol=1e-10, max_iter=1000, max_subspace=20, restart_keep=2, fp64_refine=True,
             refine_ratio=0.0, anchor_prec="fp64", vector_arith="split", autotune=True,
-            graphs=True) -> Options:
+            graphs=True, anchor_update=True) -> Options:
     o = Options()
     load().dmrg_options_default(C.byref(o))
     o.prec = PREC[prec] if isinstance(prec, str) else int(prec)
@@ -299,6 +301,7 @@ def options(prec="fp64", tol=1e-10, max_iter=1000, max_subspace=20, restart_keep
     o.vector_arith = VEC[vector_arith] if isinstance(vector_arith, str) else int(vector_arith)
     o.autotune = int(bool(autotune))
     o.graphs = int(bool(graphs))
+    o.anchor_update = int(bool(anchor_update))
     return o
 
 
@@ -371,6 +374,17 @@ class Plan:
         p = self.opt.prec if prec is None else (PREC[prec] if isinstance(prec, str) else prec)
         _check(self.lib.dmrg_project_prec(self.handle, int(p), x.data_ptr(), y.data_ptr(),
                                           _stream_ptr(stream)))
+        return y
+
+    def project_digits(self, x, digits, y=None, stream=None):
+        """dmrg_project_digits: y = H x on the FP64_TC path with the leading `digits` digits."""
+        torch = _torch()
+        _check_vec(x, self.n, "x")
+        if y is None:
+            y = torch.empty_like(x)
+        _check_vec(y, self.n, "y")
+        _check(self.lib.dmrg_project_digits(self.handle, int(digits), x.data_ptr(), y.data_ptr(),
+                                            _stream_ptr(stream)))
         return y
 
     def diagonal(self, stream=None):

@@ -497,6 +497,7 @@ extern "C" dmrg_status dmrg_davidson_solve_block(dmrg_plan* plan, int32_t nev, i
     info->restarts = s.restarts;
     info->small_eig_sweeps = s.sweeps;
     info->converged = converged ? 1 : 0;
+    info->anchor_updates = 0;
   }
   if (err == DMRG_OK && !converged) {
     set_error("block Davidson did not converge in %d iterations", s.iters);

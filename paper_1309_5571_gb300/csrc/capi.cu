@@ -38,6 +38,7 @@ void dmrg_options_default(dmrg_options* opt) {
   opt->vector_arith = DMRG_VEC_SPLIT;
   opt->autotune = 1;
   opt->graphs = 1;
+  opt->anchor_update = 1;
 }
 
 const char* dmrg_status_string(dmrg_status s) {

@@ -74,6 +74,8 @@ struct dmrg_davidson_state {
   bool did_restart = false;
   bool proj_fp64 = false;   // this iteration's projection is FP64-accurate
   bool ws_complete = false; // every workspace buffer was allocated (it may go to the plan)
+  bool w0_ready = false;    // W(:,0) of the pending anchor was formed by the anchor update
+  int anchor_updates = 0;   // anchors formed from the previous one (diagnostics)
 };
 
 namespace {
@@ -230,7 +232,8 @@ dmrg_status dmrg_state_create(dmrg_plan* plan, const double* x0, void* stream,
   const size_t col = sizeof(double) * (size_t)s->ldv;
   const size_t col32 = sizeof(float) * (size_t)s->ldv;
   const int cV = s->f32 ? 1 : s->kmax + 1, cW = s->f32 ? 1 : s->kmax;
-  const bool keep2 = plan->opt.restart_keep == 2;
+  // the two spare vectors serve the two-vector restart and the anchor update (mixed modes)
+  const bool keep2 = plan->opt.restart_keep == 2 || s->mixed;
   dmrg::SolveWorkspace* cached = nullptr;
   {
     std::lock_guard<std::mutex> g(plan->ws_mu);
@@ -313,7 +316,7 @@ void dmrg_state_destroy(dmrg_davidson_state* s) {
       w->ldv = s->ldv;
       w->kmax = s->kmax;
       w->f32 = s->f32;
-      w->keep2 = s->plan->opt.restart_keep == 2;
+      w->keep2 = s->plan->opt.restart_keep == 2 || s->mixed;
       w->V = s->V;
       w->W = s->W;
       w->V32 = s->V32;
@@ -367,6 +370,25 @@ namespace {
 // phase_a in three parts, so that a batch can group the low-precision projections:
 // begin decides the projection arithmetic (true: a low-precision one), project runs it,
 // end enqueues the rest of the phase
+// Digits of the FP64_TC split for the anchor update of a collapse at basis size k, or 0
+// for a full projection of the new anchor.  The update applies when column 0 of V and W is
+// an FP64-accurate pair (an anchor, no plain restart since), the anchors run on the
+// FP64_TC path, and the update is cheaper: with ||d|| = ||y(1:)|| (orthonormal columns),
+// the leading `digits` digits of both stages give an error of about 2^(4 - 7 digits) ||H||
+// ||d|| (truncation of the operands and of the stage-1 results, with a margin of 8), held
+// below 2^-46 ||H||, the accuracy of a full FP64_TC projection.
+int anchor_update_digits(const dmrg_davidson_state* s, int k) {
+  if (!s->mixed || !s->anchored || s->plain_restarts != 0 || k < 2) return 0;
+  if (s->plan->opt.anchor_prec != DMRG_PREC_FP64_TC || !s->plan->opt.anchor_update) return 0;
+  double t2 = 0.0;
+  for (int j = 1; j < k; ++j) t2 += s->hsmall->y[j] * s->hsmall->y[j];
+  const double ytail = std::sqrt(t2);
+  if (!(ytail > 0.0)) return 2;
+  const int digits = (int)std::ceil((50.0 + std::log2(ytail)) / 7.0);
+  if (digits >= 7) return 0;
+  return std::max(2, digits);
+}
+
 bool phase_a_begin(dmrg_davidson_state* s) {
   const bool anchor = s->mixed && s->anchor_pending;
   if (anchor) s->anchored = true;
@@ -379,6 +401,10 @@ bool phase_a_begin(dmrg_davidson_state* s) {
 }
 
 dmrg_status phase_a_project(dmrg_davidson_state* s, cudaStream_t st) {
+  if (s->w0_ready) {  // the anchor's projection was formed in phase_b
+    s->w0_ready = false;
+    return DMRG_OK;
+  }
   return project_col(s, s->k - 1, s->proj_fp64, st);
 }
 
@@ -475,9 +501,26 @@ dmrg_status phase_b(dmrg_davidson_state* s, cudaStream_t st, bool* need_c) {
     s->restart_rnorm = s->rnorm;
   }
   if (do_anchor) {
-    // collapse to the normalised Ritz vector; its projection is redone in FP64
+    // collapse to the normalised Ritz vector; its projection is redone FP64-accurately
     DMRG_TRY(ritz(s, k, s->xbuf, nullptr, st));
-    DMRG_TRY(launch_normalize(s->vw, s->xbuf, s->V, n, s->small, st));
+    const int digits = anchor_update_digits(s, k);
+    if (digits > 0) {
+      // anchor update: x = y_0 v_0 + d with H v_0 = W(:,0) exact (FP64-accurate, no plain
+      // restart since), so H x = y_0 W(:,0) + H d, and H d needs accuracy relative to ||d||
+      // only: it runs with the leading `digits` digits of the FP64_TC split
+      const double y0 = s->hsmall->y[0];
+      DMRG_TRY(launch_axpby(s->vw, s->xbuf, -y0, s->V, s->pbuf, n, st));        // d
+      DMRG_TRY(launch_project_oz(s->plan, s->pbuf, s->wpbuf, st, digits));       // H d
+      DMRG_TRY(launch_axpby(s->vw, s->wpbuf, y0, s->W, s->wbuf, n, st));        // H x
+      DMRG_TRY(launch_normalize(s->vw, s->xbuf, s->V, n, s->small, st));
+      DMRG_TRY(launch_scale_copy(s->vw, s->wbuf, s->W, n, s->small, st));        // / ||x||
+      s->fp64_projections++;
+      s->anchor_updates++;
+      s->w0_ready = true;
+      if (trace_on()) fprintf(stderr, "dmrg anchor update with %d digits\n", digits);
+    } else {
+      DMRG_TRY(launch_normalize(s->vw, s->xbuf, s->V, n, s->small, st));
+    }
     s->k = 1;
     s->restarts++;
     s->anchor_pending = true;
@@ -641,6 +684,7 @@ dmrg_status dmrg_state_get_info(const dmrg_davidson_state* s, dmrg_solve_info* i
   info->restarts = s->restarts;
   info->small_eig_sweeps = s->sweeps;
   info->converged = s->converged ? 1 : 0;
+  info->anchor_updates = s->anchor_updates;
   return DMRG_OK;
 }
 

@@ -211,7 +211,13 @@ __device__ __forceinline__ float pow2f(int e) {
 }
 
 // ---------------------------------------------------------------- grouped GEMM
-// The MMAs of one K tile: the 28 digit pairs (s, u) with s + u <= S - 1, each into the
+// The GEMM uses the leading NS <= S digits of each operand (the planes of a tile are stored
+// most significant first, so they are its first NS planes): the NS (NS + 1) / 2 digit pairs
+// with s + u <= NS - 1 (28 for NS = 7).  Dropping the digits below NS truncates each operand
+// to about 7 NS bits of its row-chunk scale; a projection whose input is known to be small
+// against the quantity it corrects (the Davidson anchor update) needs no more.
+//
+// The MMAs of one K tile: the digit pairs (s, u) with s + u <= NS - 1, each into the
 // accumulator of its scale group g = s + u, for both 16-element K steps.  The K step is
 // the outermost loop and u the innermost, so consecutive MMAs write different
 // accumulators; the descriptors are the stage's base descriptors plus constant offsets
@@ -219,16 +225,16 @@ __device__ __forceinline__ float pow2f(int e) {
 // not carry).  FIRST: the first K tile of an exponent chunk, in which the first MMA of each
 // group (s = 0, first K step) overwrites its accumulator.  Called by the whole MMA warp;
 // leader (one lane) issues.
-template <bool FIRST>
+template <int NS, bool FIRST>
 __device__ __forceinline__ void issue_ktile(uint32_t tmem_base, uint64_t ad0, uint64_t bd0,
                                             bool leader) {
   constexpr uint32_t idesc = instr_desc<false, kN>();
 #pragma unroll
   for (int kk = 0; kk < OzL::ROWB / 32; ++kk) {
 #pragma unroll
-    for (int s = 0; s < S; ++s) {
+    for (int s = 0; s < NS; ++s) {
 #pragma unroll
-      for (int u = 0; u < S - s; ++u) {
+      for (int u = 0; u < NS - s; ++u) {
         const uint64_t ad = ad0 + (uint64_t)((s * kPlane + kk * 32) >> 4);
         const uint64_t bd = bd0 + (uint64_t)((u * (kPlane / 2) + kk * 32) >> 4);
         if (leader)
@@ -239,6 +245,7 @@ __device__ __forceinline__ void issue_ktile(uint32_t tmem_base, uint64_t ad0, ui
   }
 }
 
+template <int NS>
 __global__ void __launch_bounds__(kOzThreads, 1)
 oz_gemm_kernel(const OzTile* __restrict__ tiles, int ntiles, const OzJob* __restrict__ jobs,
                const OzSeg* __restrict__ segs, const uint8_t* __restrict__ b0,
@@ -297,11 +304,11 @@ oz_gemm_kernel(const OzTile* __restrict__ tiles, int ntiles, const OzJob* __rest
             if (!mbar_wait(smem_u32(&empty_bar[stage]), phase ^ 1, &abort_flag, gerr, 11)) break;
             const uint32_t sa = smem_u32(smem + stage * kStage);
             const uint32_t fb = smem_u32(&full_bar[stage]);
-            mbar_expect_tx(fb, kStage);
-            bulk_g2s(sa, P + (int64_t)kt * kStageA, kStageA, fb);
+            mbar_expect_tx(fb, NS * kPlane + NS * (kPlane / 2));
+            bulk_g2s(sa, P + (int64_t)kt * kStageA, NS * kPlane, fb);
             const uint8_t* qk = Q + (int64_t)kt * kStageA;
 #pragma unroll
-            for (int pl = 0; pl < S; ++pl)
+            for (int pl = 0; pl < NS; ++pl)
               bulk_g2s(sa + kStageA + pl * (kPlane / 2), qk + pl * kPlane, kPlane / 2, fb);
             ++issued;
             if (++stage == kOzStages) { stage = 0; phase ^= 1; }
@@ -340,8 +347,8 @@ oz_gemm_kernel(const OzTile* __restrict__ tiles, int ntiles, const OzJob* __rest
             tc_fence_after();
             const uint32_t sa = smem_u32(smem + stage * kStage);
             const uint64_t ad0 = OzL::desc(sa), bd0 = OzL::desc(sa + kStageA);
-            if (kt == c0) issue_ktile<true>(tmem_base, ad0, bd0, leader);
-            else issue_ktile<false>(tmem_base, ad0, bd0, leader);
+            if (kt == c0) issue_ktile<NS, true>(tmem_base, ad0, bd0, leader);
+            else issue_ktile<NS, false>(tmem_base, ad0, bd0, leader);
             if (leader) tc_commit(smem_u32(&empty_bar[stage]));
             __syncwarp();
             any = true;
@@ -387,7 +394,7 @@ oz_gemm_kernel(const OzTile* __restrict__ tiles, int ntiles, const OzJob* __rest
 #pragma unroll
           for (int j = 0; j < 32; ++j) sc[j] = pow2f(ep + qe[j * qch + ch]);
 #pragma unroll 1
-          for (int g = 0; g < S; ++g) {
+          for (int g = 0; g < NS; ++g) {
             uint32_t v[32];
             tmem_ld32(tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(g * kN + half * 32), v);
             const float gs = pow2f(-7 * (g + 2));
@@ -709,20 +716,18 @@ void destroy_oz(dmrg_plan* p) {
   p->oz = nullptr;
 }
 
-dmrg_status launch_project_oz(dmrg_plan* p, const double* x, double* y, cudaStream_t st) {
-  if (!p->oz) {
-    OzPlan* o = nullptr;
-    DMRG_TRY(build_oz(p, st, &o));
-    p->oz = o;
-  }
+namespace {
+
+// the two GEMM launches of a projection with the leading NS digits of every operand
+template <int NS>
+dmrg_status launch_oz_gemms(dmrg_plan* p, const double* x, double* y, cudaStream_t st) {
   OzPlan* o = p->oz;
-  DMRG_TRY(oz_error_status(p));
   static bool configured[64] = {false};
   int dev = 0;
   DMRG_CUDA_TRY(cudaGetDevice(&dev));
   if (dev >= 0 && dev < 64 && !configured[dev]) {
-    DMRG_CUDA_TRY(cudaFuncSetAttribute(tc::oz_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)tc::kOzSmem));
+    DMRG_CUDA_TRY(cudaFuncSetAttribute(tc::oz_gemm_kernel<NS>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc::kOzSmem));
     configured[dev] = true;
   }
   if (o->n_xit > 0) {
@@ -732,7 +737,7 @@ dmrg_status launch_project_oz(dmrg_plan* p, const double* x, double* y, cudaStre
   }
   if (o->ntiles1 > 0) {
     const int grid = (int)std::min<int64_t>(o->ntiles1, o->sms);
-    tc::oz_gemm_kernel<<<grid, tc::kOzThreads, tc::kOzSmem, st>>>(
+    tc::oz_gemm_kernel<NS><<<grid, tc::kOzThreads, tc::kOzSmem, st>>>(
         o->d_tiles1, (int)o->ntiles1, o->d_jobs, o->d_segs, o->img[0], o->img[1], nullptr,
         o->exps[0], o->exps[1], nullptr, p->T, y, x, o->d_err);
     DMRG_LAUNCH_CHECK();
@@ -744,10 +749,35 @@ dmrg_status launch_project_oz(dmrg_plan* p, const double* x, double* y, cudaStre
   }
   if (o->ntiles2 > 0) {
     const int grid = (int)std::min<int64_t>(o->ntiles2, o->sms);
-    tc::oz_gemm_kernel<<<grid, tc::kOzThreads, tc::kOzSmem, st>>>(
+    tc::oz_gemm_kernel<NS><<<grid, tc::kOzThreads, tc::kOzSmem, st>>>(
         o->d_tiles2, (int)o->ntiles2, o->d_jobs, o->d_segs, o->img[0], o->img[1], o->img[2],
         o->exps[0], o->exps[1], o->exps[2], p->T, y, x, o->d_err);
     DMRG_LAUNCH_CHECK();
+  }
+  return DMRG_OK;
+}
+
+}  // namespace
+
+dmrg_status launch_project_oz(dmrg_plan* p, const double* x, double* y, cudaStream_t st,
+                              int digits) {
+  if (digits < 2 || digits > tc::S) {
+    set_error("internal: FP64_TC digit count %d outside [2, %d]", digits, tc::S);
+    return DMRG_ERR_INVALID_ARG;
+  }
+  if (!p->oz) {
+    OzPlan* o = nullptr;
+    DMRG_TRY(build_oz(p, st, &o));
+    p->oz = o;
+  }
+  DMRG_TRY(oz_error_status(p));
+  switch (digits) {
+    case 2: DMRG_TRY(launch_oz_gemms<2>(p, x, y, st)); break;
+    case 3: DMRG_TRY(launch_oz_gemms<3>(p, x, y, st)); break;
+    case 4: DMRG_TRY(launch_oz_gemms<4>(p, x, y, st)); break;
+    case 5: DMRG_TRY(launch_oz_gemms<5>(p, x, y, st)); break;
+    case 6: DMRG_TRY(launch_oz_gemms<6>(p, x, y, st)); break;
+    default: DMRG_TRY(launch_oz_gemms<7>(p, x, y, st)); break;
   }
   return launch_seg_axpy(p, x, y, nullptr, nullptr, st);
 }

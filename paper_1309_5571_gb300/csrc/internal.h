@@ -239,7 +239,10 @@ inline bool tc_lowprec(dmrg_precision prec) {
 }
 dmrg_status tc_error_status(dmrg_plan* plan);
 // gemm_oz.cu
-dmrg_status launch_project_oz(dmrg_plan* plan, const double* x, double* y, cudaStream_t stream);
+// y = H x with the leading `digits` (2..7) base-128 digits of every operand (7: FP64-accurate;
+// fewer: relative accuracy ~2^(-7 digits + 1), for inputs small against what they correct)
+dmrg_status launch_project_oz(dmrg_plan* plan, const double* x, double* y, cudaStream_t stream,
+                              int digits = 7);
 void destroy_oz(dmrg_plan* plan);
 dmrg_status oz_error_status(dmrg_plan* plan);
 
@@ -285,7 +288,7 @@ void vec_work_destroy(VecWork* w);
 struct SolveWorkspace {
   int64_t ldv = 0;
   int kmax = 0;
-  bool f32 = false, keep2 = false;
+  bool f32 = false, keep2 = false;  // keep2: the spare vectors pbuf and wpbuf exist
   double *V = nullptr, *W = nullptr;
   float *V32 = nullptr, *W32 = nullptr;
   double *tbuf = nullptr, *D = nullptr, *xbuf = nullptr, *wbuf = nullptr;
@@ -323,6 +326,12 @@ dmrg_status launch_ritz(const double* V, const double* W, int64_t ldv, int64_t n
 dmrg_status launch_normalize(const VecWork& w, const double* src, double* dst, int64_t n,
                              DevSmall* small, cudaStream_t st);
 dmrg_status launch_set_B00(DevSmall* small, cudaStream_t st);
+// out = a + c b (n elements)
+dmrg_status launch_axpby(const VecWork& w, const double* a, double c, const double* b, double* out,
+                         int64_t n, cudaStream_t st);
+// dst = src / sqrt(small->nrm2) (the norm of the last launch_normalize)
+dmrg_status launch_scale_copy(const VecWork& w, const double* src, double* dst, int64_t n,
+                              const DevSmall* small, cudaStream_t st);
 // two-vector restart: x = V C0, p = V C1, wx = W C0, wp = W C1 (n elements each)
 dmrg_status launch_ritz2(const double* V, const double* W, int64_t ldv, int64_t n, int k,
                          const DevSmall* small, double* x, double* p, double* wx, double* wp,

@@ -832,4 +832,18 @@ dmrg_status dmrg_project(dmrg_plan* p, const double* x, double* y, void* stream)
   return dmrg_project_prec(p, DMRG_PREC_FP64, x, y, stream);
 }
 
+dmrg_status dmrg_project_digits(dmrg_plan* p, int32_t digits, const double* x, double* y,
+                                void* stream) {
+  if (!p || (p->n && (!x || !y)) || digits < 2 || digits > 7) {
+    set_error("dmrg_project_digits: NULL argument or digits outside [2, 7]");
+    return DMRG_ERR_INVALID_ARG;
+  }
+  if (p->n == 0) return DMRG_OK;
+  if ((const double*)y < x + p->n && x < (const double*)y + p->n) {
+    set_error("x and y overlap");
+    return DMRG_ERR_INVALID_ARG;
+  }
+  return launch_project_oz(p, x, y, (cudaStream_t)stream, digits);
+}
+
 }  // extern "C"

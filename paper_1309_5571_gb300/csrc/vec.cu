@@ -378,6 +378,13 @@ __global__ void scale_copy_kernel(const double* __restrict__ src, double* __rest
     dst[e] = src[e] * inv;
 }
 
+__global__ void axpby_kernel(const double* __restrict__ a, double c, const double* __restrict__ b,
+                             double* __restrict__ out, int64_t n) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x)
+    out[e] = fma(c, b[e], a[e]);
+}
+
 __global__ void set_B00_kernel(DevSmall* small) {
   // after a restart the basis is the single Ritz vector x with B = [lambda] = 1 x 1
   for (int j = threadIdx.x; j < KMAX * KMAX; j += blockDim.x) small->B[j] = 0.0;
@@ -462,6 +469,20 @@ dmrg_status launch_normalize(const VecWork& w, const double* src, double* dst, i
                              DevSmall* small, cudaStream_t st) {
   sumsq_kernel<<<w.grid, kVecThreads, 0, st>>>(src, n, w.partials, w.counter, small);
   DMRG_LAUNCH_CHECK();
+  scale_copy_kernel<<<w.grid, kVecThreads, 0, st>>>(src, dst, n, small);
+  DMRG_LAUNCH_CHECK();
+  return DMRG_OK;
+}
+
+dmrg_status launch_axpby(const VecWork& w, const double* a, double c, const double* b, double* out,
+                         int64_t n, cudaStream_t st) {
+  axpby_kernel<<<w.grid, kVecThreads, 0, st>>>(a, c, b, out, n);
+  DMRG_LAUNCH_CHECK();
+  return DMRG_OK;
+}
+
+dmrg_status launch_scale_copy(const VecWork& w, const double* src, double* dst, int64_t n,
+                              const DevSmall* small, cudaStream_t st) {
   scale_copy_kernel<<<w.grid, kVecThreads, 0, st>>>(src, dst, n, small);
   DMRG_LAUNCH_CHECK();
   return DMRG_OK;

@@ -48,7 +48,7 @@ def test_status_strings_and_defaults(lib):
     assert (o.prec, o.tol, o.max_iter, o.max_subspace, o.fp64_refine) == (0, 1e-10, 1000, 20, 1)
     assert o.refine_ratio == 0.0
     assert o.anchor_prec == 0 and o.vector_arith == 2  # DMRG_VEC_SPLIT
-    assert o.autotune == 1 and o.restart_keep == 2 and o.graphs == 1
+    assert o.autotune == 1 and o.restart_keep == 2 and o.graphs == 1 and o.anchor_update == 1
 
 
 def _desc_from(sb):

@@ -37,6 +37,8 @@ VARIANTS = {
     "bf16x3+fp64": dict(prec="bf16x3", anchor_prec="fp64"),
     "bf16x2+fp64tc": dict(prec="bf16x2", anchor_prec="fp64tc"),
     "tf32+fp64tc": dict(prec="tf32", anchor_prec="fp64tc"),
+    # every anchor a full FP64_TC projection (no anchor update)
+    "bf16x2+fp64tc/full-anchors": dict(prec="bf16x2", anchor_prec="fp64tc", anchor_update=False),
 }
 
 
@@ -59,9 +61,15 @@ def test_full_size_solve_matches_golden_energy(name, variant):
     g = golden()[name]
     sb = workload(name)
     assert sb.n == g["n"]
-    info = _check_solve(sb, g["energy"], VARIANTS[variant])
+    opts = VARIANTS[variant]
+    info = _check_solve(sb, g["energy"], opts)
     if variant not in ("fp64", "fp64tc"):
         assert info["fp64_projections"] >= 1 and info["projections"] >= 1
+    if opts.get("anchor_prec") != "fp64tc" or opts.get("anchor_update") is False:
+        assert info["anchor_updates"] == 0
+    elif name == "hub_L64_m2048":
+        # later anchors of this solve are formed from the previous one (a few digits suffice)
+        assert 1 <= info["anchor_updates"] <= info["fp64_projections"]
 
 
 def test_golden_file_is_the_oracles():
