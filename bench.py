@@ -69,12 +69,12 @@ TC_TRAFFIC = {
     ("bf16x3", (6, 17)): 535.3e6,
     # BF16x2, captured with `bench.py --mode traffic --prec bf16x2 --scheds ...` under
     # `ncu --metrics gpu__time_duration.sum,dram__bytes_read.sum,dram__bytes_write.sum`
-    ("bf16x2", (6, 6)): 306.6e6, ("bf16x2", (6, 7)): 305.8e6, ("bf16x2", (6, 8)): 305.8e6,
-    ("bf16x2", (6, 15)): 412.2e6, ("bf16x2", (6, 16)): 361.5e6, ("bf16x2", (6, 17)): 360.7e6,
-    ("bf16x2", (7, 6)): 303.8e6, ("bf16x2", (7, 7)): 302.9e6, ("bf16x2", (7, 8)): 303.4e6,
-    ("bf16x2", (7, 15)): 408.5e6, ("bf16x2", (7, 16)): 358.9e6, ("bf16x2", (7, 17)): 358.6e6,
-    ("bf16x2", (8, 6)): 304.2e6, ("bf16x2", (8, 7)): 303.6e6, ("bf16x2", (8, 8)): 304.3e6,
-    ("bf16x2", (8, 15)): 409.0e6, ("bf16x2", (8, 16)): 360.4e6, ("bf16x2", (8, 17)): 359.7e6,
+    ("bf16x2", (6, 6)): 306.0e6, ("bf16x2", (6, 7)): 306.4e6, ("bf16x2", (6, 8)): 305.2e6,
+    ("bf16x2", (6, 15)): 410.8e6, ("bf16x2", (6, 16)): 360.8e6, ("bf16x2", (6, 17)): 362.4e6,
+    ("bf16x2", (7, 6)): 303.8e6, ("bf16x2", (7, 7)): 302.6e6, ("bf16x2", (7, 8)): 302.9e6,
+    ("bf16x2", (7, 15)): 408.8e6, ("bf16x2", (7, 16)): 357.4e6, ("bf16x2", (7, 17)): 358.7e6,
+    ("bf16x2", (8, 6)): 304.2e6, ("bf16x2", (8, 7)): 302.8e6, ("bf16x2", (8, 8)): 303.6e6,
+    ("bf16x2", (8, 15)): 409.8e6, ("bf16x2", (8, 16)): 360.5e6, ("bf16x2", (8, 17)): 358.5e6,
 }
 
 
