@@ -174,6 +174,46 @@ def cpu_oracle_projection_sample(sb, x, budget_s=15.0):
     return flops / dt / 1e12, reps, dt, y
 
 
+_SINGLE_THREAD_SAMPLE = """
+import sys, time
+from dmrg_inputs import superblock, warmup
+from oracle import projection as oproj
+sb = superblock.load_npz(sys.argv[1])
+x = warmup.start_vector(sb.n, 0)
+budget = float(sys.argv[2])
+oproj.project_blocks(sb, x)
+t0 = time.perf_counter()
+reps = 0
+while True:
+    oproj.project_blocks(sb, x)
+    reps += 1
+    if time.perf_counter() - t0 >= budget or reps >= 5:
+        break
+print((time.perf_counter() - t0) / reps, reps)
+"""
+
+
+def cpu_oracle_single_thread(sb, budget_s=5.0):
+    """The same oracle projection with the host BLAS held to one thread: in a subprocess,
+    since the thread count of a BLAS that is already loaded cannot be changed portably.
+    Returns (TFLOP/s, projections timed, seconds each) or None if the subprocess fails."""
+    import tempfile
+    from dmrg_inputs import superblock
+    from oracle import projection as oproj
+    flops = oproj.flop_count(sb)["flops"]
+    env = dict(os.environ, OPENBLAS_NUM_THREADS="1", OMP_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    try:
+        with tempfile.TemporaryDirectory() as d:
+            path = os.path.join(d, "superblock.npz")
+            superblock.save_npz(sb, path)
+            r = subprocess.run([sys.executable, "-c", _SINGLE_THREAD_SAMPLE, path, str(budget_s)],
+                               env=env, cwd=ROOT, capture_output=True, text=True, timeout=600)
+        dt, reps = r.stdout.split()[-2:]
+        return flops / float(dt) / 1e12, int(reps), float(dt)
+    except Exception:
+        return None
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -594,6 +634,11 @@ def main():
         cpu = {"value": val, "unit": "TFLOP/s", "cores": os.cpu_count(), "kind": "oracle",
                "sample": f"{reps} FP64 oracle projections (NumPy, Eq. 11) of the same "
                          f"superblock, {dt:.2f} s each"}
+        one = cpu_oracle_single_thread(sb)
+        cpu["single_thread"] = None if one is None else {
+            "value": one[0], "unit": "TFLOP/s", "cores": 1,
+            "sample": f"{one[1]} projections with the host BLAS held to one thread, "
+                      f"{one[2]:.2f} s each"}
         ymax = float(np.max(np.abs(y_ref)))
         proj_err = {p: float(np.max(np.abs(proj_out[p] - y_ref)) / ymax) for p in variants}
 
