@@ -214,6 +214,15 @@ def cpu_oracle_single_thread(sb, budget_s=5.0):
         return None
 
 
+def workload_config(name, n, flops, ws):
+    """The `config` object of a bench line: what defines the workload and its timing, the
+    same in both arms (run-specific facts go to the line's `run` object)."""
+    return {"workload": name, "desc": workload_desc(name), "n": n,
+            "flops_per_projection": flops, "tol": 1e-10, "parallelism": f"replicas x{ws}",
+            "l2": f"solve working set (V, W: 2 x 20 x {8 * n / 1e6:.0f} MB) > L2; "
+                  "L2 flushed between projection timings"}
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -237,8 +246,7 @@ def run_reference(args):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": dt * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "desc": WORKLOAD_DESC, "n": sb.n,
-                   "flops_per_projection": flops},
+        "config": workload_config(WORKLOAD, sb.n, flops, ws),
         "cpu_baseline": {"value": val, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
                          "sample": f"each step = one FP64 oracle projection (Eq. 11, NumPy) "
                                    f"of the {WORKLOAD} superblock"},
@@ -652,14 +660,10 @@ def main():
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64" if prec == "fp64" else f"{prec}+f64",
             "data": "synthetic (seeded warm-up generator; operators shaped like the paper's runs)",
-            "config": {"workload": args.workload, "desc": workload_desc(args.workload), "n": sb.n,
-                       "prec": prec,
-                       "records": plan.stats["records"], "flops_per_projection": flops,
-                       "tol": 1e-10, "parallelism": f"replicas x{ws}",
-                       "l2": f"solve working set (V, W: 2 x 20 x {8 * sb.n / 1e6:.0f} MB) > L2; "
-                             "L2 flushed between projection timings",
-                       "tc_schedule": plan.get_stats()["tc_schedule"],
-                       "device_gb": (plan.get_stats()["device_bytes"] + 8 * 44 * sb.n) / 1e9},
+            "config": workload_config(args.workload, sb.n, flops, ws),
+            "run": {"prec": prec, "anchor_prec": args.anchor, "records": plan.stats["records"],
+                    "tc_schedule": plan.get_stats()["tc_schedule"],
+                    "device_gb": (plan.get_stats()["device_bytes"] + 8 * 44 * sb.n) / 1e9},
             "solve": {"ms": t_step * 1e3, "start_vector_seeds": seeds,
                       "iters": statistics.mean(i["iters"] for i in infos),
                       "iters_per_step": [i["iters"] for i in infos],
